@@ -1,0 +1,20 @@
+"""Plain FP64 CPU oracle of the KFBI layer-potential apply and the Dirichlet BVP solve.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the CUDA library, its Python
+binding) may import, call or link anything in this package.  Only the tests, the
+``smoke()`` check in ``__graft_entry__`` and the ``cpu_baseline`` / ``--impl reference``
+legs of ``bench.py`` use it.  It shares no code with the CUDA path; the only common
+module is ``kfbi_workloads`` (seeded input generators, no method arithmetic).
+
+Every function follows the method as the paper states it (Sec. 2.1-2.2, Alg. 1-5),
+with the readings of unstated details written out in each docstring.
+"""
+from .kfbi2d import (GeometryError, Geometry2D, jumps_cartesian, box_solve_dst,
+                     box_solve_dense, correct_rhs, interpolate_plus, apply_interface,
+                     apply_double_layer, apply_volume, combined_grid_solution, gmres,
+                     richardson, solve_bvp, error_norms, lagrange_basis)
+
+__all__ = ["GeometryError", "Geometry2D", "jumps_cartesian", "box_solve_dst",
+           "box_solve_dense", "correct_rhs", "interpolate_plus", "apply_interface",
+           "apply_double_layer", "apply_volume", "combined_grid_solution", "gmres",
+           "richardson", "solve_bvp", "error_norms", "lagrange_basis"]
