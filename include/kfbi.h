@@ -1,0 +1,190 @@
+/*
+ * kfbi.h - C ABI of the GB300 (sm_103a) kernel-free boundary integral (KFBI) library.
+ *
+ * The library evaluates the double-layer boundary operator K_D = 1/2 I + W of the
+ * modified Helmholtz / Poisson equation  Lap u - kappa^2 u = f  on a 2-D domain Omega
+ * embedded in the box B = [lo, hi]^2, WITHOUT a Green's function: the potential is the
+ * solution of the equivalent interface problem on a Cartesian grid of B (paper Sec. 2.2,
+ * "Indirect evaluation of integrals"; table of F and Phi there):
+ *     Lap v - kappa^2 v = F in B \ Gamma,  [v] = Phi,  [d_n v] = psi on Gamma,  v = 0 on dB,
+ * discretised by Alg. 1: jumps at grid-line/interface crossings, Taylor correction of the
+ * right-hand side at irregular nodes (Alg. 2), a fast sine-transform box solve (Alg. 4),
+ * corrected interpolation to the control points (Alg. 3).  The Dirichlet BVP is solved
+ * through the BIE 1/2 phi + W phi + Y f = g (Sec. 2.1) by restarted GMRES (Alg. 5), in
+ * plain FP64 or in mixed precision (FP32 box solves with FP64 iterative refinement).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named d_* are DEVICE pointers owned by the caller (e.g. allocated through
+ *     PyTorch); the library never frees them and never keeps them after the call returns.
+ *     Pointers named h_* are host pointers.  All arrays are contiguous, C order, FP64.
+ *   - Grid arrays are (N+1) x (N+1) with x fastest: a[j*(N+1) + i] = value at
+ *     (lo + i h, lo + j h), h = (hi - lo)/N.
+ *   - Interface arrays have M entries (points/normals: M x 2, interleaved x,y).  Points
+ *     are counter-clockwise samples of Gamma at equispaced parameter t_k = 2 pi k / M;
+ *     normals are outward unit normals; curv is the signed curvature (> 0 where convex).
+ *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed as void*,
+ *     NULL = legacy default stream) unless documented as synchronising.
+ *   - All workspace is allocated by kfbi_setup; apply and solve calls allocate nothing.
+ *   - Errors are returned as kfbi_status; kfbi_last_error() gives a message for the
+ *     calling thread.  No entry point aborts, exits or traps on the device.
+ *   - A context may be used by one host thread at a time.
+ */
+#ifndef KFBI_H
+#define KFBI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kfbi_ctx_s* kfbi_ctx;
+
+typedef enum {
+  KFBI_OK = 0,
+  KFBI_ERR_ARG = 1,            /* bad argument (null pointer, size, option)            */
+  KFBI_ERR_GEOMETRY = 2,       /* interface under-resolved, tangent to a grid line at a
+                                  point with no label change, or within two cells of dB */
+  KFBI_ERR_NOMEM = 3,          /* device allocation failed in kfbi_setup                 */
+  KFBI_ERR_CUDA = 4,           /* a CUDA runtime call failed                             */
+  KFBI_ERR_NOT_CONVERGED = 5,  /* GMRES reached its iteration limit; outputs hold the
+                                  last iterate and info->rel_residual its residual      */
+  KFBI_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up                     */
+  KFBI_ERR_NUMERIC = 7,        /* NaN/Inf met in the iteration                           */
+  KFBI_ERR_UNSUPPORTED = 8     /* valid request this build does not implement            */
+} kfbi_status;
+
+typedef enum {
+  KFBI_FP64 = 0,         /* every stage in FP64                                          */
+  KFBI_MIXED_FP32 = 1    /* box solve in FP32; geometry, jumps, Arnoldi, Givens and the
+                            refinement residual in FP64 (GMRES-IR)                       */
+} kfbi_precision;
+
+typedef enum {
+  KFBI_DOUBLE_LAYER = 0, /* [v] = density, [d_n v] = 0: returns v^+ = (1/2 I + W) density */
+  KFBI_SINGLE_LAYER = 1  /* [v] = 0, [d_n v] = density: returns v^+ on Gamma              */
+} kfbi_layer;
+
+typedef struct {
+  int dim;              /* 2                                                            */
+  int N;                /* cells per side, N = 2^a or 3*2^a, 32 <= N <= 16384            */
+  double lo, hi;        /* box [lo, hi]^dim                                             */
+  double kappa;         /* >= 0; PDE Lap u - kappa^2 u = f                               */
+  int precision;        /* kfbi_precision used by kfbi_solve_bvp                         */
+  int gmres_m;          /* GMRES restart length (Alg. 5), 1..128                         */
+  int max_restarts;     /* FP64: GMRES restarts; mixed: outer refinement steps           */
+  double tol;           /* stop when ||g_hat - K_D phi||_2 <= tol ||g_hat||_2            */
+  double inner_tol;     /* mixed: relative tolerance of each inner FP32-apply GMRES      */
+} kfbi_options;
+
+typedef struct {
+  int iterations;        /* Arnoldi steps over all cycles                                 */
+  int outer_iterations;  /* mixed: refinement steps; FP64: restart cycles                 */
+  int applies_fp64;      /* K_D (and Y) applies with an FP64 box solve                   */
+  int applies_low;       /* K_D applies with an FP32 box solve                           */
+  double rel_residual;   /* final ||g_hat - K_D phi|| / ||g_hat|| (FP64 apply)           */
+  int converged;         /* 1 if rel_residual <= tol                                     */
+} kfbi_solve_info;
+
+typedef struct {
+  int N, M;
+  int n_crossings_x;     /* crossings of Gamma with the lines x = x_i                     */
+  int n_crossings_y;     /* crossings of Gamma with the lines y = y_j                     */
+  int n_irregular;       /* interior nodes with a 5-point neighbour across Gamma          */
+  int n_inside;          /* grid nodes inside Omega                                      */
+  int64_t device_bytes;  /* workspace held by the context                                */
+} kfbi_ctx_info;
+
+/* Fills *opt with dim 2, N 128, box [-1,1], kappa 0, FP64, m 50, 20 restarts,
+   tol 1e-10, inner_tol 1e-6. */
+void kfbi_default_options(kfbi_options* opt);
+
+/* Builds the discrete interface problem on the device (Procedure 1 of Sec. 4.4, Alg. 1
+   steps 1-3): the periodic degree-5 interpolant of the control points, the crossings
+   of Gamma with every grid line, the inside/outside node labels, the compacted list
+   of irregular nodes with their crossed arms (Sec. 2.2, Fig. of irregular nodes), and
+   the FP64 linear maps density -> corrected right-hand side (Alg. 2) and grid values
+   -> v^+ at the control points (Alg. 3).  All geometry is computed in FP64 on the GPU.
+   d_pts, d_normals: M x 2; d_curv: M.  Synchronises the stream (reads back counts).
+   Returns KFBI_ERR_GEOMETRY for an under-resolved interface; *out is NULL on error. */
+kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
+                       const double* d_normals, const double* d_curv, void* stream,
+                       kfbi_ctx* out);
+
+/* One layer-potential apply (the hot path, Alg. 1 steps 4-6): jumps from the density
+   (Alg. 2 line 4), RHS correction at irregular nodes, sine-transform box solve (Alg. 4)
+   in the given precision, corrected interpolation to the control points (Alg. 3).
+   For KFBI_DOUBLE_LAYER the result is K_D density = (1/2 I + W) density (Sec. 3.3).
+   d_density, d_out: M values.  Asynchronous. */
+kfbi_status kfbi_apply_layer_potential(kfbi_ctx ctx, int layer, int precision,
+                                       const double* d_density, double* d_out, void* stream);
+
+/* (Y f)^+ at the control points: interface problem with F = zero extension of f to
+   the box and Phi = 0 (Sec. 2.2 table).  d_f_grid: (N+1)^2, values outside Omega are
+   ignored; d_f_ctrl: f at the M control points (gives the jump [F] on Gamma). */
+kfbi_status kfbi_apply_volume(kfbi_ctx ctx, int precision, const double* d_f_grid,
+                              const double* d_f_ctrl, double* d_out, void* stream);
+
+/* Full interface solve with [v] = density, [d_n v] = 0, F = zero-extended f: writes the
+   corrected right-hand side (d_rhs_grid, may be NULL), the grid solution v on all nodes
+   (d_v_grid, may be NULL) and v^+ at the control points (d_out, may be NULL).
+   d_density, d_f_grid, d_f_ctrl may each be NULL (= zero).  Exposes the stages of one
+   apply for testing and post-processing. */
+kfbi_status kfbi_interface_solve(kfbi_ctx ctx, int precision, const double* d_density,
+                                 const double* d_f_grid, const double* d_f_ctrl,
+                                 double* d_rhs_grid, double* d_v_grid, double* d_out,
+                                 void* stream);
+
+/* Box solve alone (Alg. 4): (Lap_h - kappa^2) v = b at interior nodes, v = 0 on dB,
+   b and v (N+1)^2 grids (boundary entries of b ignored). */
+kfbi_status kfbi_box_solve(kfbi_ctx ctx, int precision, const double* d_b_grid,
+                           double* d_v_grid, void* stream);
+
+/* Dirichlet BVP (Procedures 2-3 of Sec. 4.4): g_hat = g - (Y f)^+, K_D phi = g_hat by
+   GMRES(m) (Alg. 5; FP64 Arnoldi with CGS2 and Givens rotations on the device), then
+   u = W phi + Y f on the grid (Sec. 2.1).  opt->precision selects plain FP64 or mixed
+   FP32 box solves with FP64 iterative refinement of the BIE residual.
+   d_u_grid: (N+1)^2, written inside Omega, zero outside.  d_density_out: M or NULL.
+   h_info: host struct or NULL.  Synchronising (convergence is checked on the host). */
+kfbi_status kfbi_solve_bvp(kfbi_ctx ctx, const double* d_f_grid, const double* d_f_ctrl,
+                           const double* d_g_ctrl, double* d_u_grid, double* d_density_out,
+                           kfbi_solve_info* h_info, void* stream);
+
+/* Node labels: d_mask[(N+1)^2] = 1 inside Omega, 0 outside.  Asynchronous. */
+kfbi_status kfbi_get_inside_mask(kfbi_ctx ctx, uint8_t* d_mask, void* stream);
+
+/* Counts and sizes of the context (host struct).  No device work. */
+kfbi_status kfbi_get_info(kfbi_ctx ctx, kfbi_ctx_info* h_info);
+
+/* Sets the precision / restart / tolerance fields used by later kfbi_solve_bvp calls. */
+kfbi_status kfbi_set_solver(kfbi_ctx ctx, int precision, int gmres_m, int max_restarts,
+                            double tol, double inner_tol);
+
+/* Releases all device memory of the context.  Synchronises its stream first. */
+kfbi_status kfbi_destroy(kfbi_ctx ctx);
+
+const char* kfbi_status_string(kfbi_status s);
+const char* kfbi_last_error(void);
+
+/* ---------------------------------------------------------------- batched problems
+   Many independent 2-D problems (uneven N and M) solved together: every GMRES step
+   runs one apply per problem with the problems' kernels launched back to back on the
+   same stream and the small Arnoldi kernels of all problems fused into single launches.
+   The contexts stay owned by the caller and must outlive the batch. */
+typedef struct kfbi_batch_s* kfbi_batch;
+
+kfbi_status kfbi_batch_create(const kfbi_ctx* ctxs, int count, kfbi_batch* out);
+
+/* Solves count x nrhs BVPs: problem p, right-hand side r uses d_f_grid[p*nrhs + r],
+   d_f_ctrl[...], d_g_ctrl[...] and writes d_u_grid[p*nrhs + r] (device pointers, layout
+   as in kfbi_solve_bvp).  h_info: count*nrhs structs or NULL.  Synchronising. */
+kfbi_status kfbi_batch_solve(kfbi_batch b, int nrhs, const double* const* d_f_grid,
+                             const double* const* d_f_ctrl, const double* const* d_g_ctrl,
+                             double* const* d_u_grid, kfbi_solve_info* h_info, void* stream);
+
+kfbi_status kfbi_batch_destroy(kfbi_batch b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KFBI_H */

@@ -1,0 +1,321 @@
+// extern "C" entry points of libkfbi (declared and documented in include/kfbi.h).
+#include <cstdarg>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kfbi_internal.cuh"
+
+namespace kfbi {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+kfbi_status alloc_bytes(Ctx& c, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return KFBI_ERR_NOMEM;
+  }
+  e = cudaMemsetAsync(*p, 0, bytes, c.stream);
+  if (e != cudaSuccess) {
+    set_error("cudaMemsetAsync failed: %s", cudaGetErrorString(e));
+    return KFBI_ERR_CUDA;
+  }
+  c.allocs.push_back(*p);
+  c.bytes += (int64_t)bytes;
+  return KFBI_OK;
+}
+
+}  // namespace kfbi
+
+using kfbi::Ctx;
+
+static void free_handle(kfbi_ctx_s* hd) {
+  if (!hd) return;
+  Ctx& c = hd->c;
+  if (c.stream) cudaStreamSynchronize(c.stream);
+  for (void* p : c.allocs) cudaFree(p);
+  if (c.basis) {
+    cudaFree(c.basis); cudaFree(c.hess); cudaFree(c.givens); cudaFree(c.gvec);
+    cudaFree(c.hcol); cudaFree(c.yvec);
+  }
+  if (c.h_pinned) cudaFreeHost(c.h_pinned);
+  delete hd;
+}
+
+extern "C" {
+
+void kfbi_default_options(kfbi_options* o) {
+  if (!o) return;
+  o->dim = 2;
+  o->N = 128;
+  o->lo = -1.0;
+  o->hi = 1.0;
+  o->kappa = 0.0;
+  o->precision = KFBI_FP64;
+  o->gmres_m = 50;
+  o->max_restarts = 20;
+  o->tol = 1e-10;
+  o->inner_tol = 1e-6;
+}
+
+const char* kfbi_status_string(kfbi_status s) {
+  switch (s) {
+    case KFBI_OK: return "ok";
+    case KFBI_ERR_ARG: return "invalid argument";
+    case KFBI_ERR_GEOMETRY: return "interface geometry rejected";
+    case KFBI_ERR_NOMEM: return "out of device memory";
+    case KFBI_ERR_CUDA: return "CUDA error";
+    case KFBI_ERR_NOT_CONVERGED: return "GMRES did not converge";
+    case KFBI_ERR_TIMEOUT: return "device wait timed out";
+    case KFBI_ERR_NUMERIC: return "non-finite value in the iteration";
+    case KFBI_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+const char* kfbi_last_error(void) { return kfbi::g_err; }
+
+kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
+                       const double* d_normals, const double* d_curv, void* stream,
+                       kfbi_ctx* out) {
+  if (out) *out = nullptr;
+  if (!opt || !out || !d_pts || !d_normals || !d_curv) {
+    kfbi::set_error("kfbi_setup: null argument");
+    return KFBI_ERR_ARG;
+  }
+  if (opt->dim != 2) {
+    kfbi::set_error("kfbi_setup: only dim = 2 is implemented");
+    return KFBI_ERR_UNSUPPORTED;
+  }
+  kfbi::FftPlan plan;
+  if (!kfbi::make_fft_plan(opt->N, &plan) || opt->N > 8192) {
+    kfbi::set_error("kfbi_setup: N = %d must be 2^a or 3*2^a with 32 <= N <= 8192", opt->N);
+    return KFBI_ERR_ARG;
+  }
+  if (M < 8 || M > (1 << 22) || !(opt->hi > opt->lo) || !(opt->kappa >= 0.0) ||
+      opt->gmres_m < 1 || opt->gmres_m > 128 || opt->max_restarts < 0 || !(opt->tol > 0.0)) {
+    kfbi::set_error("kfbi_setup: bad size or option");
+    return KFBI_ERR_ARG;
+  }
+  kfbi_ctx_s* hd = new (std::nothrow) kfbi_ctx_s();
+  if (!hd) return KFBI_ERR_NOMEM;
+  Ctx& c = hd->c;
+  c.opt = *opt;
+  c.N = opt->N;
+  c.M = (int)M;
+  c.lo = opt->lo;
+  c.hi = opt->hi;
+  c.h = (opt->hi - opt->lo) / opt->N;
+  c.kappa = opt->kappa;
+  c.kappa2 = opt->kappa * opt->kappa;
+  c.stream = (cudaStream_t)stream;
+  c.plan = plan;
+  kfbi_status s = KFBI_OK;
+  const size_t grid = (size_t)c.N * c.N;
+#define SETUP_TRY(expr)       \
+  do {                        \
+    s = (expr);               \
+    if (s != KFBI_OK) {       \
+      free_handle(hd);        \
+      return s;               \
+    }                         \
+  } while (0)
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.err_flag, sizeof(int) * 4));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.pts, sizeof(double) * 2 * M));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.nrm, sizeof(double) * 2 * M));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.curv, sizeof(double) * M));
+  if (cudaMemcpyAsync(c.pts, d_pts, sizeof(double) * 2 * M, cudaMemcpyDeviceToDevice, c.stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(c.nrm, d_normals, sizeof(double) * 2 * M, cudaMemcpyDeviceToDevice,
+                      c.stream) != cudaSuccess ||
+      cudaMemcpyAsync(c.curv, d_curv, sizeof(double) * M, cudaMemcpyDeviceToDevice, c.stream) !=
+          cudaSuccess) {
+    kfbi::set_error("kfbi_setup: copying the interface failed: %s",
+                    cudaGetErrorString(cudaGetLastError()));
+    free_handle(hd);
+    return KFBI_ERR_CUDA;
+  }
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.B32, sizeof(float) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.V32, sizeof(float) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.B64, sizeof(double) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.V64, sizeof(double) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.scal, sizeof(double) * 16));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.vecs, sizeof(double) * 8 * M));
+  if (cudaMallocHost((void**)&c.h_pinned, sizeof(double) * 16) != cudaSuccess) {
+    kfbi::set_error("kfbi_setup: pinned host allocation failed");
+    free_handle(hd);
+    return KFBI_ERR_NOMEM;
+  }
+  SETUP_TRY(kfbi::init_box_tables(c));
+  SETUP_TRY(kfbi::setup_geometry(c));
+  SETUP_TRY(kfbi::alloc_gmres(c, c.opt.gmres_m));
+  if (cudaStreamSynchronize(c.stream) != cudaSuccess) {
+    kfbi::set_error("kfbi_setup: %s", cudaGetErrorString(cudaGetLastError()));
+    free_handle(hd);
+    return KFBI_ERR_CUDA;
+  }
+#undef SETUP_TRY
+  *out = hd;
+  return KFBI_OK;
+}
+
+static Ctx* ctx_of(kfbi_ctx h, cudaStream_t st) {
+  if (!h) return nullptr;
+  h->c.stream = st;
+  return &h->c;
+}
+
+kfbi_status kfbi_apply_layer_potential(kfbi_ctx ctx, int layer, int precision,
+                                       const double* d_density, double* d_out, void* stream) {
+  Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
+  if (!c || !d_density || !d_out || (layer != KFBI_DOUBLE_LAYER && layer != KFBI_SINGLE_LAYER) ||
+      (precision != KFBI_FP64 && precision != KFBI_MIXED_FP32)) {
+    kfbi::set_error("kfbi_apply_layer_potential: bad argument");
+    return KFBI_ERR_ARG;
+  }
+  return kfbi::apply_potential(*c, layer == KFBI_DOUBLE_LAYER ? kfbi::Layer::Double
+                                                              : kfbi::Layer::Single,
+                               precision, d_density, d_out);
+}
+
+kfbi_status kfbi_apply_volume(kfbi_ctx ctx, int precision, const double* d_f_grid,
+                              const double* d_f_ctrl, double* d_out, void* stream) {
+  Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
+  if (!c || !d_f_grid || !d_f_ctrl || !d_out ||
+      (precision != KFBI_FP64 && precision != KFBI_MIXED_FP32)) {
+    kfbi::set_error("kfbi_apply_volume: bad argument");
+    return KFBI_ERR_ARG;
+  }
+  return kfbi::interface_solve(*c, precision, nullptr, d_f_grid, d_f_ctrl, nullptr, nullptr,
+                               d_out);
+}
+
+kfbi_status kfbi_interface_solve(kfbi_ctx ctx, int precision, const double* d_density,
+                                 const double* d_f_grid, const double* d_f_ctrl,
+                                 double* d_rhs_grid, double* d_v_grid, double* d_out,
+                                 void* stream) {
+  Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
+  if (!c || (precision != KFBI_FP64 && precision != KFBI_MIXED_FP32)) {
+    kfbi::set_error("kfbi_interface_solve: bad argument");
+    return KFBI_ERR_ARG;
+  }
+  return kfbi::interface_solve(*c, precision, d_density, d_f_grid, d_f_ctrl, d_rhs_grid, d_v_grid,
+                               d_out);
+}
+
+kfbi_status kfbi_box_solve(kfbi_ctx ctx, int precision, const double* d_b_grid, double* d_v_grid,
+                           void* stream) {
+  Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
+  if (!c || !d_b_grid || !d_v_grid || (precision != KFBI_FP64 && precision != KFBI_MIXED_FP32)) {
+    kfbi::set_error("kfbi_box_solve: bad argument");
+    return KFBI_ERR_ARG;
+  }
+  return kfbi::box_solve_grid(*c, precision, d_b_grid, d_v_grid);
+}
+
+kfbi_status kfbi_solve_bvp(kfbi_ctx ctx, const double* d_f_grid, const double* d_f_ctrl,
+                           const double* d_g_ctrl, double* d_u_grid, double* d_density_out,
+                           kfbi_solve_info* h_info, void* stream) {
+  Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
+  if (!c || !d_f_grid || !d_f_ctrl || !d_g_ctrl) {
+    kfbi::set_error("kfbi_solve_bvp: bad argument");
+    return KFBI_ERR_ARG;
+  }
+  return kfbi::solve_bvp(*c, d_f_grid, d_f_ctrl, d_g_ctrl, d_u_grid, d_density_out, h_info);
+}
+
+kfbi_status kfbi_get_inside_mask(kfbi_ctx ctx, uint8_t* d_mask, void* stream) {
+  Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
+  if (!c || !d_mask) return KFBI_ERR_ARG;
+  return kfbi::inside_mask(*c, d_mask);
+}
+
+kfbi_status kfbi_get_info(kfbi_ctx ctx, kfbi_ctx_info* info) {
+  if (!ctx || !info) return KFBI_ERR_ARG;
+  const Ctx& c = ctx->c;
+  info->N = c.N;
+  info->M = c.M;
+  info->n_crossings_x = c.ncross[0];
+  info->n_crossings_y = c.ncross[1];
+  info->n_irregular = c.nirr;
+  info->n_inside = c.n_inside;
+  info->device_bytes = c.bytes + (int64_t)sizeof(double) * ((int64_t)(c.gm_m + 1) * c.M);
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_set_solver(kfbi_ctx ctx, int precision, int gmres_m, int max_restarts,
+                            double tol, double inner_tol) {
+  if (!ctx || (precision != KFBI_FP64 && precision != KFBI_MIXED_FP32) || gmres_m < 1 ||
+      gmres_m > 128 || max_restarts < 0 || !(tol > 0) || !(inner_tol > 0)) {
+    kfbi::set_error("kfbi_set_solver: bad argument");
+    return KFBI_ERR_ARG;
+  }
+  Ctx& c = ctx->c;
+  c.opt.precision = precision;
+  c.opt.gmres_m = gmres_m;
+  c.opt.max_restarts = max_restarts;
+  c.opt.tol = tol;
+  c.opt.inner_tol = inner_tol;
+  return kfbi::alloc_gmres(c, gmres_m);
+}
+
+kfbi_status kfbi_destroy(kfbi_ctx ctx) {
+  if (!ctx) return KFBI_ERR_ARG;
+  free_handle(ctx);
+  return KFBI_OK;
+}
+
+// ---------------------------------------------------------------- batches
+struct kfbi_batch_s {
+  std::vector<kfbi_ctx> ctxs;
+};
+
+kfbi_status kfbi_batch_create(const kfbi_ctx* ctxs, int count, kfbi_batch* out) {
+  if (out) *out = nullptr;
+  if (!ctxs || !out || count < 1) {
+    kfbi::set_error("kfbi_batch_create: bad argument");
+    return KFBI_ERR_ARG;
+  }
+  kfbi_batch_s* b = new (std::nothrow) kfbi_batch_s();
+  if (!b) return KFBI_ERR_NOMEM;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i]) {
+      delete b;
+      kfbi::set_error("kfbi_batch_create: null context %d", i);
+      return KFBI_ERR_ARG;
+    }
+    b->ctxs.push_back(ctxs[i]);
+  }
+  *out = b;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_batch_solve(kfbi_batch b, int nrhs, const double* const* d_f_grid,
+                             const double* const* d_f_ctrl, const double* const* d_g_ctrl,
+                             double* const* d_u_grid, kfbi_solve_info* h_info, void* stream) {
+  if (!b || nrhs < 1 || !d_f_grid || !d_f_ctrl || !d_g_ctrl || !d_u_grid) {
+    kfbi::set_error("kfbi_batch_solve: bad argument");
+    return KFBI_ERR_ARG;
+  }
+  return kfbi::batch_solve(b->ctxs.data(), (int)b->ctxs.size(), nrhs, d_f_grid, d_f_ctrl,
+                           d_g_ctrl, d_u_grid, h_info, (cudaStream_t)stream);
+}
+
+kfbi_status kfbi_batch_destroy(kfbi_batch b) {
+  if (!b) return KFBI_ERR_ARG;
+  delete b;
+  return KFBI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,156 @@
+// Internal definitions of the GB300 KFBI library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/kfbi.h"
+
+namespace kfbi {
+
+void set_error(const char* fmt, ...);
+
+#define KFBI_CUDA_TRY(expr)                                                          \
+  do {                                                                               \
+    cudaError_t e_ = (expr);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      ::kfbi::set_error("%s:%d: %s -> %s", __FILE__, __LINE__, #expr,                \
+                        cudaGetErrorString(e_));                                     \
+      return KFBI_ERR_CUDA;                                                          \
+    }                                                                                \
+  } while (0)
+
+#define KFBI_TRY(expr)                 \
+  do {                                 \
+    kfbi_status s_ = (expr);           \
+    if (s_ != KFBI_OK) return s_;      \
+  } while (0)
+
+// ------------------------------------------------------------------ FFT plan
+// Complex FFT of length N = 2^a or 3*2^a in shared memory.  Every thread of a line
+// holds EPT values per stage; each stage radix divides EPT (16 for 2^a, 24 for 3*2^a).
+struct FftPlan {
+  int N;
+  int ept;       // values per thread per stage
+  int tpl;       // threads per line = N / ept
+  int nst;       // number of stages
+  int radix[12];
+};
+
+bool make_fft_plan(int N, FftPlan* p);
+
+// Padded shared-memory index: one spare slot every 16 complex values keeps the
+// stride-R writes of a Stockham stage free of bank conflicts.
+__host__ __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int padded_len(int N) { return N + (N >> 4) + 1; }
+
+// Device tables of one precision for the box solve on an N x N work grid.
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { typedef float2 type; };
+template <> struct Vec2<double> { typedef double2 type; };
+
+template <typename T>
+struct BoxTables {
+  typename Vec2<T>::type* tw;  // e^{-i pi t/N}, t < 2N
+  T* lam;        // lambda_k = -(4/h^2) sin^2(pi k / 2N), k < N (lam[0] unused)
+};
+
+// ------------------------------------------------------------------ context
+struct Ctx {
+  // problem
+  int N = 0, M = 0;
+  double lo = -1, hi = 1, h = 0, kappa = 0, kappa2 = 0;
+  kfbi_options opt{};
+  cudaStream_t stream = nullptr;
+  FftPlan plan{};
+
+  // interface (device, FP64)
+  double* pts = nullptr;      // M x 2
+  double* nrm = nullptr;      // M x 2
+  double* curv = nullptr;     // M
+
+  // crossings: axis 0 = on vertical lines x = x_i, axis 1 = on horizontal lines y = y_j
+  int ncross[2] = {0, 0};
+  int* cr_line[2] = {nullptr, nullptr};
+  int* cr_seg[2] = {nullptr, nullptr};
+  double* cr_tau[2] = {nullptr, nullptr};
+  double* cr_along[2] = {nullptr, nullptr};   // coordinate along the line (snapped)
+  int* line_ptr[2] = {nullptr, nullptr};      // CSR over lines (N+2 entries), sorted by along
+  int* cr_flip[2] = {nullptr, nullptr};       // arm index (lower node) each crossing belongs to
+
+  uint8_t* inside = nullptr;                  // (N+1)^2 labels
+
+  // irregular nodes and their crossed arms (CSR)
+  int nirr = 0, narms = 0;
+  int* irr_node = nullptr;                    // work-grid index j*N + i
+  int* arm_ptr = nullptr;                     // nirr + 1
+  int* arm_seg = nullptr;                     // narms: segment of the crossing
+  double* arm_wD = nullptr;                   // narms x 6: density -> correction (double layer)
+  double* arm_wS = nullptr;                   // narms x 6: density -> correction (single layer)
+  double* arm_wF = nullptr;                   // narms x 6: f on Gamma -> correction (volume)
+
+  // control points: 6-node stencils
+  int* ctrl_node = nullptr;                   // M x 6 work-grid index, -1 on the box boundary
+  double* ctrl_w = nullptr;                   // M x 6 quadratic interpolation weights
+  double* ctrl_cD = nullptr;                  // M x 6 density weights of the jump Taylor terms
+  double* ctrl_cS = nullptr;                  // M x 6 (single layer)
+  double* ctrl_eF = nullptr;                  // M   f(z) weight of the jump Taylor terms
+
+  // work grids (N x N, row 0 and column 0 identically zero)
+  float* B32 = nullptr;  float* V32 = nullptr;     // sparse RHS (irregular entries only), work
+  double* B64 = nullptr; double* V64 = nullptr;
+  BoxTables<float> t32{};
+  BoxTables<double> t64{};
+
+  // GMRES workspace (FP64)
+  int gm_m = 0;
+  double* basis = nullptr;     // (m+1) x M
+  double* hess = nullptr;      // (m+1) x m, column major: hess[j*(m+1) + i]
+  double* givens = nullptr;    // 2m (c, s)
+  double* gvec = nullptr;      // m+1
+  double* hcol = nullptr;      // m+1 scratch dot products
+  double* scal = nullptr;      // 16 scalars
+  double* vecs = nullptr;      // 6 x M scratch vectors
+  double* yvec = nullptr;      // m
+  double* h_pinned = nullptr;  // pinned host mirror of scal
+  int* err_flag = nullptr;     // device error flag
+
+  int64_t bytes = 0;
+  int n_inside = 0;
+  std::vector<void*> allocs;                  // device allocations owned by the context
+};
+
+// ------------------------------------------------------------------ stages
+kfbi_status setup_geometry(Ctx& c);                 // setup2d.cu
+kfbi_status alloc_bytes(Ctx& c, void** p, size_t bytes);
+
+// box solve (dst.cu): three passes in place on the N x N work grid `work`, reading the
+// right-hand side from `rhs` (may equal work).
+kfbi_status box_solve_f32(Ctx& c, const float* rhs, float* work);
+kfbi_status box_solve_f64(Ctx& c, const double* rhs, double* work);
+kfbi_status init_box_tables(Ctx& c);
+
+// apply stages (apply2d.cu)
+enum class Layer { Double, Single };
+kfbi_status apply_potential(Ctx& c, Layer layer, int precision, const double* dens, double* out);
+kfbi_status interface_solve(Ctx& c, int precision, const double* dens, const double* f_grid,
+                            const double* f_ctrl, double* rhs_grid, double* v_grid,
+                            double* out);
+kfbi_status box_solve_grid(Ctx& c, int precision, const double* b_grid, double* v_grid);
+kfbi_status inside_mask(Ctx& c, uint8_t* mask);
+
+// solver (gmres.cu)
+kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const double* g_ctrl,
+                      double* u_grid, double* dens_out, kfbi_solve_info* info);
+kfbi_status alloc_gmres(Ctx& c, int m);
+kfbi_status batch_solve(kfbi_ctx* ctxs, int count, int nrhs, const double* const* f_grid,
+                        const double* const* f_ctrl, const double* const* g_ctrl,
+                        double* const* u_grid, kfbi_solve_info* info, cudaStream_t stream);
+
+}  // namespace kfbi
+
+struct kfbi_ctx_s {
+  kfbi::Ctx c;
+};

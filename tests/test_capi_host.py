@@ -1,0 +1,61 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for sm_103a, loads,
+exports every function include/kfbi.h declares, and rejects bad arguments before any
+device work."""
+import ctypes
+import os
+
+import pytest
+
+import paper_2404_15249_gb300 as K
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(K.LIB_PATH):
+        from paper_2404_15249_gb300 import build
+        build.build()
+    return K.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = K.header_symbols()
+    assert len(names) >= 16
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_defaults(lib):
+    for code in range(9):
+        assert lib.kfbi_status_string(code)
+    o = K.default_options()
+    assert (o.dim, o.N, o.lo, o.hi, o.kappa, o.gmres_m, o.max_restarts) == (2, 128, -1.0, 1.0, 0.0, 50, 20)
+    assert o.tol == 1e-10 and o.precision == K.KFBI_FP64
+
+
+def test_bad_arguments_are_rejected_on_the_host(lib):
+    o = K.default_options()
+    h = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(16)
+    # null interface pointers
+    assert lib.kfbi_setup(ctypes.byref(o), 64, None, None, None, None, ctypes.byref(h)) == 1
+    # unsupported grid size (not 2^a or 3 * 2^a)
+    o.N = 100
+    assert lib.kfbi_setup(ctypes.byref(o), 64, dummy, dummy, dummy, None, ctypes.byref(h)) == 1
+    assert b"N = 100" in lib.kfbi_last_error()
+    o.N = 128
+    o.dim = 3
+    assert lib.kfbi_setup(ctypes.byref(o), 64, dummy, dummy, dummy, None, ctypes.byref(h)) == 8
+    assert not h.value
+    assert lib.kfbi_apply_layer_potential(None, 0, 0, dummy, dummy, None) == 1
+    assert lib.kfbi_destroy(None) == 1
+    assert lib.kfbi_batch_create(None, 0, ctypes.byref(h)) == 1
+
+
+def test_product_path_does_not_import_the_oracle():
+    """The binding, build script and CUDA sources never reach into oracle/."""
+    pkg = os.path.dirname(K.__file__)
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(root, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f

@@ -1,0 +1,182 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle, element by
+element on the same seeded inputs.
+
+Tolerances: plain FP64 GPU path within 1e-11 relative of the oracle (max norm over the
+control points and over the grid); FP32 box solves within 2e-5 relative for one apply;
+the mixed-precision BVP density within 1e-6 relative and its grid error below the
+discretisation error; node labels and irregular-node counts bit-exact."""
+import numpy as np
+import pytest
+
+import kfbi_workloads as W
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_2404_15249_gb300 as K
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def make(prob, **kw):
+    ctx = K.Kfbi2D(prob.iface.pts, prob.iface.normals, prob.iface.curv, prob.N, prob.kappa, **kw)
+    geom = O.Geometry2D(prob.iface.pts, prob.iface.normals, prob.iface.curv, prob.N, prob.kappa)
+    return ctx, geom
+
+
+CASES = {
+    "flower128_poisson": lambda: W.config_poisson_flower(128, 256),
+    "flower96_k1": lambda: W.config_helmholtz(96, 1.0, "flower"),
+    "ellipse256_k10": lambda: W.config_helmholtz(256, 10.0, "ellipse"),
+    "ellipse48_k1": lambda: W.Problem(W.ellipse(96, 0.7, 0.4, 30.0), 48, 1.0, W.manufactured_exp_sin2y(1.0)),
+    "star192_batchlike": lambda: W.config_batch(1, 1, seed=3, sizes=(192,))[0][0],
+}
+
+
+@pytest.mark.parametrize("N", [32, 48, 96, 128, 384])
+@pytest.mark.parametrize("kappa", [0.0, 3.0])
+def test_box_solve_parity(N, kappa):
+    prob = W.Problem(W.circle(64, 0.4, (0.01, 0.02)), N, kappa, W.manufactured_sinpi(kappa))
+    ctx, geom = make(prob)
+    rng = np.random.default_rng(N)
+    b = np.zeros((N + 1, N + 1))
+    b[1:N, 1:N] = rng.standard_normal((N - 1, N - 1))
+    ref = O.box_solve_dst(b, N, geom.h, kappa * kappa)
+    v64 = ctx.box_solve(b, K.KFBI_FP64).cpu().numpy()
+    v32 = ctx.box_solve(b, K.KFBI_MIXED_FP32).cpu().numpy()
+    assert rel(v64, ref) < 1e-12
+    assert rel(v32, ref) < 2e-5
+    assert np.all(v64[-1] == 0) and np.all(v64[:, -1] == 0) and np.all(v64[0] == 0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_geometry_labels_bit_exact(case):
+    prob = CASES[case]()
+    ctx, geom = make(prob)
+    mask = ctx.inside_mask().cpu().numpy().astype(bool)
+    assert np.array_equal(mask, geom.inside)
+    info = ctx.info()
+    assert info["n_irregular"] == int(geom.irregular.sum())
+    assert info["n_crossings_x"] == len(geom.crossings[0]["line"])
+    assert info["n_crossings_y"] == len(geom.crossings[1]["line"])
+    assert info["n_inside"] == int(geom.inside.sum())
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_interface_solve_stages_fp64(case):
+    prob = CASES[case]()
+    ctx, geom = make(prob)
+    phi = W.random_density(prob.iface.M, seed=11)
+    fg, fc = prob.f_grid(), prob.f_ctrl()
+    rhs, v, out = ctx.interface_solve(phi, fg, fc, K.KFBI_FP64)
+    o_out, o_b, o_v = O.apply_interface(geom, phi=phi, f_ctrl=fc, F_grid=fg, return_all=True)
+    assert rel(rhs.cpu().numpy(), o_b) < 1e-11
+    assert rel(v.cpu().numpy(), o_v) < 1e-11
+    assert rel(out.cpu().numpy(), o_out) < 1e-11
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_double_layer_apply_parity(case):
+    prob = CASES[case]()
+    ctx, geom = make(prob)
+    phi = W.random_density(prob.iface.M, seed=5)
+    ref = O.apply_double_layer(geom, phi)
+    g64 = ctx.apply_layer_potential(phi, K.KFBI_DOUBLE_LAYER, K.KFBI_FP64).cpu().numpy()
+    g32 = ctx.apply_layer_potential(phi, K.KFBI_DOUBLE_LAYER, K.KFBI_MIXED_FP32).cpu().numpy()
+    assert rel(g64, ref) < 1e-11
+    assert rel(g32, ref) < 2e-5
+    # repeated applies are bit-identical
+    again = ctx.apply_layer_potential(phi, K.KFBI_DOUBLE_LAYER, K.KFBI_FP64).cpu().numpy()
+    assert np.array_equal(again, g64)
+    ctx.close()
+
+
+def test_single_layer_and_volume_parity():
+    prob = W.config_helmholtz(128, 1.0, "ellipse")
+    ctx, geom = make(prob)
+    psi = W.random_density(prob.iface.M, seed=9)
+    ref = O.apply_interface(geom, psi=psi)
+    got = ctx.apply_layer_potential(psi, K.KFBI_SINGLE_LAYER, K.KFBI_FP64).cpu().numpy()
+    assert rel(got, ref) < 1e-11
+    fg, fc = prob.f_grid(), prob.f_ctrl()
+    assert rel(ctx.apply_volume(fg, fc).cpu().numpy(), O.apply_volume(geom, fg, fc)) < 1e-11
+    ctx.close()
+
+
+def test_constant_density_indicator_kappa0():
+    prob = W.config_poisson_flower(256, 512)
+    ctx, geom = make(prob)
+    out = ctx.apply_layer_potential(np.ones(512)).cpu().numpy()
+    assert np.max(np.abs(out - 1.0)) < 1e-12
+    _, v, _ = ctx.interface_solve(np.ones(512))
+    assert np.max(np.abs(v.cpu().numpy() - geom.inside)) < 1e-12
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", ["flower128_poisson", "ellipse256_k10"])
+def test_solve_bvp_fp64_matches_oracle(case):
+    prob = CASES[case]()
+    ctx, geom = make(prob, tol=1e-13, gmres_m=50)
+    u, phi, info = ctx.solve_bvp(prob.f_grid(), prob.f_ctrl(), prob.g_ctrl())
+    u_o, phi_o, info_o = O.solve_bvp(geom, prob.f_grid(), prob.f_ctrl(), prob.g_ctrl(), tol=1e-13)
+    assert info["converged"] and info["rel_residual"] <= 1e-13
+    assert rel(phi.cpu().numpy(), phi_o) < 1e-11
+    assert rel(u.cpu().numpy(), u_o) < 1e-11
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", ["flower128_poisson", "ellipse256_k10", "star192_batchlike"])
+def test_solve_bvp_mixed_precision(case):
+    prob = CASES[case]()
+    ctx, geom = make(prob, precision=K.KFBI_MIXED_FP32, tol=1e-10, inner_tol=1e-5)
+    u, phi, info = ctx.solve_bvp(prob.f_grid(), prob.f_ctrl(), prob.g_ctrl())
+    u_o, phi_o, _ = O.solve_bvp(geom, prob.f_grid(), prob.f_ctrl(), prob.g_ctrl(), tol=1e-12)
+    assert info["converged"], info
+    assert info["applies_low"] > 0
+    assert rel(phi.cpu().numpy(), phi_o) < 1e-6
+    u_exact = prob.u_grid()
+    disc = np.max(np.abs(u_o - u_exact)[geom.inside])
+    assert np.max(np.abs(u.cpu().numpy() - u_o)[geom.inside]) < disc
+    ctx.close()
+
+
+def test_geometry_error_is_reported():
+    prob = W.Problem(W.circle(64, 0.97, (0.0, 0.0)), 32, 0.0, W.manufactured_sinpi())
+    with pytest.raises(K.KfbiError) as e:
+        K.Kfbi2D(prob.iface.pts, prob.iface.normals, prob.iface.curv, 32, 0.0)
+    assert e.value.status == 2
+    under = W.flower(128, r0=0.5, a=0.3, k=20)      # petals thinner than a cell at N = 32
+    with pytest.raises(O.GeometryError):
+        O.Geometry2D(under.pts, under.normals, under.curv, 32, 0.0)
+    with pytest.raises(K.KfbiError) as e:
+        K.Kfbi2D(under.pts, under.normals, under.curv, 32, 0.0)
+    assert e.value.status == 2
+
+
+def test_zero_density_gives_zero():
+    prob = W.config_poisson_flower(64, 128)
+    ctx, _ = make(prob)
+    out = ctx.apply_layer_potential(np.zeros(128)).cpu().numpy()
+    assert np.all(out == 0.0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("N", [2048, 4096])
+def test_full_size_apply_parity(N):
+    """The benchmark's sizes (2-D Helmholtz, flower, kappa = 10, M = 2N): every control
+    point of one FP64 and one FP32 apply against the oracle."""
+    prob = W.config_helmholtz(N, 10.0, "flower")
+    ctx, geom = make(prob)
+    phi = W.random_density(prob.iface.M, seed=21)
+    ref = O.apply_double_layer(geom, phi)
+    assert rel(ctx.apply_layer_potential(phi, 0, K.KFBI_FP64).cpu().numpy(), ref) < 1e-11
+    assert rel(ctx.apply_layer_potential(phi, 0, K.KFBI_MIXED_FP32).cpu().numpy(), ref) < 1e-4
+    ctx.close()
