@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark of the KFBI Dirichlet BVP solve on one GB300 (or N independent replicas).
+
+Metric: KFBI full-solve ms & grid-pts/s per potential apply, mixed precision vs FP64 at
+the same error.  One step = one full BVP solve of the 2-D modified Helmholtz problem
+(flower r = 0.5 + 0.15 cos 5t, N = 4096 cells per side, M = 8192 control points,
+kappa = 1, manufactured u = exp(x) sin(2y), GMRES(50) to 1e-10): volume term, GMRES with
+the layer-potential apply as its operator, final grid solution.  The geometry setup is
+timed separately (setup_ms).
+
+value = (N+1)^2 * (layer-potential applies per solve) / (solve time), summed over ranks
+(grid points per second per apply); ms_per_step is the full-solve time.
+
+--impl reference times the FP64 CPU oracle on the host cores on the same workload: each
+step is one oracle layer-potential apply (the oracle's full solve at N = 4096 would take
+minutes), reported in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "KFBI full-solve ms & grid-pts/s per potential apply: mixed vs FP64, same error"
+UNIT = "grid-pts/s"
+FALLBACK_HBM_GBS = 6800.0
+NOMINAL_FP64_GFLOPS = 1250.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kfbi", choices=["kfbi", "reference"])
+    ap.add_argument("--N", type=int, default=4096)
+    ap.add_argument("--kappa", type=float, default=1.0)
+    ap.add_argument("--shape", default="flower", choices=["flower", "ellipse"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return (f"2-D modified Helmholtz Dirichlet BVP (Lap u - kappa^2 u = f), {a.shape} interface, "
+            f"N={a.N} ({a.N + 1}^2 nodes), M={2 * a.N}, kappa={a.kappa:g}, u=exp(x)sin(2y), "
+            f"double-layer BIE by GMRES(50) to 1e-10")
+
+
+# ------------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    h.update(open(os.path.join(ROOT, "paper_2404_15249_gb300", "csrc", "dst.cu"), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def traffic_for(kernel, N):
+    """DRAM bytes per launch from the committed ncu summary, if taken on this source."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    src = kernel_source_hash()
+    for line in open(p):
+        f = line.split()
+        if len(f) >= 5 and not line.startswith("#") and f[0] == kernel and f[1] == src:
+            n_cap, bytes_cap = int(f[2]), float(f[3])
+            return bytes_cap * (N * N) / (n_cap * n_cap)      # scale by grid units
+    return None
+
+
+STAGE_KERNEL = {"dst_rows_f32": ("dst_rows_kernel<float>", 4), "dst_cols_f32": ("dst_cols_solve_kernel<float>", 4),
+                "dst_rows_f64": ("dst_rows_kernel<double>", 8), "dst_cols_f64": ("dst_cols_solve_kernel<double>", 8),
+                "refine": ("refine_kernel", 0)}
+
+
+def roofline(stage_ms, N):
+    """Dominant stage of the timed region -> roofline entry for its kernel."""
+    cand = {k: v for k, v in stage_ms.items() if k in STAGE_KERNEL and v[1] > 0 and v[0] > 0}
+    if not cand:
+        return None
+    name = max(cand, key=lambda k: cand[k][0])
+    ms, launches = cand[name]
+    avg_s = ms / launches / 1e3
+    kernel, esize = STAGE_KERNEL[name]
+    if name.endswith("f64"):
+        # FP64 transforms are bound by the FP64 ALU: 5 N log2 N flops per complex FFT of
+        # length N per line (rows: 1 FFT per line, columns: 2)
+        ffts = 1 if "rows" in name else 2
+        flops = ffts * N * 5.0 * N * math.log2(N)
+        return {"bound": "alu", "kernel": kernel, "achieved": flops / avg_s / 1e12,
+                "peak": NOMINAL_FP64_GFLOPS / 1e3, "unit": "TFLOP/s",
+                "frac": flops / avg_s / 1e12 / (NOMINAL_FP64_GFLOPS / 1e3),
+                "peak_source": "nominal FP64", "traffic": None, "launches": launches,
+                "avg_launch_us": avg_s * 1e6}
+    peak, src = peaks()
+    nbytes = 2.0 * N * N * esize          # every unknown read once and written once
+    ach = nbytes / avg_s / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "peak_source": src, "traffic": traffic_for(kernel, N),
+            "algorithmic_bytes": nbytes, "launches": launches, "avg_launch_us": avg_s * 1e6}
+
+
+# ------------------------------------------------------------------------ arms
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_applies(prob, budget_s=12.0, max_applies=4):
+    """Time FP64 oracle double-layer applies on the host cores (bounded sample)."""
+    import numpy as np
+    import kfbi_workloads as W
+    import oracle as O
+    g = O.Geometry2D(prob.iface.pts, prob.iface.normals, prob.iface.curv, prob.N, prob.kappa)
+    phi = W.random_density(prob.iface.M, seed=5)
+    n, t0 = 0, time.perf_counter()
+    while n < max_applies and (n == 0 or time.perf_counter() - t0 < budget_s):
+        O.apply_double_layer(g, phi)
+        n += 1
+    dt = time.perf_counter() - t0
+    return n, dt
+
+
+def run_reference(a):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    import kfbi_workloads as W
+    import oracle as O
+    prob = W.config_helmholtz(a.N, a.kappa, a.shape)
+    g = O.Geometry2D(prob.iface.pts, prob.iface.normals, prob.iface.curv, prob.N, prob.kappa)
+    phi = W.random_density(prob.iface.M, seed=5)
+    for _ in range(a.warmup):
+        O.apply_double_layer(g, phi)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        O.apply_double_layer(g, phi)
+    dt = (time.perf_counter() - t0) / a.steps
+    value = (a.N + 1) ** 2 / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(a), "N": a.N, "M": 2 * a.N, "kappa": a.kappa,
+                       "step": "one FP64 oracle double-layer apply (numpy, host cores)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{a.steps} timed oracle applies at N={a.N}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_kfbi(a):
+    import numpy as np
+    import torch
+    import kfbi_workloads as W
+    import paper_2404_15249_gb300 as K
+
+    rank, world, local = dist_info()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (the CUDA library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    N, M = a.N, 2 * a.N
+    prob = W.config_helmholtz(N, a.kappa, a.shape)
+    fg = torch.as_tensor(prob.f_grid(), device=dev)
+    fc = torch.as_tensor(prob.f_ctrl(), device=dev)
+    gc = torch.as_tensor(prob.g_ctrl(), device=dev)
+    u = torch.empty((N + 1, N + 1), dtype=torch.float64, device=dev)
+    phi = torch.empty(M, dtype=torch.float64, device=dev)
+    u_exact = prob.u_grid()
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = K.Kfbi2D(prob.iface.pts, prob.iface.normals, prob.iface.curv, N, a.kappa,
+                   precision=K.KFBI_MIXED_FP32, gmres_m=50, max_restarts=20, tol=1e-10)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    inside = ctx.inside_mask().cpu().numpy().astype(bool)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    def err_inf(ut):
+        return float(np.max(np.abs(ut.cpu().numpy() - u_exact)[inside]))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- mixed-precision solve (the timed path)
+    for _ in range(a.warmup):
+        ctx.solve_bvp(fg, fc, gc, u_out=u, dens_out=phi)
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    ctx.profile(True)
+    st = torch.cuda.current_stream()
+    step_ms, infos = [], []
+    for _ in range(a.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _, _, info = ctx.solve_bvp(fg, fc, gc, u_out=u, dens_out=phi)
+        e1.record(st)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        infos.append(info)
+    stages = ctx.profile_read()
+    ctx.profile(False)
+    barrier()
+    clk = clocks.stop()
+    ms = statistics.mean(step_ms)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    applies = infos[-1]["applies_fp64"] + infos[-1]["applies_low"]
+    err_mixed = err_inf(u)
+    value = world * (N + 1) ** 2 * applies / (ms / 1e3)
+
+    # ---------------- FP64 path on the same inputs (same error check, speedup)
+    fp64 = {}
+    if not a.no_fp64:
+        ctx.set_solver(K.KFBI_FP64, 50, 20, 1e-10, 1e-6)
+        ctx.solve_bvp(fg, fc, gc, u_out=u, dens_out=phi)
+        t64 = []
+        for _ in range(2):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _, _, i64 = ctx.solve_bvp(fg, fc, gc, u_out=u, dens_out=phi)
+            e1.record(st)
+            e1.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        fp64 = {"fp64_solve_ms": statistics.mean(t64), "err_inf_fp64": err_inf(u),
+                "fp64_iterations": i64["iterations"],
+                "speedup_vs_fp64": statistics.mean(t64) / ms}
+        ctx.set_solver(K.KFBI_MIXED_FP32, 50, 20, 1e-10, 1e-6)
+
+    # ---------------- end to end through the API with host buffers
+    e2e = None
+    if not a.no_e2e:
+        h_fg = torch.as_tensor(prob.f_grid()).pin_memory()
+        h_fc = torch.as_tensor(prob.f_ctrl()).pin_memory()
+        h_gc = torch.as_tensor(prob.g_ctrl()).pin_memory()
+        h_u = torch.empty((N + 1, N + 1), dtype=torch.float64).pin_memory()
+        h_phi = torch.empty(M, dtype=torch.float64).pin_memory()
+        d_fg, d_fc, d_gc = torch.empty_like(fg), torch.empty_like(fc), torch.empty_like(gc)
+        e2e_ms = []
+        barrier()
+        for _ in range(a.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            d_fg.copy_(h_fg, non_blocking=True)
+            d_fc.copy_(h_fc, non_blocking=True)
+            d_gc.copy_(h_gc, non_blocking=True)
+            ctx.solve_bvp(d_fg, d_fc, d_gc, u_out=u, dens_out=phi)
+            h_u.copy_(u, non_blocking=True)
+            h_phi.copy_(phi, non_blocking=True)
+            e1.record(st)
+            e1.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+        em = statistics.mean(e2e_ms)
+        if dist is not None:
+            t = torch.tensor([em], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            em = float(t.item())
+        e2e = {"value": world * (N + 1) ** 2 * applies / (em / 1e3), "unit": UNIT,
+               "ms_per_step": em,
+               "h2d_bytes_per_step": (h_fg.numel() + h_fc.numel() + h_gc.numel()) * 8,
+               "d2h_bytes_per_step": (h_u.numel() + h_phi.numel()) * 8}
+
+    # ---------------- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        n, dt = cpu_oracle_applies(prob)
+        cpu = {"value": (N + 1) ** 2 * n / dt, "unit": UNIT, "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"{n} FP64 oracle double-layer applies of this N={N} problem "
+                         f"({dt:.1f} s, numpy on the host cores); unit as value"}
+
+    launches = int(sum(v[1] for v in stages.values()))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "N": N, "M": M, "kappa": a.kappa,
+                       "precision": "FP32 box solves, FP64 geometry/Krylov/refinement",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "replicas": world},
+            "roofline": roofline(stages, N),
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "setup_ms": setup_ms,
+            "applies_per_solve": applies,
+            "iterations": infos[-1]["iterations"],
+            "outer_iterations": infos[-1]["outer_iterations"],
+            "rel_residual": infos[-1]["rel_residual"],
+            "err_inf_mixed": err_mixed,
+            "stage_ms": {k: round(v[0] / a.steps, 4) for k, v in stages.items() if v[1]},
+            "stage_launches": {k: int(v[1]) for k, v in stages.items() if v[1]},
+            **fp64}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.warmup < 3:
+        a.warmup = 3
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_kfbi(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

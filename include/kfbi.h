@@ -67,7 +67,7 @@ typedef enum {
 
 typedef struct {
   int dim;              /* 2                                                            */
-  int N;                /* cells per side, N = 2^a or 3*2^a, 32 <= N <= 16384            */
+  int N;                /* cells per side, N = 2^a or 3*2^a, 32 <= N <= 8192            */
   double lo, hi;        /* box [lo, hi]^dim                                             */
   double kappa;         /* >= 0; PDE Lap u - kappa^2 u = f                               */
   int precision;        /* kfbi_precision used by kfbi_solve_bvp                         */
@@ -112,7 +112,7 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
                        kfbi_ctx* out);
 
 /* One layer-potential apply (the hot path, Alg. 1 steps 4-6): jumps from the density
-   (Alg. 2 line 4), RHS correction at irregular nodes, sine-transform box solve (Alg. 4)
+   (Alg. 2), RHS correction at irregular nodes, sine-transform box solve (Alg. 4)
    in the given precision, corrected interpolation to the control points (Alg. 3).
    For KFBI_DOUBLE_LAYER the result is K_D density = (1/2 I + W) density (Sec. 3.3).
    d_density, d_out: M values.  Asynchronous. */
@@ -159,6 +159,25 @@ kfbi_status kfbi_get_info(kfbi_ctx ctx, kfbi_ctx_info* h_info);
 /* Sets the precision / restart / tolerance fields used by later kfbi_solve_bvp calls. */
 kfbi_status kfbi_set_solver(kfbi_ctx ctx, int precision, int gmres_m, int max_restarts,
                             double tol, double inner_tol);
+
+/* ---------------------------------------------------------------- stage timers
+   Per-stage device time (CUDA events recorded on the context's stream around each
+   launch of the apply pipeline) and launch counts of every kernel the library issues.
+   Stages: 0 setup, 1 correction gather, 2 DST rows FP32, 3 DST columns FP32, 4 DST rows
+   FP64, 5 DST columns FP64, 6 interpolation, 7 dense grid build/copy, 8 Krylov vector
+   kernels, 9 FP64 residual refinement of FP32 box solves.  Launch counts are always
+   kept; times only while profiling is on (enabling clears both). */
+#define KFBI_NSTAGES 16
+typedef struct {
+  double ms[KFBI_NSTAGES];          /* summed device time per stage (0 when not timed) */
+  long long launches[KFBI_NSTAGES]; /* kernel launches per stage                      */
+  int nstages;                      /* stages in use                                   */
+} kfbi_stage_times;
+
+kfbi_status kfbi_profile(kfbi_ctx ctx, int enable);
+/* Synchronises the context's stream and returns the totals since the last enable. */
+kfbi_status kfbi_profile_read(kfbi_ctx ctx, kfbi_stage_times* h_out);
+const char* kfbi_stage_name(int stage);
 
 /* Releases all device memory of the context.  Synchronises its stream first. */
 kfbi_status kfbi_destroy(kfbi_ctx ctx);

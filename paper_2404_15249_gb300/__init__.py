@@ -58,6 +58,14 @@ class CtxInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+NSTAGES = 16
+
+
+class StageTimes(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * NSTAGES), ("launches", ctypes.c_longlong * NSTAGES),
+                ("nstages", ctypes.c_int)]
+
+
 _LIB = None
 P = ctypes.c_void_p
 I = ctypes.c_int
@@ -80,6 +88,9 @@ _SIGS = {
     "kfbi_batch_solve": (I, [P, I, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                              ctypes.POINTER(P), ctypes.POINTER(SolveInfo), P]),
     "kfbi_batch_destroy": (I, [P]),
+    "kfbi_profile": (I, [P, I]),
+    "kfbi_profile_read": (I, [P, ctypes.POINTER(StageTimes)]),
+    "kfbi_stage_name": (ctypes.c_char_p, [I]),
 }
 
 
@@ -221,6 +232,16 @@ class Kfbi2D:
         i = CtxInfo()
         _check(lib().kfbi_get_info(self.handle, ctypes.byref(i)), "kfbi_get_info")
         return i.as_dict()
+
+    def profile(self, enable=True):
+        """Start (clearing the totals) or stop per-stage event timing."""
+        _check(lib().kfbi_profile(self.handle, 1 if enable else 0), "kfbi_profile")
+
+    def profile_read(self):
+        """{stage name: (ms, launches)} since the last profile(True)."""
+        t = StageTimes()
+        _check(lib().kfbi_profile_read(self.handle, ctypes.byref(t)), "kfbi_profile_read")
+        return {lib().kfbi_stage_name(i).decode(): (t.ms[i], t.launches[i]) for i in range(t.nstages)}
 
     def close(self):
         if getattr(self, "handle", None):

@@ -114,9 +114,11 @@ template <typename T>
 static kfbi_status correct(Ctx& c, const double* dens, const double* psi, const double* fctl,
                            T* B, int add) {
   if (c.nirr == 0) return KFBI_OK;
+  const int pr = prof_begin(c, ST_CORR);
   correction_kernel<T><<<(c.nirr + 127) / 128, 128, 0, c.stream>>>(
       c.nirr, c.M, c.irr_node, c.arm_ptr, c.arm_seg, c.arm_wD, c.arm_wS, c.arm_wF, dens, psi,
       fctl, B, add);
+  prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
 }
@@ -124,9 +126,11 @@ static kfbi_status correct(Ctx& c, const double* dens, const double* psi, const 
 template <typename T>
 static kfbi_status interp(Ctx& c, const T* V, const double* dens, const double* psi,
                           const double* fctl, double* out) {
+  const int pr = prof_begin(c, ST_INTERP);
   interp_kernel<T><<<(c.M + 127) / 128, 128, 0, c.stream>>>(c.M, c.ctrl_node, c.ctrl_w,
                                                             c.ctrl_cD, c.ctrl_cS, c.ctrl_eF, V,
                                                             dens, psi, fctl, out);
+  prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
 }
@@ -153,16 +157,19 @@ template <typename T>
 static kfbi_status interface_solve_t(Ctx& c, int precision, T* W, const double* dens,
                                      const double* f_grid, const double* f_ctrl,
                                      double* rhs_grid, double* v_grid, double* out) {
+  prof_count(c, ST_GRID);
   rhs_dense_kernel<T><<<gs_blocks((long)c.N * c.N), 256, 0, c.stream>>>(c.N, f_grid, c.inside, W);
   KFBI_CUDA_TRY(cudaGetLastError());
   KFBI_TRY(correct<T>(c, dens, nullptr, f_ctrl, W, 1));
   if (rhs_grid) {
+    prof_count(c, ST_GRID);
     work_to_grid_kernel<T><<<gs_blocks((long)(c.N + 1) * (c.N + 1)), 256, 0, c.stream>>>(
         c.N, W, nullptr, rhs_grid);
     KFBI_CUDA_TRY(cudaGetLastError());
   }
   KFBI_TRY(box(c, precision, W, W));
   if (v_grid) {
+    prof_count(c, ST_GRID);
     work_to_grid_kernel<T><<<gs_blocks((long)(c.N + 1) * (c.N + 1)), 256, 0, c.stream>>>(
         c.N, W, nullptr, v_grid);
     KFBI_CUDA_TRY(cudaGetLastError());
@@ -185,11 +192,13 @@ kfbi_status interface_solve(Ctx& c, int precision, const double* dens, const dou
 kfbi_status combined_u(Ctx& c, const double* dens, const double* f_grid, const double* f_ctrl,
                        double* u_grid) {
   double* W = c.V64;
+  prof_count(c, ST_GRID);
   rhs_dense_kernel<double><<<gs_blocks((long)c.N * c.N), 256, 0, c.stream>>>(c.N, f_grid,
                                                                              c.inside, W);
   KFBI_CUDA_TRY(cudaGetLastError());
   KFBI_TRY(correct<double>(c, dens, nullptr, f_ctrl, W, 1));
   KFBI_TRY(box_solve_f64(c, W, W));
+  prof_count(c, ST_GRID);
   work_to_grid_kernel<double><<<gs_blocks((long)(c.N + 1) * (c.N + 1)), 256, 0, c.stream>>>(
       c.N, W, c.inside, u_grid);
   KFBI_CUDA_TRY(cudaGetLastError());
@@ -198,9 +207,11 @@ kfbi_status combined_u(Ctx& c, const double* dens, const double* f_grid, const d
 
 template <typename T>
 static kfbi_status box_grid_t(Ctx& c, int precision, T* W, const double* b_grid, double* v_grid) {
+  prof_count(c, ST_GRID);
   grid_to_work_kernel<T><<<gs_blocks((long)c.N * c.N), 256, 0, c.stream>>>(c.N, b_grid, W);
   KFBI_CUDA_TRY(cudaGetLastError());
   KFBI_TRY(box(c, precision, W, W));
+  prof_count(c, ST_GRID);
   work_to_grid_kernel<T><<<gs_blocks((long)(c.N + 1) * (c.N + 1)), 256, 0, c.stream>>>(
       c.N, W, nullptr, v_grid);
   KFBI_CUDA_TRY(cudaGetLastError());
@@ -220,6 +231,7 @@ __global__ void copy_mask_kernel(long n, const uint8_t* in, uint8_t* out) {
 
 kfbi_status inside_mask(Ctx& c, uint8_t* mask) {
   const long n = (long)(c.N + 1) * (c.N + 1);
+  prof_count(c, ST_GRID);
   copy_mask_kernel<<<gs_blocks(n), 256, 0, c.stream>>>(n, c.inside, mask);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;

@@ -319,3 +319,84 @@ kfbi_status kfbi_batch_destroy(kfbi_batch b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- stage timers
+namespace kfbi {
+
+static const int kProfPairs = 4096;
+
+void prof_flush(Ctx& c) {
+  Prof& p = c.prof;
+  if (p.used == 0) return;
+  cudaStreamSynchronize(c.stream);
+  for (int i = 0; i < p.used; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]) == cudaSuccess)
+      p.ms[p.stage[i]] += ms;
+  }
+  p.used = 0;
+}
+
+int prof_begin(Ctx& c, int stage) {
+  Prof& p = c.prof;
+  ++p.launches[stage];
+  if (!p.on) return -1;
+  if (p.used == kProfPairs) prof_flush(c);
+  const int i = p.used++;
+  p.stage[i] = stage;
+  cudaEventRecord(p.ev[2 * i], c.stream);
+  return i;
+}
+
+void prof_end(Ctx& c, int pair) {
+  if (pair >= 0) cudaEventRecord(c.prof.ev[2 * pair + 1], c.stream);
+}
+
+}  // namespace kfbi
+
+extern "C" {
+
+kfbi_status kfbi_profile(kfbi_ctx ctx, int enable) {
+  if (!ctx) return KFBI_ERR_ARG;
+  kfbi::Ctx& c = ctx->c;
+  kfbi::Prof& p = c.prof;
+  if (enable) {
+    if (p.ev.empty()) {
+      p.ev.resize(2 * kfbi::kProfPairs);
+      p.stage.resize(kfbi::kProfPairs);
+      for (auto& e : p.ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+          kfbi::set_error("kfbi_profile: cudaEventCreate failed");
+          return KFBI_ERR_CUDA;
+        }
+    }
+    p.used = 0;
+    for (int s = 0; s < KFBI_NSTAGES; ++s) { p.ms[s] = 0.0; p.launches[s] = 0; }
+    p.on = true;
+  } else {
+    kfbi::prof_flush(c);
+    p.on = false;
+  }
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_profile_read(kfbi_ctx ctx, kfbi_stage_times* out) {
+  if (!ctx || !out) return KFBI_ERR_ARG;
+  kfbi::Ctx& c = ctx->c;
+  kfbi::prof_flush(c);
+  for (int s = 0; s < KFBI_NSTAGES; ++s) {
+    out->ms[s] = c.prof.ms[s];
+    out->launches[s] = c.prof.launches[s];
+  }
+  out->nstages = kfbi::ST_COUNT;
+  return KFBI_OK;
+}
+
+const char* kfbi_stage_name(int s) {
+  static const char* names[] = {"setup", "correction", "dst_rows_f32", "dst_cols_f32",
+                                "dst_rows_f64", "dst_cols_f64", "interpolation", "grid",
+                                "krylov", "refine"};
+  return (s >= 0 && s < kfbi::ST_COUNT) ? names[s] : "unused";
+}
+
+}  // extern "C"

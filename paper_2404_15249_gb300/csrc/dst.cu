@@ -347,6 +347,7 @@ kfbi_status init_box_tables(Ctx& c) {
   KFBI_TRY(alloc_bytes(c, (void**)&c.t32.tw, sizeof(float2) * 2 * N));
   KFBI_TRY(alloc_bytes(c, (void**)&c.t64.lam, sizeof(double) * N));
   KFBI_TRY(alloc_bytes(c, (void**)&c.t32.lam, sizeof(float) * N));
+  prof_count(c, ST_SETUP);
   box_tables_kernel<<<(2 * N + 255) / 256, 256, 0, c.stream>>>(N, c.h, c.t64.tw, c.t32.tw,
                                                                 c.t64.lam, c.t32.lam);
   KFBI_CUDA_TRY(cudaGetLastError());
@@ -383,7 +384,9 @@ static kfbi_status launch_rows(Ctx& c, const T* in, T* out, const cx<T>* tw, T s
   if (per_sm < 1) per_sm = 1;
   int blocks = (p.N + lpc - 1) / lpc;
   blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
+  const int pr = prof_begin(c, sizeof(T) == 4 ? ST_ROWS32 : ST_ROWS64);
   dst_rows_kernel<T, EPT><<<blocks, threads, smem, c.stream>>>(in, out, p, tw, scale);
+  prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
 }
@@ -410,8 +413,10 @@ static kfbi_status launch_cols(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   int blocks = (p.N + L - 1) / L;
   blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
   const T scale = T((2.0 / p.N) * (2.0 / p.N));
+  const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
   dst_cols_solve_kernel<T, EPT, MAXT><<<blocks, threads, smem, c.stream>>>(V, p, L, tw, lam,
-                                                                     T(c.kappa2), scale);
+                                                                           T(c.kappa2), scale);
+  prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
 }

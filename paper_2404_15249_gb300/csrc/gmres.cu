@@ -191,22 +191,30 @@ static kfbi_status gmres_run(Ctx& c, int precision, const double* rhs, double* x
     KFBI_CUDA_TRY(cudaMemcpyAsync(r, rhs, sizeof(double) * M, cudaMemcpyDeviceToDevice, st));
   } else {
     KFBI_TRY(apply_K(c, precision, x, tmp, cnt));
+    prof_count(c, ST_KRYLOV);
     sub_kernel<<<vb(M), 256, 0, st>>>(r, rhs, tmp, M);
   }
+  prof_count(c, ST_KRYLOV);
   norm_kernel<<<1, 1024, 0, st>>>(r, M, c.scal, 2);
   KFBI_TRY(read_scal(c, 4));
   double beta = c.h_pinned[2];
   if (!std::isfinite(beta)) return KFBI_ERR_NUMERIC;
   for (int cyc = 0; cyc < max_cycles && beta > tol_abs; ++cyc) {
+    prof_count(c, ST_KRYLOV);
     cycle_start_kernel<<<vb(M > m + 1 ? M : m + 1), 256, 0, st>>>(c.basis, r, M, c.gvec, m, c.scal);
     int k = 0;
     for (int j = 0; j < m; ++j) {
       KFBI_TRY(apply_K(c, precision, c.basis + (size_t)j * M, w, cnt));
       ++cnt.iters;
+      prof_count(c, ST_KRYLOV);
       multidot_kernel<<<j + 1, RED_T, 0, st>>>(c.basis, M, M, w, h1);
+      prof_count(c, ST_KRYLOV);
       mv_update_kernel<<<vb(M), 256, 0, st>>>(w, c.basis, M, M, h1, j + 1, -1.0);
+      prof_count(c, ST_KRYLOV);
       multidot_kernel<<<j + 1, RED_T, 0, st>>>(c.basis, M, M, w, h2);
+      prof_count(c, ST_KRYLOV);
       mv_update_kernel<<<vb(M), 256, 0, st>>>(w, c.basis, M, M, h2, j + 1, -1.0);
+      prof_count(c, ST_KRYLOV);
       finish_kernel<<<1, 1024, 0, st>>>(j, m, M, w, c.basis, M, h1, h2, c.hess, c.givens,
                                         c.gvec, c.scal);
       KFBI_CUDA_TRY(cudaGetLastError());
@@ -215,7 +223,9 @@ static kfbi_status gmres_run(Ctx& c, int precision, const double* rhs, double* x
       if (c.h_pinned[3] != 0.0) return KFBI_ERR_NUMERIC;
       if (c.h_pinned[0] <= tol_abs || c.h_pinned[1] != 0.0) break;
     }
+    prof_count(c, ST_KRYLOV);
     lsq_kernel<<<1, 32, 0, st>>>(k, m, c.hess, c.gvec, c.yvec);
+    prof_count(c, ST_KRYLOV);
     mv_update_kernel<<<vb(M), 256, 0, st>>>(x, c.basis, M, M, c.yvec, k, 1.0);
     KFBI_CUDA_TRY(cudaGetLastError());
     const bool last = cyc + 1 == max_cycles;
@@ -224,7 +234,9 @@ static kfbi_status gmres_run(Ctx& c, int precision, const double* rhs, double* x
       break;
     }
     KFBI_TRY(apply_K(c, precision, x, tmp, cnt));
+    prof_count(c, ST_KRYLOV);
     sub_kernel<<<vb(M), 256, 0, st>>>(r, rhs, tmp, M);
+    prof_count(c, ST_KRYLOV);
     norm_kernel<<<1, 1024, 0, st>>>(r, M, c.scal, 2);
     KFBI_TRY(read_scal(c, 4));
     beta = c.h_pinned[2];
@@ -246,7 +258,9 @@ kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const 
   // g_hat = g - (Y f)^+   (FP64 volume solve)
   KFBI_TRY(interface_solve(c, KFBI_FP64, nullptr, f_grid, f_ctrl, nullptr, nullptr, d));
   ++cnt.applies64;
+  prof_count(c, ST_KRYLOV);
   sub_kernel<<<vb(M), 256, 0, st>>>(ghat, g_ctrl, d, M);
+  prof_count(c, ST_KRYLOV);
   norm_kernel<<<1, 1024, 0, st>>>(ghat, M, c.scal, 4);
   KFBI_TRY(read_scal(c, 5));
   const double gnorm = c.h_pinned[4];
@@ -266,7 +280,9 @@ kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const 
       double* rr = ghat;
       if (outer > 0) {
         KFBI_TRY(apply_K(c, KFBI_FP64, phi, d, cnt));
+        prof_count(c, ST_KRYLOV);
         sub_kernel<<<vb(M), 256, 0, st>>>(r, ghat, d, M);
+        prof_count(c, ST_KRYLOV);
         norm_kernel<<<1, 1024, 0, st>>>(r, M, c.scal, 5);
         KFBI_TRY(read_scal(c, 6));
         res = c.h_pinned[5];
@@ -280,13 +296,16 @@ kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const 
       double inner_res = 0.0;
       KFBI_TRY(gmres_run(c, KFBI_MIXED_FP32, rr, corr, true, c.opt.inner_tol * res, 3, false,
                          cnt, &inner_res));
+      prof_count(c, ST_KRYLOV);
       axpy_kernel<<<vb(M), 256, 0, st>>>(phi, corr, 1.0, M);     // phi += d
       KFBI_CUDA_TRY(cudaGetLastError());
     }
     if (res > tol_abs) {
       // final true residual after the last correction
       KFBI_TRY(apply_K(c, KFBI_FP64, phi, d, cnt));
+      prof_count(c, ST_KRYLOV);
       sub_kernel<<<vb(M), 256, 0, st>>>(r, ghat, d, M);
+      prof_count(c, ST_KRYLOV);
       norm_kernel<<<1, 1024, 0, st>>>(r, M, c.scal, 5);
       KFBI_TRY(read_scal(c, 6));
       res = c.h_pinned[5];

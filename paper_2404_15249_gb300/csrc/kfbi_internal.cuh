@@ -57,6 +57,21 @@ struct BoxTables {
   T* lam;        // lambda_k = -(4/h^2) sin^2(pi k / 2N), k < N (lam[0] unused)
 };
 
+// ------------------------------------------------------------------ stage timers
+enum Stage : int {
+  ST_SETUP = 0, ST_CORR = 1, ST_ROWS32 = 2, ST_COLS32 = 3, ST_ROWS64 = 4, ST_COLS64 = 5,
+  ST_INTERP = 6, ST_GRID = 7, ST_KRYLOV = 8, ST_REFINE = 9, ST_COUNT = 10
+};
+
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;     // 2 per timed launch
+  std::vector<int> stage;          // stage of each event pair
+  int used = 0;
+  double ms[KFBI_NSTAGES] = {};
+  long long launches[KFBI_NSTAGES] = {};
+};
+
 // ------------------------------------------------------------------ context
 struct Ctx {
   // problem
@@ -120,7 +135,15 @@ struct Ctx {
   int64_t bytes = 0;
   int n_inside = 0;
   std::vector<void*> allocs;                  // device allocations owned by the context
+  Prof prof;
 };
+
+// Launch bookkeeping: every kernel launch site calls prof_begin before and prof_end
+// after the launch; the pair is timed with events only while profiling is on.
+inline void prof_count(Ctx& c, int stage, int n = 1) { c.prof.launches[stage] += n; }
+int prof_begin(Ctx& c, int stage);
+void prof_end(Ctx& c, int pair);
+void prof_flush(Ctx& c);
 
 // ------------------------------------------------------------------ stages
 kfbi_status setup_geometry(Ctx& c);                 // setup2d.cu

@@ -511,9 +511,12 @@ kfbi_status setup_geometry(Ctx& c) {
   KFBI_TRY(alloc_bytes(c, (void**)&tmp_i, sizeof(int) * (2 * nsub + 2)));
   int* counts = tmp_i;
   int* offs = tmp_i + nsub;
+  prof_count(c, ST_SETUP);
   samples_kernel<<<nblk(M * (SUB + 1), 256), 256, 0, st>>>(c.pts, M, samp);
+  prof_count(c, ST_SETUP);
   crossings_kernel<<<nblk(nsub, 256), 256, 0, st>>>(c.pts, samp, M, N, c.lo, c.h, 0, counts,
                                                      nullptr, nullptr, nullptr, nullptr, nullptr);
+  prof_count(c, ST_SETUP);
   scan_kernel<<<1, 1024, 0, st>>>(counts, offs, nsub);
   KFBI_CUDA_TRY(cudaGetLastError());
   // per-axis totals: the axis-0 sub-intervals come first
@@ -530,6 +533,7 @@ kfbi_status setup_geometry(Ctx& c) {
   KFBI_TRY(alloc_bytes(c, (void**)&seg, sizeof(int) * (total + 1)));
   KFBI_TRY(alloc_bytes(c, (void**)&tau, sizeof(double) * (total + 1)));
   KFBI_TRY(alloc_bytes(c, (void**)&along, sizeof(double) * (total + 1)));
+  prof_count(c, ST_SETUP);
   crossings_kernel<<<nblk(nsub, 256), 256, 0, st>>>(c.pts, samp, M, N, c.lo, c.h, 1, nullptr,
                                                      offs, line, seg, tau, along);
   KFBI_CUDA_TRY(cudaGetLastError());
@@ -552,12 +556,16 @@ kfbi_status setup_geometry(Ctx& c) {
     KFBI_CUDA_TRY(cudaMemsetAsync(lcnt, 0, sizeof(int) * (N + 2), st));
     KFBI_CUDA_TRY(cudaMemsetAsync(fill, 0, sizeof(int) * (N + 2), st));
     if (n > 0) line_count_kernel<<<nblk(n, 256), 256, 0, st>>>(line + base, n, lcnt);
+    prof_count(c, ST_SETUP);
     scan_kernel<<<1, 1024, 0, st>>>(lcnt, c.line_ptr[ax], N + 1);
     if (n > 0) {
+      prof_count(c, ST_SETUP);
       line_scatter_kernel<<<nblk(n, 256), 256, 0, st>>>(line + base, n, c.line_ptr[ax], fill,
                                                         perm);
+      prof_count(c, ST_SETUP);
       line_sort_kernel<<<nblk(N + 1, 128), 128, 0, st>>>(N + 1, c.line_ptr[ax], perm,
                                                          along + base, seg + base, tau + base);
+      prof_count(c, ST_SETUP);
       gather_cross_kernel<<<nblk(n, 256), 256, 0, st>>>(n, perm, line + base, seg + base,
                                                          tau + base, along + base, c.cr_line[ax],
                                                          c.cr_seg[ax], c.cr_tau[ax],
@@ -568,16 +576,20 @@ kfbi_status setup_geometry(Ctx& c) {
 
   // labels from row parity; matching of crossings to label changes on every line
   KFBI_TRY(alloc_bytes(c, (void**)&c.inside, (size_t)(N + 1) * (N + 1)));
+  prof_count(c, ST_SETUP);
   labels_kernel<<<dim3(nblk(N + 1, 256), N + 1), 256, 0, st>>>(N, c.lo, c.h, c.line_ptr[1],
                                                                c.cr_along[1], c.inside,
                                                                c.err_flag);
-  for (int ax = 0; ax < 2; ++ax)
+  for (int ax = 0; ax < 2; ++ax) {
+    prof_count(c, ST_SETUP);
     match_kernel<<<nblk(N + 1, 64), 64, 0, st>>>(N, c.lo, c.h, ax, c.line_ptr[ax],
                                                  c.cr_along[ax], c.inside, c.cr_flip[ax],
                                                  c.err_flag);
+  }
   KFBI_CUDA_TRY(cudaGetLastError());
   int* d_inside_cnt = counts;   // reuse scratch
   KFBI_CUDA_TRY(cudaMemsetAsync(d_inside_cnt, 0, sizeof(int), st));
+  prof_count(c, ST_SETUP);
   count_inside_kernel<<<256, 256, 0, st>>>((N + 1) * (N + 1), c.inside, d_inside_cnt);
   int h_err = 0;
   KFBI_CUDA_TRY(cudaMemcpyAsync(&h_err, c.err_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -600,8 +612,11 @@ kfbi_status setup_geometry(Ctx& c) {
   int* arm_off = nullptr;
   KFBI_TRY(alloc_bytes(c, (void**)&node_off, sizeof(int) * (N + 1)));
   KFBI_TRY(alloc_bytes(c, (void**)&arm_off, sizeof(int) * (N + 1)));
+  prof_count(c, ST_SETUP);
   irr_row_count_kernel<<<N - 1, 256, 0, st>>>(N, c.inside, row_nodes, row_arms);
+  prof_count(c, ST_SETUP);
   scan_kernel<<<1, 1024, 0, st>>>(row_nodes, node_off, N - 1);
+  prof_count(c, ST_SETUP);
   scan_kernel<<<1, 1024, 0, st>>>(row_arms, arm_off, N - 1);
   KFBI_CUDA_TRY(cudaGetLastError());
   int h_n[2];
@@ -620,6 +635,7 @@ kfbi_status setup_geometry(Ctx& c) {
   KFBI_TRY(alloc_bytes(c, (void**)&c.arm_wD, sizeof(double) * 6 * (c.narms + 1)));
   KFBI_TRY(alloc_bytes(c, (void**)&c.arm_wS, sizeof(double) * 6 * (c.narms + 1)));
   KFBI_TRY(alloc_bytes(c, (void**)&c.arm_wF, sizeof(double) * 6 * (c.narms + 1)));
+  prof_count(c, ST_SETUP);
   irr_row_fill_kernel<<<N - 1, 256, 0, st>>>(N, c.inside, node_off, arm_off, c.irr_node,
                                              c.arm_ptr, arm_dir, arm_owner);
   KFBI_CUDA_TRY(cudaMemcpyAsync(c.arm_ptr + c.nirr, &c.narms, sizeof(int), cudaMemcpyHostToDevice, st));
@@ -637,6 +653,7 @@ kfbi_status setup_geometry(Ctx& c) {
   KFBI_TRY(alloc_bytes(c, (void**)&c.ctrl_cD, sizeof(double) * 6 * M));
   KFBI_TRY(alloc_bytes(c, (void**)&c.ctrl_cS, sizeof(double) * 6 * M));
   KFBI_TRY(alloc_bytes(c, (void**)&c.ctrl_eF, sizeof(double) * M));
+  prof_count(c, ST_SETUP);
   ctrl_weights_kernel<<<nblk(M, 128), 128, 0, st>>>(N, M, c.lo, c.h, c.kappa2, c.pts, c.nrm,
                                                     c.curv, c.inside, c.ctrl_node, c.ctrl_w,
                                                     c.ctrl_cD, c.ctrl_cS, c.ctrl_eF, c.err_flag);
