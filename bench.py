@@ -297,7 +297,7 @@ def run_kfbi(a):
     # ---------------- FP64 path on the same inputs (same error check, speedup)
     fp64 = {}
     if not a.no_fp64:
-        ctx.set_solver(K.KFBI_FP64, 50, 20, 1e-10, 1e-6)
+        ctx.set_solver(K.KFBI_FP64, 50, 20, 1e-10, 1e-5)
         ctx.solve_bvp(fg, fc, gc, u_out=u, dens_out=phi)
         t64 = []
         for _ in range(2):
@@ -311,7 +311,7 @@ def run_kfbi(a):
         fp64 = {"fp64_solve_ms": statistics.mean(t64), "err_inf_fp64": err_inf(u),
                 "fp64_iterations": i64["iterations"],
                 "speedup_vs_fp64": statistics.mean(t64) / ms}
-        ctx.set_solver(K.KFBI_MIXED_FP32, 50, 20, 1e-10, 1e-6)
+        ctx.set_solver(K.KFBI_MIXED_FP32, 50, 20, 1e-10, 1e-5)
 
     # ---------------- end to end through the API with host buffers
     e2e = None

@@ -56,8 +56,13 @@ typedef enum {
 
 typedef enum {
   KFBI_FP64 = 0,         /* every stage in FP64                                          */
-  KFBI_MIXED_FP32 = 1    /* box solve in FP32; geometry, jumps, Arnoldi, Givens and the
+  KFBI_MIXED_FP32 = 1,   /* box solve in FP32; geometry, jumps, Arnoldi, Givens and the
                             refinement residual in FP64 (GMRES-IR)                       */
+  KFBI_FP32_REFINED = 2  /* box solve from FP32 sine transforms, corrected twice against
+                            the FP64 residual of the 5-point system: FP64-accurate (about
+                            1e-12 relative) at FP32 transform cost.  Accepted by the apply
+                            and interface-solve entry points; the mixed BVP solver uses it
+                            for every step that needs FP64 accuracy                      */
 } kfbi_precision;
 
 typedef enum {
@@ -70,18 +75,23 @@ typedef struct {
   int N;                /* cells per side, N = 2^a or 3*2^a, 32 <= N <= 8192            */
   double lo, hi;        /* box [lo, hi]^dim                                             */
   double kappa;         /* >= 0; PDE Lap u - kappa^2 u = f                               */
-  int precision;        /* kfbi_precision used by kfbi_solve_bvp                         */
+  int precision;        /* kfbi_precision used by kfbi_solve_bvp: FP64 (plain FP64 GMRES),
+                           MIXED_FP32 (GMRES-IR: FP32 inner GMRES, refined-FP32 outer
+                           residuals) or FP32_REFINED (GMRES on refined applies)        */
   int gmres_m;          /* GMRES restart length (Alg. 5), 1..128                         */
-  int max_restarts;     /* FP64: GMRES restarts; mixed: outer refinement steps           */
+  int max_restarts;     /* GMRES restarts (cycles - 1)                                  */
   double tol;           /* stop when ||g_hat - K_D phi||_2 <= tol ||g_hat||_2            */
-  double inner_tol;     /* mixed: relative tolerance of each inner FP32-apply GMRES      */
+  double inner_tol;     /* mixed: assumed relative accuracy of a plain FP32 apply; once
+                           the residual is below tol / inner_tol the Arnoldi steps use
+                           plain FP32 applies (default 1e-5)                           */
 } kfbi_options;
 
 typedef struct {
   int iterations;        /* Arnoldi steps over all cycles                                 */
-  int outer_iterations;  /* mixed: refinement steps; FP64: restart cycles                 */
-  int applies_fp64;      /* K_D (and Y) applies with an FP64 box solve                   */
-  int applies_low;       /* K_D applies with an FP32 box solve                           */
+  int outer_iterations;  /* GMRES restart cycles (each ends with an FP64-accurate residual) */
+  int applies_fp64;      /* applies with an FP64-accurate box solve (FP64, or FP32
+                            transforms refined against the FP64 residual)               */
+  int applies_low;       /* K_D applies with a plain FP32 box solve (inner GMRES)         */
   double rel_residual;   /* final ||g_hat - K_D phi|| / ||g_hat|| (FP64 apply)           */
   int converged;         /* 1 if rel_residual <= tol                                     */
 } kfbi_solve_info;
@@ -96,7 +106,7 @@ typedef struct {
 } kfbi_ctx_info;
 
 /* Fills *opt with dim 2, N 128, box [-1,1], kappa 0, FP64, m 50, 20 restarts,
-   tol 1e-10, inner_tol 1e-6. */
+   tol 1e-10, inner_tol 1e-5. */
 void kfbi_default_options(kfbi_options* opt);
 
 /* Builds the discrete interface problem on the device (Procedure 1 of Sec. 4.4, Alg. 1
@@ -143,7 +153,12 @@ kfbi_status kfbi_box_solve(kfbi_ctx ctx, int precision, const double* d_b_grid,
 /* Dirichlet BVP (Procedures 2-3 of Sec. 4.4): g_hat = g - (Y f)^+, K_D phi = g_hat by
    GMRES(m) (Alg. 5; FP64 Arnoldi with CGS2 and Givens rotations on the device), then
    u = W phi + Y f on the grid (Sec. 2.1).  opt->precision selects plain FP64 or mixed
-   FP32 box solves with FP64 iterative refinement of the BIE residual.
+   precision: one FP64 Arnoldi process whose matvecs use FP32 transforms refined once
+   against the FP64 residual (about 1e-11) while the residual is large and plain FP32
+   box solves once it is below tol / inner_tol (relaxed inexact Krylov); every restart
+   cycle ends with the true residual from a twice-refined (FP64-accurate) apply, so the
+   GMRES residual is refined in FP64; the volume term and the final grid solution use
+   the twice-refined solve as well.
    d_u_grid: (N+1)^2, written inside Omega, zero outside.  d_density_out: M or NULL.
    h_info: host struct or NULL.  Synchronising (convergence is checked on the host). */
 kfbi_status kfbi_solve_bvp(kfbi_ctx ctx, const double* d_f_grid, const double* d_f_ctrl,

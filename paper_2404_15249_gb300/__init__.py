@@ -21,6 +21,7 @@ KFBI_OK = 0
 KFBI_ERR_NOT_CONVERGED = 5
 KFBI_FP64 = 0
 KFBI_MIXED_FP32 = 1
+KFBI_FP32_REFINED = 2
 KFBI_DOUBLE_LAYER = 0
 KFBI_SINGLE_LAYER = 1
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_GEOMETRY", 3: "ERR_NOMEM", 4: "ERR_CUDA",
@@ -145,7 +146,7 @@ class Kfbi2D:
     device, then kfbi_setup builds the geometry on the GPU."""
 
     def __init__(self, pts, normals, curv, N, kappa=0.0, lo=-1.0, hi=1.0, precision=KFBI_FP64,
-                 gmres_m=50, max_restarts=20, tol=1e-10, inner_tol=1e-6, stream=None):
+                 gmres_m=50, max_restarts=20, tol=1e-10, inner_tol=1e-5, stream=None):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", torch.cuda.current_device())
@@ -207,7 +208,7 @@ class Kfbi2D:
                                     _stream_ptr(self.stream)), "kfbi_box_solve")
         return v
 
-    def set_solver(self, precision=KFBI_FP64, gmres_m=50, max_restarts=20, tol=1e-10, inner_tol=1e-6):
+    def set_solver(self, precision=KFBI_FP64, gmres_m=50, max_restarts=20, tol=1e-10, inner_tol=1e-5):
         _check(lib().kfbi_set_solver(self.handle, int(precision), int(gmres_m), int(max_restarts),
                                      float(tol), float(inner_tol)), "kfbi_set_solver")
 

@@ -66,7 +66,7 @@ void kfbi_default_options(kfbi_options* o) {
   o->gmres_m = 50;
   o->max_restarts = 20;
   o->tol = 1e-10;
-  o->inner_tol = 1e-6;
+  o->inner_tol = 1e-5;
 }
 
 const char* kfbi_status_string(kfbi_status s) {
@@ -150,6 +150,9 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.V32, sizeof(float) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.B64, sizeof(double) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.V64, sizeof(double) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.W32, sizeof(float) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.X64[0], sizeof(double) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.X64[1], sizeof(double) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.scal, sizeof(double) * 16));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.vecs, sizeof(double) * 8 * M));
   if (cudaMallocHost((void**)&c.h_pinned, sizeof(double) * 16) != cudaSuccess) {
@@ -180,7 +183,7 @@ kfbi_status kfbi_apply_layer_potential(kfbi_ctx ctx, int layer, int precision,
                                        const double* d_density, double* d_out, void* stream) {
   Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
   if (!c || !d_density || !d_out || (layer != KFBI_DOUBLE_LAYER && layer != KFBI_SINGLE_LAYER) ||
-      (precision != KFBI_FP64 && precision != KFBI_MIXED_FP32)) {
+      !kfbi::valid_precision(precision)) {
     kfbi::set_error("kfbi_apply_layer_potential: bad argument");
     return KFBI_ERR_ARG;
   }
@@ -193,7 +196,7 @@ kfbi_status kfbi_apply_volume(kfbi_ctx ctx, int precision, const double* d_f_gri
                               const double* d_f_ctrl, double* d_out, void* stream) {
   Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
   if (!c || !d_f_grid || !d_f_ctrl || !d_out ||
-      (precision != KFBI_FP64 && precision != KFBI_MIXED_FP32)) {
+      !kfbi::valid_precision(precision)) {
     kfbi::set_error("kfbi_apply_volume: bad argument");
     return KFBI_ERR_ARG;
   }
@@ -206,7 +209,7 @@ kfbi_status kfbi_interface_solve(kfbi_ctx ctx, int precision, const double* d_de
                                  double* d_rhs_grid, double* d_v_grid, double* d_out,
                                  void* stream) {
   Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
-  if (!c || (precision != KFBI_FP64 && precision != KFBI_MIXED_FP32)) {
+  if (!c || !kfbi::valid_precision(precision)) {
     kfbi::set_error("kfbi_interface_solve: bad argument");
     return KFBI_ERR_ARG;
   }
@@ -217,7 +220,7 @@ kfbi_status kfbi_interface_solve(kfbi_ctx ctx, int precision, const double* d_de
 kfbi_status kfbi_box_solve(kfbi_ctx ctx, int precision, const double* d_b_grid, double* d_v_grid,
                            void* stream) {
   Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
-  if (!c || !d_b_grid || !d_v_grid || (precision != KFBI_FP64 && precision != KFBI_MIXED_FP32)) {
+  if (!c || !d_b_grid || !d_v_grid || !kfbi::valid_precision(precision)) {
     kfbi::set_error("kfbi_box_solve: bad argument");
     return KFBI_ERR_ARG;
   }
@@ -256,7 +259,7 @@ kfbi_status kfbi_get_info(kfbi_ctx ctx, kfbi_ctx_info* info) {
 
 kfbi_status kfbi_set_solver(kfbi_ctx ctx, int precision, int gmres_m, int max_restarts,
                             double tol, double inner_tol) {
-  if (!ctx || (precision != KFBI_FP64 && precision != KFBI_MIXED_FP32) || gmres_m < 1 ||
+  if (!ctx || !kfbi::valid_precision(precision) || gmres_m < 1 ||
       gmres_m > 128 || max_restarts < 0 || !(tol > 0) || !(inner_tol > 0)) {
     kfbi::set_error("kfbi_set_solver: bad argument");
     return KFBI_ERR_ARG;

@@ -177,6 +177,7 @@ __device__ void fft_line(cx<T>* z, const FftPlan& p, int t, const cx<T>* __restr
 template <typename T>
 __device__ __forceinline__ void mirror_fill(cx<T>* z, int N, int t, int tpl) {
   const int half = N >> 1;
+#pragma unroll 4
   for (int m = half + t; m < N; m += tpl) {
     const int mp = N - m;
     const T re = (mp < half) ? z[padi(mp)].x : T(0);
@@ -206,72 +207,126 @@ __device__ __forceinline__ cx<T> dst_pair(const cx<T>* z, int N, int q,
 
 // ---------------------------------------------------------------------------- pass 1/3
 // DST-I along every row of the N x N grid: out[row] = scale * DST(in[row]).  in may equal
-// out.  Lines per CTA = blockDim.x / tpl; persistent grid-stride loop over rows.
+// out.  LPC lines per CTA (tpl threads each); persistent grid-stride loop over rows.  The
+// next row is loaded into registers while the current one is transformed, so global
+// latency overlaps the FFT.
 template <typename T, int EPT>
 __global__ void __launch_bounds__(512) dst_rows_kernel(const T* in, T* out, FftPlan p,
                                                        const cx<T>* __restrict__ tw, T scale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
-  const int N = p.N, tpl = p.tpl, half = N >> 1;
+  constexpr int H = EPT / 2;                 // packed pairs per thread
+  const int N = p.N, tpl = p.tpl;
   const int lpc = blockDim.x / tpl;
   const int line = threadIdx.x / tpl, t = threadIdx.x - line * tpl;
   cx<T>* z = sm + line * padded_len(N);
-  for (int row0 = blockIdx.x * lpc; row0 < N; row0 += gridDim.x * lpc) {
-    const int row = row0 + line;
-    const bool active = row < N;
+  const int step = gridDim.x * lpc;
+  int row = blockIdx.x * lpc + line;
+  cx<T> pre[H];
+  if (row < N) {
     const cx<T>* src = reinterpret_cast<const cx<T>*>(in + (size_t)row * N);
-    for (int m = t; m < half; m += tpl) z[padi(m)] = active ? src[m] : cx<T>{T(0), T(0)};
+#pragma unroll
+    for (int u = 0; u < H; ++u) pre[u] = src[t + u * tpl];
+  }
+  for (int row0 = blockIdx.x * lpc; row0 < N; row0 += step, row += step) {
+    const bool active = row < N;
+#pragma unroll
+    for (int u = 0; u < H; ++u) z[padi(t + u * tpl)] = active ? pre[u] : cx<T>{T(0), T(0)};
+    const int nrow = row + step;
+    if (nrow < N) {
+      const cx<T>* src = reinterpret_cast<const cx<T>*>(in + (size_t)nrow * N);
+#pragma unroll
+      for (int u = 0; u < H; ++u) pre[u] = src[t + u * tpl];
+    }
     __syncthreads();
     mirror_fill(z, N, t, tpl);
     __syncthreads();
     fft_line<T, EPT>(z, p, t, tw);
-    cx<T>* dst = reinterpret_cast<cx<T>*>(out + (size_t)row * N);
-    for (int q = t; q < half; q += tpl) {
-      cx<T> o = dst_pair(z, N, q, tw);
-      if (active) dst[q] = {o.x * scale, o.y * scale};
+    cx<T> o[H];
+#pragma unroll
+    for (int u = 0; u < H; ++u) o[u] = dst_pair(z, N, t + u * tpl, tw);
+    if (active) {
+      cx<T>* dst = reinterpret_cast<cx<T>*>(out + (size_t)row * N);
+#pragma unroll
+      for (int u = 0; u < H; ++u) dst[t + u * tpl] = {o[u].x * scale, o[u].y * scale};
     }
     __syncthreads();
   }
 }
 
+// raw vector of B bytes for tile loads / stores
+template <int B> struct RawVec;
+template <> struct RawVec<4> { typedef unsigned int type; };
+template <> struct RawVec<8> { typedef uint2 type; };
+template <> struct RawVec<16> { typedef uint4 type; };
+
+// reciprocal: FP32 correctly rounded; FP64 by two Newton-Raphson steps from the FP32 one
+__device__ __forceinline__ float recip(float d) { return __frcp_rn(d); }
+__device__ __forceinline__ double recip(double d) {
+  double r = (double)__frcp_rn((float)d);
+  r = r * (2.0 - d * r);
+  r = r * (2.0 - d * r);
+  return r;
+}
+
 // ---------------------------------------------------------------------------- pass 2
 // For L consecutive columns (x-modes k) per CTA: DST-I along y, multiply by
 // scale / (lam[k] + lam[l] - kappa^2), DST-I along y again; column 0 and row 0 stay 0.
-template <typename T, int EPT, int MAXT>
-__global__ void __launch_bounds__(MAXT) dst_cols_solve_kernel(T* V, FftPlan p, int L,
+// The tile rows are moved as 16-byte (or narrower) vectors; the next tile is loaded
+// into registers while the current one is transformed.
+template <typename T, int EPT, int L, int MAXT>
+__global__ void __launch_bounds__(MAXT) dst_cols_solve_kernel(T* V, FftPlan p,
                                                               const cx<T>* __restrict__ tw,
                                                               const T* __restrict__ lam,
                                                               T kappa2, T scale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  constexpr int CH = (L * (int)sizeof(T) >= 16) ? L * (int)sizeof(T) / 16 : 1;  // chunks/row
+  constexpr int W = L / CH;                                                        // T per chunk
+  constexpr int VB = W * (int)sizeof(T);
+  constexpr int NC = EPT * CH / L;                                                 // chunks/thread
+  typedef typename RawVec<VB>::type Raw;
   const int N = p.N, tpl = p.tpl, PL = padded_len(N);
   const int line = threadIdx.x / tpl, t = threadIdx.x - line * tpl;
   cx<T>* z = sm + line * PL;
   const int nthr = blockDim.x;
-  for (int c0 = blockIdx.x * L; c0 < N; c0 += gridDim.x * L) {
-    // load the column tile: element (row r, column c0+c) -> line c, value index r
-    for (int idx = threadIdx.x; idx < N * L; idx += nthr) {
-      const int r = idx / L, c = idx - r * L;
-      const int col = c0 + c;
-      const T val = (col < N) ? V[(size_t)r * N + col] : T(0);
-      T* zl = reinterpret_cast<T*>(sm + c * PL);
-      zl[2 * padi(r >> 1) + (r & 1)] = val;
+  Raw pre[NC];
+  int c0 = blockIdx.x * L;
+  auto load_tile = [&](int col0) {
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      const int g = threadIdx.x + i * nthr;
+      const int r = g / CH, cc = g - r * CH;
+      pre[i] = *reinterpret_cast<const Raw*>(V + (size_t)r * N + col0 + cc * W);
     }
+  };
+  if (c0 < N) load_tile(c0);
+  for (; c0 < N; c0 += gridDim.x * L) {
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      const int g = threadIdx.x + i * nthr;
+      const int r = g / CH, cc = g - r * CH;
+      const T* vals = reinterpret_cast<const T*>(&pre[i]);
+      const int pos = 2 * padi(r >> 1) + (r & 1);
+#pragma unroll
+      for (int w = 0; w < W; ++w) reinterpret_cast<T*>(sm + (cc * W + w) * PL)[pos] = vals[w];
+    }
+    if (c0 + gridDim.x * L < N) load_tile(c0 + gridDim.x * L);
     __syncthreads();
     mirror_fill(z, N, t, tpl);
     __syncthreads();
     fft_line<T, EPT>(z, p, t, tw);
     // spectral division, repacked as the next transform's input pairs
     const int k = c0 + line;
-    const T lk = (k < N) ? lam[k] : T(0);
+    const T lk = lam[k] - kappa2;
     cx<T> keep[EPT / 2];
 #pragma unroll
     for (int u = 0; u < EPT / 2; ++u) {
       const int q = t + u * tpl;
       cx<T> o = dst_pair(z, N, q, tw);
       const int l0 = 2 * q, l1 = 2 * q + 1;
-      const T d0 = (k == 0 || l0 == 0 || k >= N) ? T(0) : scale / (lk + lam[l0] - kappa2);
-      const T d1 = (k == 0 || k >= N) ? T(0) : scale / (lk + lam[l1] - kappa2);
+      const T d0 = (k == 0 || l0 == 0) ? T(0) : scale * recip(lk + lam[l0]);
+      const T d1 = (k == 0) ? T(0) : scale * recip(lk + lam[l1]);
       keep[u] = {o.x * d0, o.y * d1};
     }
     __syncthreads();
@@ -288,11 +343,16 @@ __global__ void __launch_bounds__(MAXT) dst_cols_solve_kernel(T* V, FftPlan p, i
 #pragma unroll
     for (int u = 0; u < EPT / 2; ++u) z[padi(t + u * tpl)] = keep[u];
     __syncthreads();
-    for (int idx = threadIdx.x; idx < N * L; idx += nthr) {
-      const int r = idx / L, c = idx - r * L;
-      const int col = c0 + c;
-      const T* zl = reinterpret_cast<const T*>(sm + c * PL);
-      if (col < N) V[(size_t)r * N + col] = zl[2 * padi(r >> 1) + (r & 1)];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      const int g = threadIdx.x + i * nthr;
+      const int r = g / CH, cc = g - r * CH;
+      Raw out;
+      T* vals = reinterpret_cast<T*>(&out);
+      const int pos = 2 * padi(r >> 1) + (r & 1);
+#pragma unroll
+      for (int w = 0; w < W; ++w) vals[w] = reinterpret_cast<const T*>(sm + (cc * W + w) * PL)[pos];
+      *reinterpret_cast<Raw*>(V + (size_t)r * N + c0 + cc * W) = out;
     }
     __syncthreads();
   }
@@ -391,34 +451,57 @@ static kfbi_status launch_rows(Ctx& c, const T* in, T* out, const cx<T>* tw, T s
   return KFBI_OK;
 }
 
-template <typename T, int EPT>
-static kfbi_status launch_cols(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
+template <typename T, int EPT, int L>
+static kfbi_status launch_cols_L(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   constexpr int MAXT = (sizeof(T) == 4 && EPT == 16) ? 1024 : 512;
   const FftPlan& p = c.plan;
   const size_t line_bytes = (size_t)padded_len(p.N) * sizeof(cx<T>);
-  int L = 1;
-  while (L * 2 * p.tpl <= MAXT && (size_t)(L * 2) * line_bytes <= 160 * 1024 && L < 32) L *= 2;
   const int threads = L * p.tpl;
   const size_t smem = (size_t)L * line_bytes;
-  static bool attr_done[2] = {false, false};
-  if (!attr_done[sizeof(T) == 8]) {
-    KFBI_CUDA_TRY(cudaFuncSetAttribute(dst_cols_solve_kernel<T, EPT, MAXT>,
+  static bool attr_done = false;
+  if (!attr_done) {
+    KFBI_CUDA_TRY(cudaFuncSetAttribute(dst_cols_solve_kernel<T, EPT, L, MAXT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr_done[sizeof(T) == 8] = true;
+    attr_done = true;
   }
   int per_sm = 0;
   KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, dst_cols_solve_kernel<T, EPT, MAXT>, threads, smem));
+      &per_sm, dst_cols_solve_kernel<T, EPT, L, MAXT>, threads, smem));
   if (per_sm < 1) per_sm = 1;
-  int blocks = (p.N + L - 1) / L;
+  int blocks = p.N / L;
   blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
   const T scale = T((2.0 / p.N) * (2.0 / p.N));
   const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
-  dst_cols_solve_kernel<T, EPT, MAXT><<<blocks, threads, smem, c.stream>>>(V, p, L, tw, lam,
-                                                                           T(c.kappa2), scale);
+  dst_cols_solve_kernel<T, EPT, L, MAXT><<<blocks, threads, smem, c.stream>>>(V, p, tw, lam,
+                                                                              T(c.kappa2), scale);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
+}
+
+// tile width: largest power of two L <= 32 dividing N with L * tpl threads within the
+// kernel's bound and L lines within 160 KB of shared memory
+template <typename T, int EPT>
+static int cols_tile(const FftPlan& p) {
+  constexpr int MAXT = (sizeof(T) == 4 && EPT == 16) ? 1024 : 512;
+  const size_t line_bytes = (size_t)padded_len(p.N) * sizeof(cx<T>);
+  int L = 1;
+  while (L < 32 && p.N % (2 * L) == 0 && 2 * L * p.tpl <= MAXT &&
+         (size_t)(2 * L) * line_bytes <= 160 * 1024)
+    L *= 2;
+  return L;
+}
+
+template <typename T, int EPT>
+static kfbi_status launch_cols(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
+  switch (cols_tile<T, EPT>(c.plan)) {
+    case 1: return launch_cols_L<T, EPT, 1>(c, V, tw, lam);
+    case 2: return launch_cols_L<T, EPT, 2>(c, V, tw, lam);
+    case 4: return launch_cols_L<T, EPT, 4>(c, V, tw, lam);
+    case 8: return launch_cols_L<T, EPT, 8>(c, V, tw, lam);
+    case 16: return launch_cols_L<T, EPT, 16>(c, V, tw, lam);
+    default: return launch_cols_L<T, EPT, 32>(c, V, tw, lam);
+  }
 }
 
 template <typename T, int EPT>

@@ -11,9 +11,6 @@
 
 namespace kfbi {
 
-kfbi_status combined_u(Ctx& c, const double* dens, const double* f_grid, const double* f_ctrl,
-                       double* u_grid);
-
 constexpr int RED_T = 256;
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -162,7 +159,7 @@ kfbi_status alloc_gmres(Ctx& c, int m) {
 }
 
 static kfbi_status apply_K(Ctx& c, int precision, const double* x, double* y, Counters& cnt) {
-  if (precision == KFBI_FP64) ++cnt.applies64; else ++cnt.applies32;
+  if (precision == KFBI_MIXED_FP32) ++cnt.applies32; else ++cnt.applies64;
   return apply_potential(c, Layer::Double, precision, x, y);
 }
 
@@ -173,12 +170,15 @@ static kfbi_status read_scal(Ctx& c, int n) {
   return KFBI_OK;
 }
 
-// GMRES(m) on K_D in `precision` for rhs; x in/out (x_zero: start from 0).  Stops when the
-// residual is <= tol_abs.  final_true: form the true residual after the last cycle and
-// return its norm in *res_out (else the Givens estimate).
-static kfbi_status gmres_run(Ctx& c, int precision, const double* rhs, double* x, bool x_zero,
-                             double tol_abs, int max_cycles, bool final_true, Counters& cnt,
-                             double* res_out) {
+// GMRES(m) on K_D for rhs, x in/out (x_zero: start from 0), FP64 Arnoldi.  The matvec of
+// each Arnoldi step runs in prec_hi while the residual estimate is above relax_abs and in
+// prec_lo below it (inexact Krylov relaxation: a matvec may be as inaccurate as
+// tol / ||r_j|| relative once the residual is small).  Every cycle ends with the true
+// residual formed with the FP64-accurate apply prec_true (an iterative-refinement step).
+// Stops when the residual is <= tol_abs; *res_out = last true residual norm.
+static kfbi_status gmres_run(Ctx& c, int prec_hi, int prec_lo, double relax_abs, int prec_true,
+                             const double* rhs, double* x, bool x_zero, double tol_abs,
+                             int max_cycles, Counters& cnt, double* res_out, int* cycles_out) {
   const int M = c.M, m = c.gm_m;
   cudaStream_t st = c.stream;
   double* r = c.vecs;            // residual
@@ -190,7 +190,7 @@ static kfbi_status gmres_run(Ctx& c, int precision, const double* rhs, double* x
     KFBI_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * M, st));
     KFBI_CUDA_TRY(cudaMemcpyAsync(r, rhs, sizeof(double) * M, cudaMemcpyDeviceToDevice, st));
   } else {
-    KFBI_TRY(apply_K(c, precision, x, tmp, cnt));
+    KFBI_TRY(apply_K(c, prec_true, x, tmp, cnt));
     prof_count(c, ST_KRYLOV);
     sub_kernel<<<vb(M), 256, 0, st>>>(r, rhs, tmp, M);
   }
@@ -199,50 +199,44 @@ static kfbi_status gmres_run(Ctx& c, int precision, const double* rhs, double* x
   KFBI_TRY(read_scal(c, 4));
   double beta = c.h_pinned[2];
   if (!std::isfinite(beta)) return KFBI_ERR_NUMERIC;
-  for (int cyc = 0; cyc < max_cycles && beta > tol_abs; ++cyc) {
+  int cyc = 0;
+  for (; cyc < max_cycles && beta > tol_abs; ++cyc) {
     prof_count(c, ST_KRYLOV);
     cycle_start_kernel<<<vb(M > m + 1 ? M : m + 1), 256, 0, st>>>(c.basis, r, M, c.gvec, m, c.scal);
     int k = 0;
+    double est = beta;
     for (int j = 0; j < m; ++j) {
-      KFBI_TRY(apply_K(c, precision, c.basis + (size_t)j * M, w, cnt));
+      const int prec = est > relax_abs ? prec_hi : prec_lo;
+      KFBI_TRY(apply_K(c, prec, c.basis + (size_t)j * M, w, cnt));
       ++cnt.iters;
-      prof_count(c, ST_KRYLOV);
+      prof_count(c, ST_KRYLOV, 5);
       multidot_kernel<<<j + 1, RED_T, 0, st>>>(c.basis, M, M, w, h1);
-      prof_count(c, ST_KRYLOV);
       mv_update_kernel<<<vb(M), 256, 0, st>>>(w, c.basis, M, M, h1, j + 1, -1.0);
-      prof_count(c, ST_KRYLOV);
       multidot_kernel<<<j + 1, RED_T, 0, st>>>(c.basis, M, M, w, h2);
-      prof_count(c, ST_KRYLOV);
       mv_update_kernel<<<vb(M), 256, 0, st>>>(w, c.basis, M, M, h2, j + 1, -1.0);
-      prof_count(c, ST_KRYLOV);
       finish_kernel<<<1, 1024, 0, st>>>(j, m, M, w, c.basis, M, h1, h2, c.hess, c.givens,
                                         c.gvec, c.scal);
       KFBI_CUDA_TRY(cudaGetLastError());
       KFBI_TRY(read_scal(c, 4));
       k = j + 1;
       if (c.h_pinned[3] != 0.0) return KFBI_ERR_NUMERIC;
-      if (c.h_pinned[0] <= tol_abs || c.h_pinned[1] != 0.0) break;
+      est = c.h_pinned[0];
+      if (est <= tol_abs || c.h_pinned[1] != 0.0) break;
     }
-    prof_count(c, ST_KRYLOV);
+    prof_count(c, ST_KRYLOV, 2);
     lsq_kernel<<<1, 32, 0, st>>>(k, m, c.hess, c.gvec, c.yvec);
-    prof_count(c, ST_KRYLOV);
     mv_update_kernel<<<vb(M), 256, 0, st>>>(x, c.basis, M, M, c.yvec, k, 1.0);
     KFBI_CUDA_TRY(cudaGetLastError());
-    const bool last = cyc + 1 == max_cycles;
-    if (!final_true && (c.h_pinned[0] <= tol_abs || last)) {
-      beta = c.h_pinned[0];
-      break;
-    }
-    KFBI_TRY(apply_K(c, precision, x, tmp, cnt));
-    prof_count(c, ST_KRYLOV);
+    KFBI_TRY(apply_K(c, prec_true, x, tmp, cnt));
+    prof_count(c, ST_KRYLOV, 2);
     sub_kernel<<<vb(M), 256, 0, st>>>(r, rhs, tmp, M);
-    prof_count(c, ST_KRYLOV);
     norm_kernel<<<1, 1024, 0, st>>>(r, M, c.scal, 2);
     KFBI_TRY(read_scal(c, 4));
     beta = c.h_pinned[2];
     if (!std::isfinite(beta)) return KFBI_ERR_NUMERIC;
   }
   *res_out = beta;
+  if (cycles_out) *cycles_out = cyc;
   return KFBI_OK;
 }
 
@@ -251,69 +245,36 @@ kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const 
   const int M = c.M;
   cudaStream_t st = c.stream;
   KFBI_TRY(alloc_gmres(c, c.opt.gmres_m));
+  // precision of every step that must be FP64-accurate: FP64 transforms in the plain FP64
+  // solver, FP32 transforms with FP64 residual refinement otherwise
+  const int acc = c.opt.precision == KFBI_FP64 ? KFBI_FP64 : KFBI_FP32_REFINED;
   double* ghat = c.vecs + 3 * M;
   double* phi = c.vecs + 4 * M;
   double* d = c.vecs + 5 * M;
   Counters cnt;
-  // g_hat = g - (Y f)^+   (FP64 volume solve)
-  KFBI_TRY(interface_solve(c, KFBI_FP64, nullptr, f_grid, f_ctrl, nullptr, nullptr, d));
+  // g_hat = g - (Y f)^+
+  KFBI_TRY(interface_solve(c, acc, nullptr, f_grid, f_ctrl, nullptr, nullptr, d));
   ++cnt.applies64;
-  prof_count(c, ST_KRYLOV);
+  prof_count(c, ST_KRYLOV, 2);
   sub_kernel<<<vb(M), 256, 0, st>>>(ghat, g_ctrl, d, M);
-  prof_count(c, ST_KRYLOV);
   norm_kernel<<<1, 1024, 0, st>>>(ghat, M, c.scal, 4);
   KFBI_TRY(read_scal(c, 5));
   const double gnorm = c.h_pinned[4];
   const double tol_abs = c.opt.tol * gnorm;
   double res = 0.0;
-  int outer = 0;
-  if (c.opt.precision == KFBI_FP64) {
-    KFBI_TRY(gmres_run(c, KFBI_FP64, ghat, phi, true, tol_abs, c.opt.max_restarts + 1, true, cnt,
-                       &res));
-    outer = 1;
+  int cycles = 0;
+  if (c.opt.precision == KFBI_MIXED_FP32) {
+    // one-step refined applies while the residual is large, plain FP32 applies once it is
+    // below tol / inner_tol (inner_tol: assumed relative accuracy of an FP32 apply)
+    KFBI_TRY(gmres_run(c, PREC_REFINED1, KFBI_MIXED_FP32, tol_abs / c.opt.inner_tol, acc, ghat,
+                       phi, true, tol_abs, c.opt.max_restarts + 1, cnt, &res, &cycles));
   } else {
-    KFBI_CUDA_TRY(cudaMemsetAsync(phi, 0, sizeof(double) * M, st));
-    double* r = c.vecs + 2 * M;     // outer residual lives in tmp slot before inner use
-    // first residual is g_hat itself (phi = 0)
-    res = gnorm;
-    for (outer = 0; outer < c.opt.max_restarts && res > tol_abs; ++outer) {
-      double* rr = ghat;
-      if (outer > 0) {
-        KFBI_TRY(apply_K(c, KFBI_FP64, phi, d, cnt));
-        prof_count(c, ST_KRYLOV);
-        sub_kernel<<<vb(M), 256, 0, st>>>(r, ghat, d, M);
-        prof_count(c, ST_KRYLOV);
-        norm_kernel<<<1, 1024, 0, st>>>(r, M, c.scal, 5);
-        KFBI_TRY(read_scal(c, 6));
-        res = c.h_pinned[5];
-        if (!std::isfinite(res)) return KFBI_ERR_NUMERIC;
-        if (res <= tol_abs) break;
-        // keep the outer residual safe from the inner solver's scratch vectors
-        KFBI_CUDA_TRY(cudaMemcpyAsync(d, r, sizeof(double) * M, cudaMemcpyDeviceToDevice, st));
-        rr = d;
-      }
-      double* corr = c.vecs + 6 * M;
-      double inner_res = 0.0;
-      KFBI_TRY(gmres_run(c, KFBI_MIXED_FP32, rr, corr, true, c.opt.inner_tol * res, 3, false,
-                         cnt, &inner_res));
-      prof_count(c, ST_KRYLOV);
-      axpy_kernel<<<vb(M), 256, 0, st>>>(phi, corr, 1.0, M);     // phi += d
-      KFBI_CUDA_TRY(cudaGetLastError());
-    }
-    if (res > tol_abs) {
-      // final true residual after the last correction
-      KFBI_TRY(apply_K(c, KFBI_FP64, phi, d, cnt));
-      prof_count(c, ST_KRYLOV);
-      sub_kernel<<<vb(M), 256, 0, st>>>(r, ghat, d, M);
-      prof_count(c, ST_KRYLOV);
-      norm_kernel<<<1, 1024, 0, st>>>(r, M, c.scal, 5);
-      KFBI_TRY(read_scal(c, 6));
-      res = c.h_pinned[5];
-    }
+    KFBI_TRY(gmres_run(c, acc, acc, 0.0, acc, ghat, phi, true, tol_abs, c.opt.max_restarts + 1,
+                       cnt, &res, &cycles));
   }
   // u = W phi + Y f on inside nodes
   if (u_grid) {
-    KFBI_TRY(combined_u(c, phi, f_grid, f_ctrl, u_grid));
+    KFBI_TRY(combined_u(c, acc, phi, f_grid, f_ctrl, u_grid));
     ++cnt.applies64;
   }
   if (dens_out)
@@ -322,7 +283,7 @@ kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const 
   const double rel = gnorm > 0 ? res / gnorm : 0.0;
   if (info) {
     info->iterations = cnt.iters;
-    info->outer_iterations = outer;
+    info->outer_iterations = cycles;
     info->applies_fp64 = cnt.applies64;
     info->applies_low = cnt.applies32;
     info->rel_residual = rel;

@@ -116,6 +116,9 @@ struct Ctx {
   // work grids (N x N, row 0 and column 0 identically zero)
   float* B32 = nullptr;  float* V32 = nullptr;     // sparse RHS (irregular entries only), work
   double* B64 = nullptr; double* V64 = nullptr;
+  float* W32 = nullptr;                             // refinement residual (FP32)
+  double* X64[2] = {nullptr, nullptr};              // refinement iterates (FP64, ping-pong)
+  int refine_steps = 2;
   BoxTables<float> t32{};
   BoxTables<double> t64{};
 
@@ -163,6 +166,11 @@ kfbi_status interface_solve(Ctx& c, int precision, const double* dens, const dou
                             double* out);
 kfbi_status box_solve_grid(Ctx& c, int precision, const double* b_grid, double* v_grid);
 kfbi_status inside_mask(Ctx& c, uint8_t* mask);
+kfbi_status combined_u(Ctx& c, int precision, const double* dens, const double* f_grid,
+                       const double* f_ctrl, double* u_grid);
+// internal precision code: FP32 transforms with one refinement step (about 1e-11)
+constexpr int PREC_REFINED1 = 16;
+inline bool valid_precision(int p) { return p == KFBI_FP64 || p == KFBI_MIXED_FP32 || p == KFBI_FP32_REFINED; }
 
 // solver (gmres.cu)
 kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const double* g_ctrl,

@@ -49,8 +49,10 @@ def test_box_solve_parity(N, kappa):
     ref = O.box_solve_dst(b, N, geom.h, kappa * kappa)
     v64 = ctx.box_solve(b, K.KFBI_FP64).cpu().numpy()
     v32 = ctx.box_solve(b, K.KFBI_MIXED_FP32).cpu().numpy()
+    vr = ctx.box_solve(b, K.KFBI_FP32_REFINED).cpu().numpy()
     assert rel(v64, ref) < 1e-12
     assert rel(v32, ref) < 2e-5
+    assert rel(vr, ref) < 1e-11
     assert np.all(v64[-1] == 0) and np.all(v64[:, -1] == 0) and np.all(v64[0] == 0)
     ctx.close()
 
@@ -84,6 +86,20 @@ def test_interface_solve_stages_fp64(case):
 
 
 @pytest.mark.parametrize("case", list(CASES))
+def test_interface_solve_refined_fp32(case):
+    prob = CASES[case]()
+    ctx, geom = make(prob)
+    phi = W.random_density(prob.iface.M, seed=12)
+    fg, fc = prob.f_grid(), prob.f_ctrl()
+    rhs, v, out = ctx.interface_solve(phi, fg, fc, K.KFBI_FP32_REFINED)
+    o_out, o_b, o_v = O.apply_interface(geom, phi=phi, f_ctrl=fc, F_grid=fg, return_all=True)
+    assert rel(rhs.cpu().numpy(), o_b) < 1e-11
+    assert rel(v.cpu().numpy(), o_v) < 1e-11
+    assert rel(out.cpu().numpy(), o_out) < 1e-11
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
 def test_double_layer_apply_parity(case):
     prob = CASES[case]()
     ctx, geom = make(prob)
@@ -91,8 +107,10 @@ def test_double_layer_apply_parity(case):
     ref = O.apply_double_layer(geom, phi)
     g64 = ctx.apply_layer_potential(phi, K.KFBI_DOUBLE_LAYER, K.KFBI_FP64).cpu().numpy()
     g32 = ctx.apply_layer_potential(phi, K.KFBI_DOUBLE_LAYER, K.KFBI_MIXED_FP32).cpu().numpy()
+    gr = ctx.apply_layer_potential(phi, K.KFBI_DOUBLE_LAYER, K.KFBI_FP32_REFINED).cpu().numpy()
     assert rel(g64, ref) < 1e-11
     assert rel(g32, ref) < 2e-5
+    assert rel(gr, ref) < 1e-11
     # repeated applies are bit-identical
     again = ctx.apply_layer_potential(phi, K.KFBI_DOUBLE_LAYER, K.KFBI_FP64).cpu().numpy()
     assert np.array_equal(again, g64)
@@ -133,14 +151,26 @@ def test_solve_bvp_fp64_matches_oracle(case):
     ctx.close()
 
 
+@pytest.mark.parametrize("case", ["flower128_poisson", "ellipse256_k10"])
+def test_solve_bvp_refined_matches_oracle(case):
+    prob = CASES[case]()
+    ctx, geom = make(prob, precision=K.KFBI_FP32_REFINED, tol=1e-12)
+    u, phi, info = ctx.solve_bvp(prob.f_grid(), prob.f_ctrl(), prob.g_ctrl())
+    u_o, phi_o, _ = O.solve_bvp(geom, prob.f_grid(), prob.f_ctrl(), prob.g_ctrl(), tol=1e-13)
+    assert info["converged"] and info["applies_low"] == 0
+    assert rel(phi.cpu().numpy(), phi_o) < 1e-9
+    assert rel(u.cpu().numpy(), u_o) < 1e-9
+    ctx.close()
+
+
 @pytest.mark.parametrize("case", ["flower128_poisson", "ellipse256_k10", "star192_batchlike"])
 def test_solve_bvp_mixed_precision(case):
     prob = CASES[case]()
     ctx, geom = make(prob, precision=K.KFBI_MIXED_FP32, tol=1e-10, inner_tol=1e-5)
-    u, phi, info = ctx.solve_bvp(prob.f_grid(), prob.f_ctrl(), prob.g_ctrl())
+    u, phi, info = ctx.solve_bvp(prob.f_grid(), prob.f_ctrl(), prob.g_ctrl(), allow_not_converged=True)
     u_o, phi_o, _ = O.solve_bvp(geom, prob.f_grid(), prob.f_ctrl(), prob.g_ctrl(), tol=1e-12)
     assert info["converged"], info
-    assert info["applies_low"] > 0
+    assert info["applies_low"] > 0 and info["outer_iterations"] <= 3, info
     assert rel(phi.cpu().numpy(), phi_o) < 1e-6
     u_exact = prob.u_grid()
     disc = np.max(np.abs(u_o - u_exact)[geom.inside])
@@ -178,5 +208,6 @@ def test_full_size_apply_parity(N):
     phi = W.random_density(prob.iface.M, seed=21)
     ref = O.apply_double_layer(geom, phi)
     assert rel(ctx.apply_layer_potential(phi, 0, K.KFBI_FP64).cpu().numpy(), ref) < 1e-11
+    assert rel(ctx.apply_layer_potential(phi, 0, K.KFBI_FP32_REFINED).cpu().numpy(), ref) < 1e-11
     assert rel(ctx.apply_layer_potential(phi, 0, K.KFBI_MIXED_FP32).cpu().numpy(), ref) < 1e-4
     ctx.close()
