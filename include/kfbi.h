@@ -56,13 +56,16 @@ typedef enum {
 
 typedef enum {
   KFBI_FP64 = 0,         /* every stage in FP64                                          */
-  KFBI_MIXED_FP32 = 1,   /* box solve in FP32; geometry, jumps, Arnoldi, Givens and the
-                            refinement residual in FP64 (GMRES-IR)                       */
-  KFBI_FP32_REFINED = 2  /* box solve from FP32 sine transforms, corrected twice against
-                            the FP64 residual of the 5-point system: FP64-accurate (about
-                            1e-12 relative) at FP32 transform cost.  Accepted by the apply
-                            and interface-solve entry points; the mixed BVP solver uses it
-                            for every step that needs FP64 accuracy                      */
+  KFBI_MIXED_FP32 = 1,   /* box solve in FP32 (apply); as a solver mode: FP64 Arnoldi and
+                            Givens with relaxed-precision matvecs and FP64-accurate
+                            residuals (see kfbi_solve_bvp)                               */
+  KFBI_FP32_REFINED = 2, /* box solve from FP32 sine transforms corrected twice against
+                            the residual of the 5-point system, formed in double-single
+                            (exact FP32-pair) arithmetic at regular nodes and in FP64 at
+                            irregular nodes: FP64-accurate (about 1e-13 relative) at FP32
+                            cost; the mixed BVP solver uses it for its accurate steps    */
+  KFBI_FP32_REFINED_ONCE = 3  /* one refinement step (about 1e-11 relative at N = 1024,
+                            3e-10 at N = 4096)                                           */
 } kfbi_precision;
 
 typedef enum {
@@ -153,12 +156,12 @@ kfbi_status kfbi_box_solve(kfbi_ctx ctx, int precision, const double* d_b_grid,
 /* Dirichlet BVP (Procedures 2-3 of Sec. 4.4): g_hat = g - (Y f)^+, K_D phi = g_hat by
    GMRES(m) (Alg. 5; FP64 Arnoldi with CGS2 and Givens rotations on the device), then
    u = W phi + Y f on the grid (Sec. 2.1).  opt->precision selects plain FP64 or mixed
-   precision: one FP64 Arnoldi process whose matvecs use FP32 transforms refined once
-   against the FP64 residual (about 1e-11) while the residual is large and plain FP32
-   box solves once it is below tol / inner_tol (relaxed inexact Krylov); every restart
-   cycle ends with the true residual from a twice-refined (FP64-accurate) apply, so the
-   GMRES residual is refined in FP64; the volume term and the final grid solution use
-   the twice-refined solve as well.
+   precision: one FP64 Arnoldi process whose matvec precision is relaxed as the residual
+   drops (inexact Krylov): twice-refined FP32 box solves while the residual is above
+   tol / 1e-9, once-refined ones down to tol / inner_tol, plain FP32 below; every
+   restart cycle ends with the true residual from a twice-refined (FP64-accurate) apply,
+   so the GMRES residual is refined in FP64; the volume term and the final grid
+   solution use the twice-refined solve as well.
    d_u_grid: (N+1)^2, written inside Omega, zero outside.  d_density_out: M or NULL.
    h_info: host struct or NULL.  Synchronising (convergence is checked on the host). */
 kfbi_status kfbi_solve_bvp(kfbi_ctx ctx, const double* d_f_grid, const double* d_f_ctrl,

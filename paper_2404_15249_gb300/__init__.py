@@ -22,6 +22,7 @@ KFBI_ERR_NOT_CONVERGED = 5
 KFBI_FP64 = 0
 KFBI_MIXED_FP32 = 1
 KFBI_FP32_REFINED = 2
+KFBI_FP32_REFINED_ONCE = 3
 KFBI_DOUBLE_LAYER = 0
 KFBI_SINGLE_LAYER = 1
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_GEOMETRY", 3: "ERR_NOMEM", 4: "ERR_CUDA",

@@ -1,18 +1,32 @@
 // One application of the layer potential (Alg. 1 steps 4-6) and the interface solves
 // built from the same stages:
-//   correction  b_p = F~_p + sum over crossed arms of sigma/h^2 (Taylor jump)  (Alg. 2)
-//   box solve   (Lap_h - kappa^2) v = b, v = 0 on the box boundary            (Alg. 4)
-//   interpolation  v^+(z_k) = sum_p w_p v_p + jump Taylor terms               (Alg. 3)
+//   correction     b_p = F~_p + sum over crossed arms of sigma/h^2 (Taylor jump) (Alg. 2)
+//   box solve      (Lap_h - kappa^2) v = b, v = 0 on the box boundary            (Alg. 4)
+//   interpolation  v^+(z_k) = sum_p w_p v_p + jump Taylor terms                  (Alg. 3)
 // The correction is a gather over the compacted irregular-node list with precomputed
-// FP64 weights (one thread per irregular node, consecutive nodes per warp); for the
-// double-layer apply the right-hand side is nonzero only at irregular nodes, so those
-// entries of a persistent zero grid are overwritten in place and nothing else is touched.
+// FP64 weights (one thread per irregular node, consecutive nodes per warp).  For the
+// double-layer apply the right-hand side is nonzero only at irregular nodes, so only
+// those entries of a persistent zero grid are written.
+//
+// Precisions of the box solve:
+//   FP64                 FP64 sine transforms.
+//   FP32                 FP32 sine transforms.
+//   FP32 refined (1/2)   c1 = FP32 solve of b, then one or two corrections
+//                        c_{k+1} = FP32 solve of r_k = b - (Lap_h - kappa^2)(c1 + ... + c_k);
+//                        v = c1 + c2 (+ c3) summed in FP64 where it is read.  The residual
+//                        is formed in double-single arithmetic: the iterate is the exact
+//                        sum of FP32 values, the 5-point sum uses error-free TwoSum steps
+//                        and an FMA-exact product with 1/h^2, and b is held as an exact
+//                        FP32 pair (hi, lo) - FP32 instructions only, because FP64
+//                        throughput on GB300 is 1/64 of FP32.  Where b is sparse (double
+//                        layer) the irregular nodes are recomputed in FP64.
 #include "kfbi_internal.cuh"
 
 namespace kfbi {
 
 __device__ __forceinline__ int wrap(int k, int M) { return k < 0 ? k + M : (k >= M ? k - M : k); }
 
+// ------------------------------------------------------------------ correction
 // b[irr_node[k]] = (add ? b : 0) + sum_arms sum_r (wD dens + wS psi + wF f)
 template <typename T>
 __global__ void correction_kernel(int nirr, int M, const int* __restrict__ irr_node,
@@ -20,7 +34,7 @@ __global__ void correction_kernel(int nirr, int M, const int* __restrict__ irr_n
                                   const double* __restrict__ wD, const double* __restrict__ wS,
                                   const double* __restrict__ wF, const double* __restrict__ dens,
                                   const double* __restrict__ psi, const double* __restrict__ fctl,
-                                  T* __restrict__ B, int add) {
+                                  T* __restrict__ B, int add, double* __restrict__ B64) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nirr) return;
   double acc = 0.0;
@@ -36,86 +50,103 @@ __global__ void correction_kernel(int nirr, int M, const int* __restrict__ irr_n
   }
   const int node = irr_node[k];
   B[node] = add ? (T)((double)B[node] + acc) : (T)acc;
+  if (B64) B64[node] = acc;        // FP64 copy for the refinement residual
 }
 
-// same sums written to an FP64 grid and its FP32 rounding (right-hand side of a
-// refined FP32 box solve)
-__global__ void correction_dual_kernel(int nirr, int M, const int* __restrict__ irr_node,
-                                       const int* __restrict__ arm_ptr,
-                                       const int* __restrict__ arm_seg,
-                                       const double* __restrict__ wD, const double* __restrict__ wS,
-                                       const double* __restrict__ dens,
-                                       const double* __restrict__ psi, double* __restrict__ B64,
-                                       float* __restrict__ B32) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nirr) return;
-  double acc = 0.0;
-  for (int a = arm_ptr[k]; a < arm_ptr[k + 1]; ++a) {
-    const int s = arm_seg[a];
-#pragma unroll
-    for (int r = 0; r < 6; ++r) {
-      const int m = wrap(s - 2 + r, M);
-      if (dens) acc += wD[6 * a + r] * dens[m];
-      if (psi) acc += wS[6 * a + r] * psi[m];
-    }
-  }
-  const int node = irr_node[k];
-  B64[node] = acc;
-  B32[node] = (float)acc;
+// ------------------------------------------------------------------ double-single residual
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
 }
 
-// One step of iterative refinement of the box solve (Lap_h - kappa^2) v = b:
-//   v_new = v_old + c  (c: FP32 correction from the last FP32 box solve, v_old FP64 or 0),
-//   r = b - (Lap_h - kappa^2) v_new in FP64, stored as FP32 for the next FP32 solve.
-// Work-grid layout N x N with row/column 0 and the implicit row/column N equal to zero.
-__global__ void refine_step_kernel(int N, double inv_h2, double kappa2,
-                                   const double* __restrict__ b, const double* __restrict__ v_old,
-                                   const float* __restrict__ c, double* __restrict__ v_new,
+// value of the iterate at work-grid index q: c1 (+ c2) as an unevaluated pair
+struct DSPair {
+  float hi, lo;
+};
+__device__ __forceinline__ DSPair iterate_at(const float* c1, const float* c2, long q) {
+  if (!c2) return {c1[q], 0.f};
+  DSPair p;
+  two_sum(c1[q], c2[q], p.hi, p.lo);
+  return p;
+}
+
+// r = b - (Lap_h - kappa^2) v, v = c1 (+ c2), b = bhi + blo (dense) or 0 (bhi == nullptr);
+// kappa^2 = k2hi + k2lo exactly.  Every product and sum that can cancel is carried as an
+// exact FP32 pair; only the final residual is rounded to FP32.
+__global__ void ds_residual_kernel(int N, float inv_h2, float k2hi, float k2lo,
+                                   const float* __restrict__ bhi, const float* __restrict__ blo,
+                                   const float* __restrict__ c1, const float* __restrict__ c2,
                                    float* __restrict__ r) {
-  const int j = blockIdx.y;                          // one grid row per blockIdx.y
+  const int j = blockIdx.y;
   const long base = (long)j * N;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const long idx = base + i;
     if (i == 0 || j == 0) {
-      v_new[idx] = 0.0;
       r[idx] = 0.f;
       continue;
     }
-    const double vc = (v_old ? v_old[idx] : 0.0) + (double)c[idx];
-    const double e = (i + 1 < N) ? (v_old ? v_old[idx + 1] : 0.0) + (double)c[idx + 1] : 0.0;
-    const double w = (v_old ? v_old[idx - 1] : 0.0) + (double)c[idx - 1];
-    const double nn = (j + 1 < N) ? (v_old ? v_old[idx + N] : 0.0) + (double)c[idx + N] : 0.0;
-    const double so = (v_old ? v_old[idx - N] : 0.0) + (double)c[idx - N];
-    const double Lv = (e + w + nn + so - 4.0 * vc) * inv_h2 - kappa2 * vc;
-    v_new[idx] = vc;
-    r[idx] = (float)(b[idx] - Lv);
-  }
-}
-
-// v = v_old + c (final refinement update) written to the (N+1)^2 grid, optional mask
-__global__ void refine_out_kernel(int N, const double* __restrict__ v_old,
-                                  const float* __restrict__ c, const uint8_t* __restrict__ mask,
-                                  double* __restrict__ G) {
-  const int j = blockIdx.y;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= N; i += gridDim.x * blockDim.x) {
-    const long g = (long)j * (N + 1) + i;
-    double v = 0.0;
-    if (i < N && j < N) {
-      const long q = (long)j * N + i;
-      v = v_old[q] + (double)c[q];
+    const DSPair vc = iterate_at(c1, c2, idx);
+    const DSPair ve = (i + 1 < N) ? iterate_at(c1, c2, idx + 1) : DSPair{0.f, 0.f};
+    const DSPair vw = iterate_at(c1, c2, idx - 1);
+    const DSPair vn = (j + 1 < N) ? iterate_at(c1, c2, idx + N) : DSPair{0.f, 0.f};
+    const DSPair vs = iterate_at(c1, c2, idx - N);
+    // S = ve + vw + vn + vs - 4 vc  as  s4 + lo
+    float s1, t1, s2, t2, s3, t3, s4, t4;
+    two_sum(ve.hi, vw.hi, s1, t1);
+    two_sum(vn.hi, vs.hi, s2, t2);
+    two_sum(s1, s2, s3, t3);
+    two_sum(s3, -4.f * vc.hi, s4, t4);
+    const float lo = ((t1 + t2) + (t3 + t4)) + ((ve.lo + vw.lo) + (vn.lo + vs.lo) - 4.f * vc.lo);
+    // S / h^2 = p1 + e1 (1/h^2 is a power-of-two multiple of an exact FP32 value)
+    const float p1 = s4 * inv_h2;
+    const float e1 = fmaf(s4, inv_h2, -p1) + lo * inv_h2;
+    // kappa^2 v = p2 + e2
+    const float p2 = k2hi * vc.hi;
+    const float e2 = fmaf(k2hi, vc.hi, -p2) + (k2hi * vc.lo + k2lo * vc.hi);
+    // r = b - p1 + p2 - e1 + e2
+    float d, de;
+    two_sum(p2, -p1, d, de);
+    float tail = de - e1 + e2;
+    if (bhi) {
+      float d2, de2;
+      two_sum(bhi[idx], d, d2, de2);
+      d = d2;
+      tail += de2 + blo[idx];
     }
-    if (mask && !mask[g]) v = 0.0;
-    G[g] = v;
+    r[idx] = d + tail;
   }
 }
 
-// FP64 grid -> FP32 copy (dense right-hand side of a refined solve)
-__global__ void round_kernel(long n, const double* __restrict__ a, float* __restrict__ b) {
-  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
-       k += (long)gridDim.x * blockDim.x)
-    b[k] = (float)a[k];
+// r = b - (Lap_h - kappa^2)(c1 + c2) at the irregular nodes, in FP64 (sparse b)
+__global__ void residual_fix_kernel(int nirr, int N, double inv_h2, double kappa2,
+                                    const int* __restrict__ irr_node, const double* __restrict__ b,
+                                    const float* __restrict__ c1, const float* __restrict__ c2,
+                                    float* __restrict__ r) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nirr) return;
+  const int idx = irr_node[k];
+  const int i = idx % N, j = idx / N;
+  auto v = [&](int q) { return (double)c1[q] + (c2 ? (double)c2[q] : 0.0); };
+  const double s = (i + 1 < N ? v(idx + 1) : 0.0) + v(idx - 1) +
+                   (j + 1 < N ? v(idx + N) : 0.0) + v(idx - N);
+  const double vc = v(idx);
+  r[idx] = (float)(b[idx] - ((s - 4.0 * vc) * inv_h2 - kappa2 * vc));
 }
 
+// dense FP64 right-hand side -> exact FP32 pair (hi, lo)
+__global__ void split_kernel(long n, const double* __restrict__ b, float* __restrict__ hi,
+                             float* __restrict__ lo) {
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
+       k += (long)gridDim.x * blockDim.x) {
+    const double x = b[k];
+    const float h = (float)x;
+    hi[k] = h;
+    lo[k] = (float)(x - (double)h);
+  }
+}
+
+// ------------------------------------------------------------------ grid kernels
 // dense right-hand side on the N x N work grid: F at inside interior nodes, else 0
 template <typename T>
 __global__ void rhs_dense_kernel(int N, const double* __restrict__ F,
@@ -142,24 +173,33 @@ __global__ void grid_to_work_kernel(int N, const double* __restrict__ G, T* __re
   }
 }
 
-// work grid N x N -> (N+1)^2 grid; mask (optional) keeps inside nodes only
+// work grid(s) -> (N+1)^2 FP64 grid: value w1 (+ w2 + w3); mask keeps inside nodes only
 template <typename T>
-__global__ void work_to_grid_kernel(int N, const T* __restrict__ W, const uint8_t* __restrict__ mask,
+__global__ void work_to_grid_kernel(int N, const T* __restrict__ w1, const float* __restrict__ w2,
+                                    const float* __restrict__ w3, const uint8_t* __restrict__ mask,
                                     double* __restrict__ G) {
   const int j = blockIdx.y;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= N; i += gridDim.x * blockDim.x) {
     const long g = (long)j * (N + 1) + i;
-    double v = (i < N && j < N) ? (double)W[(long)j * N + i] : 0.0;
+    double v = 0.0;
+    if (i < N && j < N) {
+      const long q = (long)j * N + i;
+      v = (double)w1[q];
+      if (w2) v += (double)w2[q];
+      if (w3) v += (double)w3[q];
+    }
     if (mask && !mask[g]) v = 0.0;
     G[g] = v;
   }
 }
 
-// out_k = sum_p w_p v(node_p) + sum_r (cD dens + cS psi) + eF f_k
+// ------------------------------------------------------------------ interpolation
+// out_k = sum_p w_p v(node_p) + sum_r (cD dens + cS psi) + eF f_k, v = v1 (+ v2 + v3)
 template <typename T>
 __global__ void interp_kernel(int M, const int* __restrict__ node, const double* __restrict__ w,
                               const double* __restrict__ cD, const double* __restrict__ cS,
-                              const double* __restrict__ eF, const T* __restrict__ V,
+                              const double* __restrict__ eF, const T* __restrict__ v1,
+                              const float* __restrict__ v2, const float* __restrict__ v3,
                               const double* __restrict__ dens, const double* __restrict__ psi,
                               const double* __restrict__ fctl, double* __restrict__ out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -168,7 +208,12 @@ __global__ void interp_kernel(int M, const int* __restrict__ node, const double*
 #pragma unroll
   for (int p = 0; p < 6; ++p) {
     const int nd = node[6 * k + p];
-    if (nd >= 0) acc += w[6 * k + p] * (double)V[nd];
+    if (nd >= 0) {
+      double v = (double)v1[nd];
+      if (v2) v += (double)v2[nd];
+      if (v3) v += (double)v3[nd];
+      acc += w[6 * k + p] * v;
+    }
   }
 #pragma unroll
   for (int r = 0; r < 6; ++r) {
@@ -180,34 +225,10 @@ __global__ void interp_kernel(int M, const int* __restrict__ node, const double*
   out[k] = acc;
 }
 
-// interpolation from a refined solution v = v_old + c
-__global__ void interp_refined_kernel(int M, const int* __restrict__ node,
-                                      const double* __restrict__ w, const double* __restrict__ cD,
-                                      const double* __restrict__ cS, const double* __restrict__ eF,
-                                      const double* __restrict__ v_old, const float* __restrict__ c,
-                                      const double* __restrict__ dens,
-                                      const double* __restrict__ psi,
-                                      const double* __restrict__ fctl, double* __restrict__ out) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= M) return;
-  double acc = 0.0;
-#pragma unroll
-  for (int p = 0; p < 6; ++p) {
-    const int nd = node[6 * k + p];
-    if (nd >= 0) acc += w[6 * k + p] * (v_old[nd] + (double)c[nd]);
-  }
-#pragma unroll
-  for (int r = 0; r < 6; ++r) {
-    const int m = wrap(k - 2 + r, M);
-    if (dens) acc += cD[6 * k + r] * dens[m];
-    if (psi) acc += cS[6 * k + r] * psi[m];
-  }
-  if (fctl) acc += eF[k] * fctl[k];
-  out[k] = acc;
-}
-
+// ------------------------------------------------------------------ host helpers
 static inline dim3 rows_grid(int cols, int rows) {
-  return dim3((unsigned)((cols + 255) / 256 < 8 ? (cols + 255) / 256 : 8), (unsigned)rows);
+  const int bx = (cols + 255) / 256;
+  return dim3((unsigned)(bx < 8 ? bx : 8), (unsigned)rows);
 }
 
 static inline int gs_blocks(long n) {
@@ -217,215 +238,170 @@ static inline int gs_blocks(long n) {
 
 template <typename T>
 static kfbi_status correct(Ctx& c, const double* dens, const double* psi, const double* fctl,
-                           T* B, int add) {
+                           T* B, int add, double* B64 = nullptr) {
   if (c.nirr == 0) return KFBI_OK;
   const int pr = prof_begin(c, ST_CORR);
   correction_kernel<T><<<(c.nirr + 127) / 128, 128, 0, c.stream>>>(
       c.nirr, c.M, c.irr_node, c.arm_ptr, c.arm_seg, c.arm_wD, c.arm_wS, c.arm_wF, dens, psi,
-      fctl, B, add);
+      fctl, B, add, B64);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
 }
 
 template <typename T>
-static kfbi_status interp(Ctx& c, const T* V, const double* dens, const double* psi,
-                          const double* fctl, double* out) {
+static kfbi_status interp(Ctx& c, const T* v1, const float* v2, const float* v3,
+                          const double* dens, const double* psi, const double* fctl,
+                          double* out) {
   const int pr = prof_begin(c, ST_INTERP);
   interp_kernel<T><<<(c.M + 127) / 128, 128, 0, c.stream>>>(c.M, c.ctrl_node, c.ctrl_w,
-                                                            c.ctrl_cD, c.ctrl_cS, c.ctrl_eF, V,
-                                                            dens, psi, fctl, out);
+                                                            c.ctrl_cD, c.ctrl_cS, c.ctrl_eF, v1,
+                                                            v2, v3, dens, psi, fctl, out);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
 }
 
-static kfbi_status box(Ctx& c, int precision, const void* rhs, void* work) {
-  if (precision == KFBI_FP64) return box_solve_f64(c, (const double*)rhs, (double*)work);
-  return box_solve_f32(c, (const float*)rhs, (float*)work);
+template <typename T>
+static kfbi_status to_grid(Ctx& c, const T* w1, const float* w2, const float* w3,
+                           const uint8_t* mask, double* G) {
+  prof_count(c, ST_GRID);
+  work_to_grid_kernel<T><<<rows_grid(c.N + 1, c.N + 1), 256, 0, c.stream>>>(c.N, w1, w2, w3,
+                                                                              mask, G);
+  KFBI_CUDA_TRY(cudaGetLastError());
+  return KFBI_OK;
 }
 
-// Refined FP32 box solve: rhs b64 (FP64) and its FP32 rounding b32 (work-grid layout).
-// Leaves v = X64[final] + V32; returns the index of X64 holding the FP64 part.
-static kfbi_status refined_solve(Ctx& c, const double* b64, const float* b32, int* which,
+static int refine_steps_of(int precision) {
+  return precision == KFBI_FP32_REFINED ? 2 : (precision == KFBI_FP32_REFINED_ONCE ? 1 : 0);
+}
+
+// Refined FP32 box solve.  b32: FP32 right-hand side of the first solve; the residuals use
+// the dense exact pair (bhi, blo) or, when bhi is null, the sparse FP64 right-hand side in
+// B64 at the irregular nodes (zero elsewhere).  Result: v = V32 + U32 (+ T32 if steps = 2).
+static kfbi_status refined_solve(Ctx& c, const float* b32, const float* bhi, const float* blo,
                                  int steps) {
-  const long n = (long)c.N * c.N;
   KFBI_TRY(box_solve_f32(c, b32, c.V32));
-  const double* v_old = nullptr;
-  int cur = 0;
-  for (int it = 0; it < steps; ++it) {
+  const float inv_h2 = (float)(1.0 / (c.h * c.h));
+  const float k2hi = (float)c.kappa2, k2lo = (float)(c.kappa2 - (double)k2hi);
+  for (int s = 0; s < steps; ++s) {
+    const float* c2 = s == 0 ? nullptr : c.U32;      // current iterate = V32 (+ U32)
     const int pr = prof_begin(c, ST_REFINE);
-    refine_step_kernel<<<rows_grid(c.N, c.N), 256, 0, c.stream>>>(c.N, 1.0 / (c.h * c.h), c.kappa2, b64,
-                                                           v_old, c.V32, c.X64[cur], c.W32);
+    ds_residual_kernel<<<rows_grid(c.N, c.N), 256, 0, c.stream>>>(c.N, inv_h2, k2hi, k2lo, bhi,
+                                                                  blo, c.V32, c2, c.W32);
+    if (!bhi && c.nirr > 0)
+      residual_fix_kernel<<<(c.nirr + 127) / 128, 128, 0, c.stream>>>(
+          c.nirr, c.N, 1.0 / (c.h * c.h), c.kappa2, c.irr_node, c.B64, c.V32, c2, c.W32);
     prof_end(c, pr);
+    if (!bhi && c.nirr > 0) prof_count(c, ST_REFINE);
     KFBI_CUDA_TRY(cudaGetLastError());
-    KFBI_TRY(box_solve_f32(c, c.W32, c.V32));
-    v_old = c.X64[cur];
-    cur ^= 1;
-  }
-  *which = cur ^ 1;
-  if (steps == 0) {
-    // no refinement: FP64 part is zero
-    KFBI_CUDA_TRY(cudaMemsetAsync(c.X64[0], 0, sizeof(double) * n, c.stream));
-    *which = 0;
+    KFBI_TRY(box_solve_f32(c, c.W32, s == 0 ? c.U32 : c.T32));
   }
   return KFBI_OK;
 }
 
-static kfbi_status interp_refined(Ctx& c, int which, const double* dens, const double* psi,
-                                  const double* fctl, double* out) {
-  const int pr = prof_begin(c, ST_INTERP);
-  interp_refined_kernel<<<(c.M + 127) / 128, 128, 0, c.stream>>>(
-      c.M, c.ctrl_node, c.ctrl_w, c.ctrl_cD, c.ctrl_cS, c.ctrl_eF, c.X64[which], c.V32, dens,
-      psi, fctl, out);
-  prof_end(c, pr);
-  KFBI_CUDA_TRY(cudaGetLastError());
-  return KFBI_OK;
-}
-
+// ------------------------------------------------------------------ apply
 kfbi_status apply_potential(Ctx& c, Layer layer, int precision, const double* dens, double* out) {
   const double* d = layer == Layer::Double ? dens : nullptr;
   const double* s = layer == Layer::Single ? dens : nullptr;
   if (precision == KFBI_FP64) {
     KFBI_TRY(correct<double>(c, d, s, nullptr, c.B64, 0));
     KFBI_TRY(box_solve_f64(c, c.B64, c.V64));
-    return interp<double>(c, c.V64, d, s, nullptr, out);
+    return interp<double>(c, c.V64, nullptr, nullptr, d, s, nullptr, out);
   }
-  if (precision == KFBI_FP32_REFINED || precision == PREC_REFINED1) {
-    if (c.nirr > 0) {
-      const int pr = prof_begin(c, ST_CORR);
-      correction_dual_kernel<<<(c.nirr + 127) / 128, 128, 0, c.stream>>>(
-          c.nirr, c.M, c.irr_node, c.arm_ptr, c.arm_seg, c.arm_wD, c.arm_wS, d, s, c.B64, c.B32);
-      prof_end(c, pr);
-      KFBI_CUDA_TRY(cudaGetLastError());
-    }
-    int which = 0;
-    KFBI_TRY(refined_solve(c, c.B64, c.B32, &which, precision == PREC_REFINED1 ? 1 : c.refine_steps));
-    return interp_refined(c, which, d, s, nullptr, out);
+  const int steps = refine_steps_of(precision);
+  KFBI_TRY(correct<float>(c, d, s, nullptr, c.B32, 0, steps ? c.B64 : nullptr));
+  if (steps == 0) {
+    KFBI_TRY(box_solve_f32(c, c.B32, c.V32));
+    return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out);
   }
-  KFBI_TRY(correct<float>(c, d, s, nullptr, c.B32, 0));
-  KFBI_TRY(box_solve_f32(c, c.B32, c.V32));
-  return interp<float>(c, c.V32, d, s, nullptr, out);
+  KFBI_TRY(refined_solve(c, c.B32, nullptr, nullptr, steps));
+  return interp<float>(c, c.V32, c.U32, steps > 1 ? c.T32 : nullptr, d, s, nullptr, out);
 }
 
-// dense right-hand side F~ + corrections in FP64 in V64 (work layout)
+// ------------------------------------------------------------------ dense interface solves
+// F~ + corrections in FP64 in V64 (work layout)
 static kfbi_status dense_rhs64(Ctx& c, const double* dens, const double* f_grid,
                                const double* f_ctrl) {
   prof_count(c, ST_GRID);
   rhs_dense_kernel<double><<<rows_grid(c.N, c.N), 256, 0, c.stream>>>(c.N, f_grid, c.inside,
-                                                                             c.V64);
+                                                                      c.V64);
   KFBI_CUDA_TRY(cudaGetLastError());
   return correct<double>(c, dens, nullptr, f_ctrl, c.V64, 1);
 }
 
-template <typename T>
-static kfbi_status interface_solve_t(Ctx& c, int precision, T* W, const double* dens,
-                                     const double* f_grid, const double* f_ctrl,
-                                     double* rhs_grid, double* v_grid, double* out) {
-  prof_count(c, ST_GRID);
-  rhs_dense_kernel<T><<<rows_grid(c.N, c.N), 256, 0, c.stream>>>(c.N, f_grid, c.inside, W);
-  KFBI_CUDA_TRY(cudaGetLastError());
-  KFBI_TRY(correct<T>(c, dens, nullptr, f_ctrl, W, 1));
-  if (rhs_grid) {
-    prof_count(c, ST_GRID);
-    work_to_grid_kernel<T><<<rows_grid(c.N + 1, c.N + 1), 256, 0, c.stream>>>(
-        c.N, W, nullptr, rhs_grid);
-    KFBI_CUDA_TRY(cudaGetLastError());
-  }
-  KFBI_TRY(box(c, precision, W, W));
-  if (v_grid) {
-    prof_count(c, ST_GRID);
-    work_to_grid_kernel<T><<<rows_grid(c.N + 1, c.N + 1), 256, 0, c.stream>>>(
-        c.N, W, nullptr, v_grid);
-    KFBI_CUDA_TRY(cudaGetLastError());
-  }
-  if (out) KFBI_TRY(interp<T>(c, W, dens, nullptr, f_ctrl, out));
-  return KFBI_OK;
-}
-
-static kfbi_status interface_solve_refined(Ctx& c, const double* dens, const double* f_grid,
-                                           const double* f_ctrl, double* rhs_grid,
-                                           double* v_grid, double* out, const uint8_t* mask) {
-  KFBI_TRY(dense_rhs64(c, dens, f_grid, f_ctrl));
+// refined FP32 solve of the FP64 right-hand side in V64, split into an exact pair
+static kfbi_status refined_dense(Ctx& c, int steps) {
   const long n = (long)c.N * c.N;
-  if (rhs_grid) {
-    prof_count(c, ST_GRID);
-    work_to_grid_kernel<double><<<rows_grid(c.N + 1, c.N + 1), 256, 0, c.stream>>>(
-        c.N, c.V64, nullptr, rhs_grid);
-    KFBI_CUDA_TRY(cudaGetLastError());
-  }
   prof_count(c, ST_GRID);
-  round_kernel<<<gs_blocks(n), 256, 0, c.stream>>>(n, c.V64, c.W32);
+  split_kernel<<<gs_blocks(n), 256, 0, c.stream>>>(n, c.V64, c.H32, c.D32);
   KFBI_CUDA_TRY(cudaGetLastError());
-  int which = 0;
-  KFBI_TRY(refined_solve(c, c.V64, c.W32, &which, c.refine_steps));
-  if (v_grid) {
-    prof_count(c, ST_GRID);
-    refine_out_kernel<<<rows_grid(c.N + 1, c.N + 1), 256, 0, c.stream>>>(
-        c.N, c.X64[which], c.V32, mask, v_grid);
-    KFBI_CUDA_TRY(cudaGetLastError());
-  }
-  if (out) KFBI_TRY(interp_refined(c, which, dens, nullptr, f_ctrl, out));
-  return KFBI_OK;
+  return refined_solve(c, c.H32, c.H32, c.D32, steps);
 }
 
 kfbi_status interface_solve(Ctx& c, int precision, const double* dens, const double* f_grid,
                             const double* f_ctrl, double* rhs_grid, double* v_grid,
                             double* out) {
-  if (precision == KFBI_FP64)
-    return interface_solve_t<double>(c, precision, c.V64, dens, f_grid, f_ctrl, rhs_grid, v_grid,
-                                     out);
-  if (precision == KFBI_FP32_REFINED)
-    return interface_solve_refined(c, dens, f_grid, f_ctrl, rhs_grid, v_grid, out, nullptr);
-  return interface_solve_t<float>(c, precision, c.V32, dens, f_grid, f_ctrl, rhs_grid, v_grid,
-                                  out);
+  const int steps = refine_steps_of(precision);
+  if (precision == KFBI_FP64 || steps > 0) {
+    KFBI_TRY(dense_rhs64(c, dens, f_grid, f_ctrl));
+    if (rhs_grid) KFBI_TRY(to_grid<double>(c, c.V64, nullptr, nullptr, nullptr, rhs_grid));
+    if (precision == KFBI_FP64) {
+      KFBI_TRY(box_solve_f64(c, c.V64, c.V64));
+      if (v_grid) KFBI_TRY(to_grid<double>(c, c.V64, nullptr, nullptr, nullptr, v_grid));
+      if (out) KFBI_TRY(interp<double>(c, c.V64, nullptr, nullptr, dens, nullptr, f_ctrl, out));
+      return KFBI_OK;
+    }
+    KFBI_TRY(refined_dense(c, steps));
+    const float* v3 = steps > 1 ? c.T32 : nullptr;
+    if (v_grid) KFBI_TRY(to_grid<float>(c, c.V32, c.U32, v3, nullptr, v_grid));
+    if (out) KFBI_TRY(interp<float>(c, c.V32, c.U32, v3, dens, nullptr, f_ctrl, out));
+    return KFBI_OK;
+  }
+  // plain FP32
+  float* W = c.V32;
+  prof_count(c, ST_GRID);
+  rhs_dense_kernel<float><<<rows_grid(c.N, c.N), 256, 0, c.stream>>>(c.N, f_grid, c.inside, W);
+  KFBI_CUDA_TRY(cudaGetLastError());
+  KFBI_TRY(correct<float>(c, dens, nullptr, f_ctrl, W, 1));
+  if (rhs_grid) KFBI_TRY(to_grid<float>(c, W, nullptr, nullptr, nullptr, rhs_grid));
+  KFBI_TRY(box_solve_f32(c, W, W));
+  if (v_grid) KFBI_TRY(to_grid<float>(c, W, nullptr, nullptr, nullptr, v_grid));
+  if (out) KFBI_TRY(interp<float>(c, W, nullptr, nullptr, dens, nullptr, f_ctrl, out));
+  return KFBI_OK;
 }
 
 // u on the grid: inside nodes of the combined solve (Phi = phi, F = f~), zero elsewhere
 kfbi_status combined_u(Ctx& c, int precision, const double* dens, const double* f_grid,
                        const double* f_ctrl, double* u_grid) {
-  if (precision != KFBI_FP64)
-    return interface_solve_refined(c, dens, f_grid, f_ctrl, nullptr, u_grid, nullptr, c.inside);
-  double* W = c.V64;
   KFBI_TRY(dense_rhs64(c, dens, f_grid, f_ctrl));
-  KFBI_TRY(box_solve_f64(c, W, W));
-  prof_count(c, ST_GRID);
-  work_to_grid_kernel<double><<<rows_grid(c.N + 1, c.N + 1), 256, 0, c.stream>>>(
-      c.N, W, c.inside, u_grid);
-  KFBI_CUDA_TRY(cudaGetLastError());
-  return KFBI_OK;
-}
-
-template <typename T>
-static kfbi_status box_grid_t(Ctx& c, int precision, T* W, const double* b_grid, double* v_grid) {
-  prof_count(c, ST_GRID);
-  grid_to_work_kernel<T><<<rows_grid(c.N, c.N), 256, 0, c.stream>>>(c.N, b_grid, W);
-  KFBI_CUDA_TRY(cudaGetLastError());
-  KFBI_TRY(box(c, precision, W, W));
-  prof_count(c, ST_GRID);
-  work_to_grid_kernel<T><<<rows_grid(c.N + 1, c.N + 1), 256, 0, c.stream>>>(
-      c.N, W, nullptr, v_grid);
-  KFBI_CUDA_TRY(cudaGetLastError());
-  return KFBI_OK;
+  if (precision == KFBI_FP64) {
+    KFBI_TRY(box_solve_f64(c, c.V64, c.V64));
+    return to_grid<double>(c, c.V64, nullptr, nullptr, c.inside, u_grid);
+  }
+  const int steps = refine_steps_of(precision) > 0 ? refine_steps_of(precision) : 1;
+  KFBI_TRY(refined_dense(c, steps));
+  return to_grid<float>(c, c.V32, c.U32, steps > 1 ? c.T32 : nullptr, c.inside, u_grid);
 }
 
 kfbi_status box_solve_grid(Ctx& c, int precision, const double* b_grid, double* v_grid) {
-  if (precision == KFBI_FP64) return box_grid_t<double>(c, precision, c.V64, b_grid, v_grid);
-  if (precision == KFBI_FP32_REFINED) {
-    const long n = (long)c.N * c.N;
-    prof_count(c, ST_GRID, 2);
-    grid_to_work_kernel<double><<<rows_grid(c.N, c.N), 256, 0, c.stream>>>(c.N, b_grid, c.V64);
-    round_kernel<<<gs_blocks(n), 256, 0, c.stream>>>(n, c.V64, c.W32);
-    KFBI_CUDA_TRY(cudaGetLastError());
-    int which = 0;
-    KFBI_TRY(refined_solve(c, c.V64, c.W32, &which, c.refine_steps));
+  const int steps = refine_steps_of(precision);
+  if (precision == KFBI_FP64 || steps > 0) {
     prof_count(c, ST_GRID);
-    refine_out_kernel<<<rows_grid(c.N + 1, c.N + 1), 256, 0, c.stream>>>(
-        c.N, c.X64[which], c.V32, nullptr, v_grid);
+    grid_to_work_kernel<double><<<rows_grid(c.N, c.N), 256, 0, c.stream>>>(c.N, b_grid, c.V64);
     KFBI_CUDA_TRY(cudaGetLastError());
-    return KFBI_OK;
+    if (precision == KFBI_FP64) {
+      KFBI_TRY(box_solve_f64(c, c.V64, c.V64));
+      return to_grid<double>(c, c.V64, nullptr, nullptr, nullptr, v_grid);
+    }
+    KFBI_TRY(refined_dense(c, steps));
+    return to_grid<float>(c, c.V32, c.U32, steps > 1 ? c.T32 : nullptr, nullptr, v_grid);
   }
-  return box_grid_t<float>(c, precision, c.V32, b_grid, v_grid);
+  prof_count(c, ST_GRID);
+  grid_to_work_kernel<float><<<rows_grid(c.N, c.N), 256, 0, c.stream>>>(c.N, b_grid, c.V32);
+  KFBI_CUDA_TRY(cudaGetLastError());
+  KFBI_TRY(box_solve_f32(c, c.V32, c.V32));
+  return to_grid<float>(c, c.V32, nullptr, nullptr, nullptr, v_grid);
 }
 
 __global__ void copy_mask_kernel(long n, const uint8_t* in, uint8_t* out) {

@@ -151,8 +151,10 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.B64, sizeof(double) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.V64, sizeof(double) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.W32, sizeof(float) * grid));
-  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.X64[0], sizeof(double) * grid));
-  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.X64[1], sizeof(double) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.U32, sizeof(float) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.T32, sizeof(float) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.H32, sizeof(float) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.D32, sizeof(float) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.scal, sizeof(double) * 16));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.vecs, sizeof(double) * 8 * M));
   if (cudaMallocHost((void**)&c.h_pinned, sizeof(double) * 16) != cudaSuccess) {
@@ -161,6 +163,8 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
     return KFBI_ERR_NOMEM;
   }
   SETUP_TRY(kfbi::init_box_tables(c));
+  SETUP_TRY(kfbi::autotune_f32(c));
+  SETUP_TRY(kfbi::autotune_f64(c));
   SETUP_TRY(kfbi::setup_geometry(c));
   SETUP_TRY(kfbi::alloc_gmres(c, c.opt.gmres_m));
   if (cudaStreamSynchronize(c.stream) != cudaSuccess) {

@@ -159,7 +159,7 @@ kfbi_status alloc_gmres(Ctx& c, int m) {
 }
 
 static kfbi_status apply_K(Ctx& c, int precision, const double* x, double* y, Counters& cnt) {
-  if (precision == KFBI_MIXED_FP32) ++cnt.applies32; else ++cnt.applies64;
+  if (precision == KFBI_MIXED_FP32) ++cnt.applies32; else ++cnt.applies64;   // FP64-accurate
   return apply_potential(c, Layer::Double, precision, x, y);
 }
 
@@ -170,15 +170,22 @@ static kfbi_status read_scal(Ctx& c, int n) {
   return KFBI_OK;
 }
 
-// GMRES(m) on K_D for rhs, x in/out (x_zero: start from 0), FP64 Arnoldi.  The matvec of
-// each Arnoldi step runs in prec_hi while the residual estimate is above relax_abs and in
-// prec_lo below it (inexact Krylov relaxation: a matvec may be as inaccurate as
-// tol / ||r_j|| relative once the residual is small).  Every cycle ends with the true
-// residual formed with the FP64-accurate apply prec_true (an iterative-refinement step).
-// Stops when the residual is <= tol_abs; *res_out = last true residual norm.
-static kfbi_status gmres_run(Ctx& c, int prec_hi, int prec_lo, double relax_abs, int prec_true,
-                             const double* rhs, double* x, bool x_zero, double tol_abs,
-                             int max_cycles, Counters& cnt, double* res_out, int* cycles_out) {
+// Matvec precision of an Arnoldi step by the current residual estimate (inexact Krylov
+// relaxation: once the residual is small a matvec may be as inaccurate as tol / ||r||
+// relative).  tier[0] while est > th[0], tier[1] while est > th[1], tier[2] below.
+struct Relax {
+  int tier[3];
+  double th[2];
+  int pick(double est) const { return est > th[0] ? tier[0] : (est > th[1] ? tier[1] : tier[2]); }
+};
+
+// GMRES(m) on K_D for rhs, x in/out (x_zero: start from 0), FP64 Arnoldi, matvec
+// precision chosen per step by `relax`.  Every cycle ends with the true residual formed
+// with the FP64-accurate apply prec_true (an iterative-refinement step).  Stops when the
+// residual is <= tol_abs; *res_out = last true residual norm.
+static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const double* rhs,
+                             double* x, bool x_zero, double tol_abs, int max_cycles,
+                             Counters& cnt, double* res_out, int* cycles_out) {
   const int M = c.M, m = c.gm_m;
   cudaStream_t st = c.stream;
   double* r = c.vecs;            // residual
@@ -206,7 +213,7 @@ static kfbi_status gmres_run(Ctx& c, int prec_hi, int prec_lo, double relax_abs,
     int k = 0;
     double est = beta;
     for (int j = 0; j < m; ++j) {
-      const int prec = est > relax_abs ? prec_hi : prec_lo;
+      const int prec = relax.pick(est);
       KFBI_TRY(apply_K(c, prec, c.basis + (size_t)j * M, w, cnt));
       ++cnt.iters;
       prof_count(c, ST_KRYLOV, 5);
@@ -264,13 +271,17 @@ kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const 
   double res = 0.0;
   int cycles = 0;
   if (c.opt.precision == KFBI_MIXED_FP32) {
-    // one-step refined applies while the residual is large, plain FP32 applies once it is
-    // below tol / inner_tol (inner_tol: assumed relative accuracy of an FP32 apply)
-    KFBI_TRY(gmres_run(c, PREC_REFINED1, KFBI_MIXED_FP32, tol_abs / c.opt.inner_tol, acc, ghat,
-                       phi, true, tol_abs, c.opt.max_restarts + 1, cnt, &res, &cycles));
+    // twice-refined applies (about 1e-13) while the residual is above tol / 1e-9,
+    // once-refined (about 1e-10 at the largest grids) down to tol / inner_tol, plain FP32
+    // below (inner_tol: the assumed relative accuracy of an FP32 apply)
+    const Relax relax{{KFBI_FP32_REFINED, KFBI_FP32_REFINED_ONCE, KFBI_MIXED_FP32},
+                      {tol_abs / 1e-9, tol_abs / c.opt.inner_tol}};
+    KFBI_TRY(gmres_run(c, relax, acc, ghat, phi, true, tol_abs, c.opt.max_restarts + 1, cnt,
+                       &res, &cycles));
   } else {
-    KFBI_TRY(gmres_run(c, acc, acc, 0.0, acc, ghat, phi, true, tol_abs, c.opt.max_restarts + 1,
-                       cnt, &res, &cycles));
+    const Relax relax{{acc, acc, acc}, {0.0, 0.0}};
+    KFBI_TRY(gmres_run(c, relax, acc, ghat, phi, true, tol_abs, c.opt.max_restarts + 1, cnt,
+                       &res, &cycles));
   }
   // u = W phi + Y f on inside nodes
   if (u_grid) {

@@ -117,10 +117,13 @@ struct Ctx {
   float* B32 = nullptr;  float* V32 = nullptr;     // sparse RHS (irregular entries only), work
   double* B64 = nullptr; double* V64 = nullptr;
   float* W32 = nullptr;                             // refinement residual (FP32)
-  double* X64[2] = {nullptr, nullptr};              // refinement iterates (FP64, ping-pong)
-  int refine_steps = 2;
+  float* U32 = nullptr;                             // second FP32 solve of a refined solve
+  float* T32 = nullptr;                             // third FP32 solve (two refinement steps)
+  float* H32 = nullptr;                             // dense right-hand side, FP32 high part
+  float* D32 = nullptr;                             // dense right-hand side, FP32 low part
   BoxTables<float> t32{};
   BoxTables<double> t64{};
+  int cols_variant[2] = {0, 0};                     // column-pass variant per precision (autotuned)
 
   // GMRES workspace (FP64)
   int gm_m = 0;
@@ -157,6 +160,8 @@ kfbi_status alloc_bytes(Ctx& c, void** p, size_t bytes);
 kfbi_status box_solve_f32(Ctx& c, const float* rhs, float* work);
 kfbi_status box_solve_f64(Ctx& c, const double* rhs, double* work);
 kfbi_status init_box_tables(Ctx& c);
+kfbi_status autotune_f32(Ctx& c);   // column-pass variant per precision, on scratch grids
+kfbi_status autotune_f64(Ctx& c);
 
 // apply stages (apply2d.cu)
 enum class Layer { Double, Single };
@@ -168,9 +173,10 @@ kfbi_status box_solve_grid(Ctx& c, int precision, const double* b_grid, double* 
 kfbi_status inside_mask(Ctx& c, uint8_t* mask);
 kfbi_status combined_u(Ctx& c, int precision, const double* dens, const double* f_grid,
                        const double* f_ctrl, double* u_grid);
-// internal precision code: FP32 transforms with one refinement step (about 1e-11)
-constexpr int PREC_REFINED1 = 16;
-inline bool valid_precision(int p) { return p == KFBI_FP64 || p == KFBI_MIXED_FP32 || p == KFBI_FP32_REFINED; }
+inline bool valid_precision(int p) {
+  return p == KFBI_FP64 || p == KFBI_MIXED_FP32 || p == KFBI_FP32_REFINED ||
+         p == KFBI_FP32_REFINED_ONCE;
+}
 
 // solver (gmres.cu)
 kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const double* g_ctrl,

@@ -108,9 +108,11 @@ def test_double_layer_apply_parity(case):
     g64 = ctx.apply_layer_potential(phi, K.KFBI_DOUBLE_LAYER, K.KFBI_FP64).cpu().numpy()
     g32 = ctx.apply_layer_potential(phi, K.KFBI_DOUBLE_LAYER, K.KFBI_MIXED_FP32).cpu().numpy()
     gr = ctx.apply_layer_potential(phi, K.KFBI_DOUBLE_LAYER, K.KFBI_FP32_REFINED).cpu().numpy()
+    g1 = ctx.apply_layer_potential(phi, K.KFBI_DOUBLE_LAYER, K.KFBI_FP32_REFINED_ONCE).cpu().numpy()
     assert rel(g64, ref) < 1e-11
     assert rel(g32, ref) < 2e-5
     assert rel(gr, ref) < 1e-11
+    assert rel(g1, ref) < 1e-10
     # repeated applies are bit-identical
     again = ctx.apply_layer_potential(phi, K.KFBI_DOUBLE_LAYER, K.KFBI_FP64).cpu().numpy()
     assert np.array_equal(again, g64)
@@ -209,5 +211,6 @@ def test_full_size_apply_parity(N):
     ref = O.apply_double_layer(geom, phi)
     assert rel(ctx.apply_layer_potential(phi, 0, K.KFBI_FP64).cpu().numpy(), ref) < 1e-11
     assert rel(ctx.apply_layer_potential(phi, 0, K.KFBI_FP32_REFINED).cpu().numpy(), ref) < 1e-11
+    assert rel(ctx.apply_layer_potential(phi, 0, K.KFBI_FP32_REFINED_ONCE).cpu().numpy(), ref) < 1e-10
     assert rel(ctx.apply_layer_potential(phi, 0, K.KFBI_MIXED_FP32).cpu().numpy(), ref) < 1e-4
     ctx.close()
