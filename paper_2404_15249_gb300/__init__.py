@@ -54,10 +54,13 @@ class SolveInfo(ctypes.Structure):
 class CtxInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("n_crossings_x", ctypes.c_int),
                 ("n_crossings_y", ctypes.c_int), ("n_irregular", ctypes.c_int),
-                ("n_inside", ctypes.c_int), ("device_bytes", ctypes.c_int64)]
+                ("n_inside", ctypes.c_int), ("device_bytes", ctypes.c_int64),
+                ("dst_variant", ctypes.c_int * 4)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["dst_variant"] = list(self.dst_variant)
+        return d
 
 
 NSTAGES = 16

@@ -258,6 +258,10 @@ kfbi_status kfbi_get_info(kfbi_ctx ctx, kfbi_ctx_info* info) {
   info->n_irregular = c.nirr;
   info->n_inside = c.n_inside;
   info->device_bytes = c.bytes + (int64_t)sizeof(double) * ((int64_t)(c.gm_m + 1) * c.M);
+  info->dst_variant[0] = c.rows_variant[0];
+  info->dst_variant[1] = c.cols_variant[0];
+  info->dst_variant[2] = c.rows_variant[1];
+  info->dst_variant[3] = c.cols_variant[1];
   return KFBI_OK;
 }
 

@@ -16,11 +16,14 @@
 // DST-I of a line through one complex FFT of length N: z_m = u_{2m} + i u_{2m+1} packs the
 // odd extension u of the line (u_{2N-j} = -x_j); with Z = FFT_N(z), Z_k = a + ib and
 // Z_{N-k} = c + id,  X_k = [-(b - d) + cos(pi k/N)(a - c) + sin(pi k/N)(b + d)] / 4.
-// The FFT is a mixed-radix (16, 8, 4, 2, 3) Stockham transform in shared memory with the
-// plan fixed at compile time for each supported N, so every shared-memory offset is a
-// per-thread base plus a constant.  The first stage reads the raw line and forms the
-// packed odd extension on the fly; the last stage keeps its outputs in registers and the
-// post-processing pairs them with the partner value Z_{N-k} from shared memory.
+// The FFT is a mixed-radix (16, 8, 4, 2, 3) Stockham transform with the plan fixed at
+// compile time for each supported N (every shared-memory offset is a per-thread base plus
+// a constant).  Stage 0 reads the raw line (global memory for rows, shared memory for
+// columns) and forms the packed odd extension on the fly; later stages ping-pong between
+// two padded shared-memory buffers with one barrier per stage; twiddles come from
+// per-stage tables laid out [r][j mod Ns] so a warp's loads are contiguous; the last
+// stage keeps its outputs in registers and the post-processing pairs them with the
+// partner value Z_{N-k} from shared memory.
 #pragma once
 
 #include "kfbi_internal.cuh"
@@ -129,95 +132,107 @@ struct CPlan {
   int ept, tpl, nst;
   int radix[8];
   int ns[8];      // product of the radices of the earlier stages
+  int twoff[8];   // offset of the stage's twiddle table (stages >= 1)
+  int twtotal;    // total twiddle-table entries
 };
 
-__host__ __device__ constexpr CPlan cplan(int N) {
+// EPT values per thread per stage: 16 or 8 for N = 2^a (radices 16/8/4/2), 24 or 12 for
+// N = 3 * 2^a (radices 8/4/2 then 3).  Every radix divides EPT.
+__host__ __device__ constexpr int default_ept(int N) { return N % 3 == 0 ? 24 : 16; }
+
+__host__ __device__ constexpr CPlan cplan(int N, int EPT) {
   CPlan p{};
-  if (N % 3 == 0) {
-    p.ept = 24;
-    int r = N / 3;
-    while (r % 8 == 0 && r > 8) { p.radix[p.nst++] = 8; r /= 8; }
-    if (r > 1) p.radix[p.nst++] = r;
-    p.radix[p.nst++] = 3;
-  } else {
-    p.ept = 16;
-    int r = N;
-    while (r % 16 == 0) { p.radix[p.nst++] = 16; r /= 16; }
-    if (r > 1) p.radix[p.nst++] = r;
-  }
+  p.ept = EPT;
+  const int big = (EPT == 16 || EPT == 24) ? (EPT == 16 ? 16 : 8) : (EPT == 8 ? 8 : 4);
+  int r = N % 3 == 0 ? N / 3 : N;
+  while (r % big == 0 && r > big) { p.radix[p.nst++] = big; r /= big; }
+  if (r > 1) p.radix[p.nst++] = r;
+  if (N % 3 == 0) p.radix[p.nst++] = 3;
   p.tpl = N / p.ept;
-  int ns = 1;
-  for (int s = 0; s < p.nst; ++s) { p.ns[s] = ns; ns *= p.radix[s]; }
+  int ns = 1, off = 0;
+  for (int s = 0; s < p.nst; ++s) {
+    p.ns[s] = ns;
+    p.twoff[s] = off;
+    if (s > 0) off += (p.radix[s] - 1) * ns;
+    ns *= p.radix[s];
+  }
+  p.twtotal = off;
   return p;
 }
 
 // padded shared-memory index (one spare slot per 16 complex values)
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
-__host__ __device__ constexpr int line_len(int N) { return N + N / 16 + 2; }   // complex slots per line
+__host__ __device__ constexpr int line_len(int N) { return N + N / 16 + 2; }   // complex slots
 
-// value m of the packed odd extension, read from the raw line (T[0..N], raw[N] = 0)
+// value m of the packed odd extension z_m of a line x (x_0 = 0, x_N = 0):
+// (x_{2m}, x_{2m+1}) for m < N/2, (-x_{2m'}, -x_{2m'-1}) with m' = N - m otherwise
 template <typename T, int N>
-__device__ __forceinline__ cx<T> packed(const T* raw, int m, bool upper) {
-  if (!upper) return *reinterpret_cast<const cx<T>*>(raw + 2 * m);
+__device__ __forceinline__ cx<T> packed(const T* line, int m, bool upper) {
+  if (!upper) return *reinterpret_cast<const cx<T>*>(line + 2 * m);
   const int mp = N - m;                       // 0 < mp <= N/2
-  return {-raw[2 * mp], -raw[2 * mp - 1]};
+  const T hi = (mp < N / 2) ? line[2 * mp] : T(0);
+  return {-hi, -line[2 * mp - 1]};
 }
 
-// One in-place Stockham stage S of the plan for N.  Butterfly j reads z[j + r N/R],
-// multiplies input r by W_N^{(j mod Ns) r N/(Ns R)}, writes output r to
-// z[(j - j mod Ns) R + j mod Ns + r Ns].  The first stage reads the raw line instead.
-// The last stage leaves its outputs in v (output r of butterfly q at v[q R + r]) and
-// also stores them to z.
-template <typename T, int N, int S>
-__device__ __forceinline__ void stage(cx<T>* z, int t, const cx<T>* __restrict__ tw,
-                                      cx<T>* v) {
-  constexpr CPlan P = cplan(N);
-  constexpr int R = P.radix[S], Ns = P.ns[S], NB = P.ept / R, STR = N / R;
-  if constexpr (S == 0) {
-    const T* raw = reinterpret_cast<const T*>(z);
-#pragma unroll
-    for (int q = 0; q < NB; ++q)
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        v[q * R + r] = packed<T, N>(raw, t + q * P.tpl + r * STR, 2 * r >= R);
-  } else {
-#pragma unroll
-    for (int q = 0; q < NB; ++q)
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[q * R + r] = z[pad(t + q * P.tpl + r * STR)];
-  }
-  __syncthreads();
+// Butterflies of stage S on the values v already loaded for this thread (input r of
+// butterfly q at v[q R + r], butterfly index j = t + q tpl): twiddle by the stage table
+// tws[(r - 1) Ns + j mod Ns] = W_N^{(j mod Ns) r N/(Ns R)}, DFT_R, and store output r to
+// zo[(j - j mod Ns) R + j mod Ns + r Ns].
+template <typename T, int N, int EPT, int S>
+__device__ __forceinline__ void butterflies(cx<T>* zo, int t, const cx<T>* __restrict__ stw,
+                                            cx<T>* v) {
+  constexpr CPlan P = cplan(N, EPT);
+  constexpr int R = P.radix[S], Ns = P.ns[S], NB = P.ept / R;
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int j = t + q * P.tpl;
+    const int jm = j & (Ns - 1);
     if constexpr (Ns > 1) {
-      const int jm = j & (Ns - 1);
-      const int b2 = 2 * jm * (N / (Ns * R));
+      const cx<T>* tws = stw + P.twoff[S] + jm;
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], tw[b2 * r]);
+      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], tws[(r - 1) * Ns]);
     }
     dft<T, R>(&v[q * R]);
-    const int out0 = (j & ~(Ns - 1)) * R + (j & (Ns - 1));
+    const int out0 = (j - jm) * R + jm;
 #pragma unroll
-    for (int r = 0; r < R; ++r) z[pad(out0 + r * Ns)] = v[q * R + r];
+    for (int r = 0; r < R; ++r) zo[pad(out0 + r * Ns)] = v[q * R + r];
   }
-  __syncthreads();
 }
 
-template <typename T, int N, int S = 0>
-__device__ __forceinline__ void fft(cx<T>* z, int t, const cx<T>* __restrict__ tw, cx<T>* v) {
-  constexpr CPlan P = cplan(N);
-  stage<T, N, S>(z, t, tw, v);
-  if constexpr (S + 1 < P.nst) fft<T, N, S + 1>(z, t, tw, v);
+// Stages 1..nst-1, ping-ponging between the two line buffers; stage 0 has already been
+// written to z0.  Returns with the last stage's outputs in v (output r of butterfly q at
+// v[q R + r]) and in buffer zbuf[(nst - 1) % 2]; one barrier per stage.
+template <typename T, int N, int EPT, int S>
+__device__ __forceinline__ void later_stages(cx<T>* z0, cx<T>* z1, int t,
+                                             const cx<T>* __restrict__ stw, cx<T>* v) {
+  constexpr CPlan P = cplan(N, EPT);
+  if constexpr (S < P.nst) {
+    constexpr int R = P.radix[S], NB = P.ept / R, STR = N / R;
+    // stage s writes buffer s % 2: stage S reads what stage S-1 wrote, writes the other
+    cx<T>* src = ((S - 1) % 2 == 0) ? z0 : z1;
+    cx<T>* dst = ((S - 1) % 2 == 0) ? z1 : z0;
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q * R + r] = src[pad(t + q * P.tpl + r * STR)];
+    butterflies<T, N, EPT, S>(dst, t, stw, v);
+    __syncthreads();
+    later_stages<T, N, EPT, S + 1>(z0, z1, t, stw, v);
+  }
 }
 
-// DST-I outputs held by this thread after fft(): output e = q R + r is X_k with
-// k = t + q tpl + r N/R (R the last radix), formed from v[e] = Z_k and the partner value
-// Z_{N-k} in shared memory, and handed to f(e, k, X_k).
-template <typename T, int N, typename F>
-__device__ __forceinline__ void dst_outputs(const cx<T>* z, int t, const cx<T>* __restrict__ tw,
+template <typename T, int N, int EPT>
+__device__ __forceinline__ cx<T>* last_buffer(cx<T>* z0, cx<T>* z1) {
+  return ((cplan(N, EPT).nst - 1) % 2 == 0) ? z0 : z1;
+}
+
+// DST-I outputs held by this thread after the last stage: output e = q R + r is X_k with
+// k = t + q tpl + r N/R (R the last radix), formed from v[e] = Z_k and the partner
+// Z_{N-k} read from the last stage's buffer zl, and handed to f(e, k, X_k).
+template <typename T, int N, int EPT, typename F>
+__device__ __forceinline__ void dst_outputs(const cx<T>* zl, int t, const cx<T>* __restrict__ tw,
                                             cx<T>* v, F&& f) {
-  constexpr CPlan P = cplan(N);
+  constexpr CPlan P = cplan(N, EPT);
   constexpr int R = P.radix[P.nst - 1], NB = P.ept / R, STR = N / R;
 #pragma unroll
   for (int q = 0; q < NB; ++q)
@@ -225,59 +240,68 @@ __device__ __forceinline__ void dst_outputs(const cx<T>* z, int t, const cx<T>* 
     for (int r = 0; r < R; ++r) {
       const int k = t + q * P.tpl + r * STR;
       const cx<T> a = v[q * R + r];
-      const cx<T> b = z[pad(N - k)];            // k = 0 reads a discarded slot
-      const cx<T> w = tw[k];
+      const cx<T> b = zl[pad(N - k)];           // k = 0 reads a discarded slot
+      const cx<T> w = tw[k];                    // (cos, -sin)(pi k / N)
       const T val = T(0.25) * (-(a.y - b.y) + w.x * (a.x - b.x) - w.y * (a.y + b.y));
       f(q * R + r, k, (k == 0) ? T(0) : val);
     }
 }
 
-template <typename T, int N>
+template <typename T, int N, int EPT>
 __device__ __forceinline__ int out_index(int t, int e) {
-  constexpr CPlan P = cplan(N);
+  constexpr CPlan P = cplan(N, EPT);
   constexpr int R = P.radix[P.nst - 1], STR = N / R;
   return t + (e / R) * P.tpl + (e % R) * STR;
 }
 
+// One DST-I of a line whose raw values are read by `at(i)` (i < N, at(0) = 0): stage 0 forms
+// the packed odd extension from the raw values directly, the remaining stages run in
+// shared memory, the outputs are handed to f(e, k, X_k).  Ends with a barrier-free read of
+// the last buffer; the caller synchronises before the buffers are reused.
+template <typename T, int N, int EPT, typename Raw, typename F>
+__device__ __forceinline__ void dst_line(Raw&& load_pair, cx<T>* z0, cx<T>* z1, int t,
+                                         const cx<T>* __restrict__ stw,
+                                         const cx<T>* __restrict__ tw, F&& f) {
+  constexpr CPlan P = cplan(N, EPT);
+  constexpr int R = P.radix[0], NB = P.ept / R, STR = N / R;
+  cx<T> v[P.ept];
+#pragma unroll
+  for (int q = 0; q < NB; ++q)
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[q * R + r] = load_pair(t + q * P.tpl + r * STR, 2 * r >= R);
+  butterflies<T, N, EPT, 0>(z0, t, stw, v);
+  __syncthreads();
+  later_stages<T, N, EPT, 1>(z0, z1, t, stw, v);
+  dst_outputs<T, N, EPT>(last_buffer<T, N, EPT>(z0, z1), t, tw, v, f);
+}
+
 // ---------------------------------------------------------------------------- pass 1/3
 // DST-I along every row: out[row] = scale * DST(in[row]); in may equal out.  LPC lines per
-// CTA, persistent grid-stride loop; the next row is loaded into registers while the
-// current one is transformed.
-template <typename T, int N>
-__global__ void __launch_bounds__(512) rows_kernel(const T* in, T* out,
-                                                   const cx<T>* __restrict__ tw, T scale) {
-  constexpr CPlan P = cplan(N);
-  constexpr int H = P.ept / 2;                  // pairs of the raw line per thread
+// CTA, persistent grid-stride loop.  Stage 0 reads the row straight from global memory
+// (the odd-extension mirror is address arithmetic), outputs go straight to global memory.
+template <typename T, int N, int EPT>
+__global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl : 256),
+                                  ((cplan(N, EPT).tpl > 256 && EPT >= 16) ? 1 : 2))
+    rows_kernel(const T* in, T* out, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
+                T scale) {
+  constexpr CPlan P = cplan(N, EPT);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lpc = blockDim.x / P.tpl;
   const int line = threadIdx.x / P.tpl, t = threadIdx.x - line * P.tpl;
-  cx<T>* z = reinterpret_cast<cx<T>*>(smem_raw) + line * line_len(N);
+  cx<T>* z0 = reinterpret_cast<cx<T>*>(smem_raw) + line * 2 * line_len(N);
+  cx<T>* z1 = z0 + line_len(N);
   const int step = gridDim.x * lpc;
-  int row = blockIdx.x * lpc + line;
-  cx<T> pre[H];
-  if (row < N) {
-    const cx<T>* src = reinterpret_cast<const cx<T>*>(in + (size_t)row * N);
-#pragma unroll
-    for (int u = 0; u < H; ++u) pre[u] = src[t + u * P.tpl];
-  }
-  cx<T> v[P.ept];
-  for (int row0 = blockIdx.x * lpc; row0 < N; row0 += step, row += step) {
+  for (int row0 = blockIdx.x * lpc; row0 < N; row0 += step) {
+    const int row = row0 + line;
     const bool active = row < N;
-#pragma unroll
-    for (int u = 0; u < H; ++u) z[t + u * P.tpl] = active ? pre[u] : cx<T>{T(0), T(0)};
-    if (t == 0) reinterpret_cast<T*>(z)[N] = T(0);
-    const int nrow = row + step;
-    if (nrow < N) {
-      const cx<T>* src = reinterpret_cast<const cx<T>*>(in + (size_t)nrow * N);
-#pragma unroll
-      for (int u = 0; u < H; ++u) pre[u] = src[t + u * P.tpl];
-    }
-    __syncthreads();
-    fft<T, N>(z, t, tw, v);
+    const T* src = in + (size_t)(active ? row : 0) * N;
     T* dst = out + (size_t)row * N;
-    dst_outputs<T, N>(z, t, tw, v, [&](int, int k, T x) {
-      if (active) dst[k] = x * scale;
-    });
+    dst_line<T, N, EPT>([&](int m, bool upper) {
+                          return active ? packed<T, N>(src, m, upper) : cx<T>{T(0), T(0)};
+                        },
+                        z0, z1, t, stw, tw, [&](int, int k, T x) {
+                          if (active) dst[k] = x * scale;
+                        });
     __syncthreads();
   }
 }
@@ -296,43 +320,50 @@ __device__ __forceinline__ double recip(double d) {
   return r;
 }
 
+// shared memory of one column line: raw values (N + 2 reals) and two FFT buffers
+template <typename T, int N>
+__host__ __device__ constexpr size_t col_line_bytes() {
+  return ((size_t)(N + 2) * sizeof(T) + 15) / 16 * 16 + 2 * (size_t)line_len(N) * 2 * sizeof(T);
+}
+
 // column tile width: largest power of two <= 32 dividing N with L * tpl threads within
 // the bound and L line buffers plus the staging tile within 220 KB of shared memory
-template <typename T, int N, int MAXT>
+template <typename T, int N, int EPT, int MAXT>
 __host__ __device__ constexpr int cols_L() {
-  constexpr CPlan P = cplan(N);
+  constexpr CPlan P = cplan(N, EPT);
   int L = 1;
   while (L < 32 && N % (2 * L) == 0 && 2 * L * P.tpl <= MAXT &&
-         (size_t)(2 * L) * (line_len(N) * 2 * sizeof(T) + N * sizeof(T)) <= 220 * 1024)
+         (size_t)(2 * L) * (col_line_bytes<T, N>() + N * sizeof(T)) <= 220 * 1024)
     L *= 2;
   return L;
 }
-
 
 // ---------------------------------------------------------------------------- pass 2
 // L consecutive columns (x-modes k) per CTA: DST-I along y, multiply by
 // scale / (lam[k] + lam[l] - kappa^2), DST-I along y again.  The next column tile is
 // copied into a shared-memory staging area with cp.async while the current one is
 // transformed.
-template <typename T, int N, int MAXT>
-__global__ void __launch_bounds__(MAXT) cols_kernel(T* V, const cx<T>* __restrict__ tw,
-                                                               const T* __restrict__ lam,
-                                                               T kappa2, T scale) {
-  constexpr CPlan P = cplan(N);
-  constexpr int L = cols_L<T, N, MAXT>();
+template <typename T, int N, int EPT, int MAXT>
+__global__ void __launch_bounds__(MAXT, (MAXT <= 256 ? 2 : 1)) cols_kernel(T* V, const cx<T>* __restrict__ stw,
+                                                    const cx<T>* __restrict__ tw,
+                                                    const T* __restrict__ lam, T kappa2, T scale) {
+  constexpr CPlan P = cplan(N, EPT);
+  constexpr int L = cols_L<T, N, EPT, MAXT>();
   constexpr int CH = (L * (int)sizeof(T) >= 16) ? L * (int)sizeof(T) / 16 : 1;
   constexpr int W = L / CH;
   constexpr int VB = W * (int)sizeof(T);
   constexpr int NCH = N * CH;                   // chunks per tile
-  constexpr int LL = line_len(N);
+  constexpr size_t LB = col_line_bytes<T, N>();
   typedef typename RawVec<VB>::type Raw;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* lines = reinterpret_cast<cx<T>*>(smem_raw);
-  Raw* stage_buf = reinterpret_cast<Raw*>(lines + L * LL);     // N rows x L values
+  Raw* stage_buf = reinterpret_cast<Raw*>(smem_raw + L * LB);   // N rows x L values
   const int line = threadIdx.x / P.tpl, t = threadIdx.x - line * P.tpl;
-  cx<T>* z = lines + line * LL;
-  T* raw = reinterpret_cast<T*>(z);
+  unsigned char* lb = smem_raw + line * LB;
+  T* raw = reinterpret_cast<T*>(lb);
+  cx<T>* z0 = reinterpret_cast<cx<T>*>(lb + ((size_t)(N + 2) * sizeof(T) + 15) / 16 * 16);
+  cx<T>* z1 = z0 + line_len(N);
   const int nthr = blockDim.x;
+  auto raw_of = [&](int c) { return reinterpret_cast<T*>(smem_raw + c * LB); };
 
   auto prefetch = [&](int col0) {
     for (int g = threadIdx.x; g < NCH; g += nthr) {
@@ -351,7 +382,6 @@ __global__ void __launch_bounds__(MAXT) cols_kernel(T* V, const cx<T>* __restric
 
   int c0 = blockIdx.x * L;
   if (c0 < N) prefetch(c0);
-  cx<T> v[P.ept];
   for (; c0 < N; c0 += gridDim.x * L) {
     asm volatile("cp.async.wait_group 0;\n" ::);
     __syncthreads();
@@ -361,40 +391,53 @@ __global__ void __launch_bounds__(MAXT) cols_kernel(T* V, const cx<T>* __restric
       const Raw pk = stage_buf[g];
       const T* vals = reinterpret_cast<const T*>(&pk);
 #pragma unroll
-      for (int w = 0; w < W; ++w) reinterpret_cast<T*>(lines + (cc * W + w) * LL)[r] = vals[w];
+      for (int w = 0; w < W; ++w) raw_of(cc * W + w)[r] = vals[w];
     }
-    if (t == 0) raw[N] = T(0);
     __syncthreads();
     if (c0 + gridDim.x * L < N) prefetch(c0 + gridDim.x * L);
-    fft<T, N>(z, t, tw, v);
     const int k = c0 + line;
     const T lk = lam[k] - kappa2;
-    // each output only needs its own v[e] and a partner from shared memory, so the
-    // result can overwrite v[e].x
-    dst_outputs<T, N>(z, t, tw, v, [&](int e, int l, T x) {
-      v[e].x = (k == 0 || l == 0) ? T(0) : x * scale * recip(lk + lam[l]);
-    });
-    __syncthreads();
+    T X[P.ept];
+    // forward transform with the spectral division; results replace the raw line (the
+    // raw values were consumed by stage 0 before its barrier)
+    dst_line<T, N, EPT>([&](int m, bool upper) { return packed<T, N>(raw, m, upper); }, z0, z1,
+                        t, stw, tw, [&](int e, int l, T x) {
+                          X[e] = (k == 0 || l == 0) ? T(0) : x * scale * recip(lk + lam[l]);
+                        });
 #pragma unroll
-    for (int e = 0; e < P.ept; ++e) raw[out_index<T, N>(t, e)] = v[e].x;
-    if (t == 0) raw[N] = T(0);
+    for (int e = 0; e < P.ept; ++e) raw[out_index<T, N, EPT>(t, e)] = X[e];
     __syncthreads();
-    fft<T, N>(z, t, tw, v);
-    dst_outputs<T, N>(z, t, tw, v, [&](int e, int, T x) { v[e].x = x; });
-    __syncthreads();
+    dst_line<T, N, EPT>([&](int m, bool upper) { return packed<T, N>(raw, m, upper); }, z0, z1,
+                        t, stw, tw, [&](int e, int, T x) { X[e] = x; });
+    // stage 0 of the second transform consumed raw before a barrier: safe to overwrite
 #pragma unroll
-    for (int e = 0; e < P.ept; ++e) raw[out_index<T, N>(t, e)] = v[e].x;
+    for (int e = 0; e < P.ept; ++e) raw[out_index<T, N, EPT>(t, e)] = X[e];
     __syncthreads();
     for (int g = threadIdx.x; g < NCH; g += nthr) {
       const int r = g / CH, cc = g - r * CH;
       Raw pk;
       T* vals = reinterpret_cast<T*>(&pk);
 #pragma unroll
-      for (int w = 0; w < W; ++w) vals[w] = reinterpret_cast<const T*>(lines + (cc * W + w) * LL)[r];
+      for (int w = 0; w < W; ++w) vals[w] = raw_of(cc * W + w)[r];
       *reinterpret_cast<Raw*>(V + (size_t)r * N + c0 + cc * W) = pk;
     }
   }
   asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// ---------------------------------------------------------------------------- tables
+// stage twiddles of the plan (N, EPT): entry twoff[s] + (r - 1) Ns + jm holds
+// W_N^{jm r N/(Ns R)}, written from the base table tw[i] = e^{-i pi i/N}
+template <typename T, int N, int EPT>
+__global__ void stage_twiddles_kernel(const cx<T>* __restrict__ tw, cx<T>* __restrict__ stw) {
+  constexpr CPlan P = cplan(N, EPT);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= P.twtotal) return;
+  int s = 1;
+  while (s + 1 < P.nst && e >= P.twoff[s + 1]) ++s;
+  const int loc = e - P.twoff[s], Ns = P.ns[s], R = P.radix[s];
+  const int r = loc / Ns + 1, jm = loc - (r - 1) * Ns;
+  stw[e] = tw[2 * ((jm * r * (N / (Ns * R))) % N)];
 }
 
 // ---------------------------------------------------------------------------- launch
@@ -409,98 +452,154 @@ inline int sm_count() {
   return n;
 }
 
-template <typename T, int N>
+// per-plan stage-twiddle tables, built on first use for this context and precision
+template <typename T, int N, int EPT>
+kfbi_status stage_table(Ctx& c, const cx<T>* tw, const cx<T>** out) {
+  constexpr CPlan P = cplan(N, EPT);
+  const int slot = (sizeof(T) == 8 ? 2 : 0) + (EPT == default_ept(N) ? 0 : 1);
+  if (!c.stw[slot]) {
+    KFBI_TRY(alloc_bytes(c, &c.stw[slot], sizeof(cx<T>) * (P.twtotal > 0 ? P.twtotal : 1)));
+    if (P.twtotal > 0) {
+      prof_count(c, ST_SETUP);
+      stage_twiddles_kernel<T, N, EPT><<<(P.twtotal + 255) / 256, 256, 0, c.stream>>>(
+          tw, reinterpret_cast<cx<T>*>(c.stw[slot]));
+      KFBI_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  *out = reinterpret_cast<const cx<T>*>(c.stw[slot]);
+  return KFBI_OK;
+}
+
+template <typename T, int N, int EPT>
 kfbi_status launch_rows(Ctx& c, const T* in, T* out, const cx<T>* tw, T scale) {
-  constexpr CPlan P = cplan(N);
+  constexpr CPlan P = cplan(N, EPT);
+  const cx<T>* stw = nullptr;
+  KFBI_TRY((stage_table<T, N, EPT>(c, tw, &stw)));
   const int lpc = P.tpl >= 256 ? 1 : 256 / P.tpl;
   const int threads = lpc * P.tpl;
-  const size_t smem = (size_t)lpc * line_len(N) * sizeof(cx<T>);
+  const size_t smem = (size_t)lpc * 2 * line_len(N) * sizeof(cx<T>);
   static bool attr = false;
   if (!attr) {
-    KFBI_CUDA_TRY(cudaFuncSetAttribute(rows_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       227 * 1024));
+    KFBI_CUDA_TRY(cudaFuncSetAttribute(rows_kernel<T, N, EPT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     attr = true;
   }
   int per_sm = 0;
-  KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_kernel<T, N>, threads, smem));
+  KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_kernel<T, N, EPT>,
+                                                              threads, smem));
   if (per_sm < 1) per_sm = 1;
   int blocks = (N + lpc - 1) / lpc;
   blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
   const int pr = prof_begin(c, sizeof(T) == 4 ? ST_ROWS32 : ST_ROWS64);
-  rows_kernel<T, N><<<blocks, threads, smem, c.stream>>>(in, out, tw, scale);
+  rows_kernel<T, N, EPT><<<blocks, threads, smem, c.stream>>>(in, out, stw, tw, scale);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
 }
 
-template <typename T, int N, int MAXT>
+template <typename T, int N, int EPT, int MAXT>
 kfbi_status launch_cols(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
-  constexpr CPlan P = cplan(N);
-  constexpr int L = cols_L<T, N, MAXT>();
+  constexpr CPlan P = cplan(N, EPT);
+  constexpr int L = cols_L<T, N, EPT, MAXT>();
+  const cx<T>* stw = nullptr;
+  KFBI_TRY((stage_table<T, N, EPT>(c, tw, &stw)));
   const int threads = L * P.tpl;
-  const size_t smem = (size_t)L * line_len(N) * sizeof(cx<T>) + (size_t)N * L * sizeof(T);
+  const size_t smem = (size_t)L * col_line_bytes<T, N>() + (size_t)N * L * sizeof(T);
   static bool attr = false;
   if (!attr) {
-    KFBI_CUDA_TRY(cudaFuncSetAttribute(cols_kernel<T, N, MAXT>,
+    KFBI_CUDA_TRY(cudaFuncSetAttribute(cols_kernel<T, N, EPT, MAXT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     attr = true;
   }
   int per_sm = 0;
-  KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cols_kernel<T, N, MAXT>,
-                                                              threads, smem));
+  KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, cols_kernel<T, N, EPT, MAXT>, threads, smem));
   if (per_sm < 1) per_sm = 1;
   int blocks = N / L;
   blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
   const T scale = T((2.0 / N) * (2.0 / N));
   const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
-  cols_kernel<T, N, MAXT><<<blocks, threads, smem, c.stream>>>(V, tw, lam, T(c.kappa2), scale);
+  cols_kernel<T, N, EPT, MAXT><<<blocks, threads, smem, c.stream>>>(V, stw, tw, lam, T(c.kappa2),
+                                                                    scale);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
 }
 
-// column-pass variant chosen by the autotuner (0: 512-thread CTAs, 1: 1024-thread CTAs)
+// Kernel variants chosen by the setup-time autotuner.  Row pass: 0 = default EPT (16 or
+// 24 values per thread), 1 = half (8 or 12).  Column pass: bit 0 = CTAs of at most 256
+// threads (one column tile per 256 threads, two CTAs per SM) instead of 512, bit 1 =
+// half EPT.
 template <typename T, int N>
-kfbi_status launch_cols_v(Ctx& c, T* V, const cx<T>* tw, const T* lam, int variant) {
-  if (variant == 1 && cplan(N).tpl * 2 <= 1024) return launch_cols<T, N, 1024>(c, V, tw, lam);
-  return launch_cols<T, N, 512>(c, V, tw, lam);
+kfbi_status launch_rows_v(Ctx& c, const T* in, T* out, const cx<T>* tw, T scale, int variant) {
+  constexpr int E = default_ept(N);
+  if (variant == 1 && N / (E / 2) <= 512) return launch_rows<T, N, E / 2>(c, in, out, tw, scale);
+  return launch_rows<T, N, E>(c, in, out, tw, scale);
 }
 
-// Time both column-pass variants on the context's work grid (its contents are scratch
-// at setup) and keep the faster one for this precision.
 template <typename T, int N>
-kfbi_status autotune_cols(Ctx& c, T* V, const cx<T>* tw, const T* lam, int* choice) {
-  cudaEvent_t e[3];
-  for (auto& x : e) KFBI_CUDA_TRY(cudaEventCreate(&x));
-  float ms[2] = {0.f, 0.f};
-  for (int v = 0; v < 2; ++v) {
-    KFBI_TRY((launch_cols_v<T, N>(c, V, tw, lam, v)));           // warm-up
-    KFBI_CUDA_TRY(cudaEventRecord(e[0], c.stream));
-    for (int rep = 0; rep < 3; ++rep) KFBI_TRY((launch_cols_v<T, N>(c, V, tw, lam, v)));
-    KFBI_CUDA_TRY(cudaEventRecord(e[1], c.stream));
-    KFBI_CUDA_TRY(cudaEventSynchronize(e[1]));
-    KFBI_CUDA_TRY(cudaEventElapsedTime(&ms[v], e[0], e[1]));
+kfbi_status launch_cols_v(Ctx& c, T* V, const cx<T>* tw, const T* lam, int variant) {
+  constexpr int E = default_ept(N);
+  constexpr int EH = E / 2;
+  const bool small = variant & 1, half = (variant & 2) != 0;
+  if (half && N / EH <= 512) {
+    if (small && N / EH <= 256) return launch_cols<T, N, EH, 256>(c, V, tw, lam);
+    return launch_cols<T, N, EH, 512>(c, V, tw, lam);
   }
-  for (auto& x : e) cudaEventDestroy(x);
-  *choice = ms[1] < ms[0] ? 1 : 0;
+  if (small && N / E <= 256) return launch_cols<T, N, E, 256>(c, V, tw, lam);
+  return launch_cols<T, N, E, 512>(c, V, tw, lam);
+}
+
+// Time every variant of both passes on the context's scratch work grid and keep the
+// fastest for this precision.
+template <typename T, int N>
+kfbi_status autotune(Ctx& c, T* V, const cx<T>* tw, const T* lam, int* rows_choice,
+                     int* cols_choice) {
+  cudaEvent_t e0, e1;
+  KFBI_CUDA_TRY(cudaEventCreate(&e0));
+  KFBI_CUDA_TRY(cudaEventCreate(&e1));
+  auto time_it = [&](auto&& launch, float* ms) -> kfbi_status {
+    KFBI_TRY(launch());                                     // warm-up (also builds tables)
+    KFBI_CUDA_TRY(cudaEventRecord(e0, c.stream));
+    for (int rep = 0; rep < 3; ++rep) KFBI_TRY(launch());
+    KFBI_CUDA_TRY(cudaEventRecord(e1, c.stream));
+    KFBI_CUDA_TRY(cudaEventSynchronize(e1));
+    KFBI_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+    return KFBI_OK;
+  };
+  float best = 1e30f;
+  for (int v = 0; v < 2; ++v) {
+    float ms = 0.f;
+    KFBI_TRY(time_it([&] { return launch_rows_v<T, N>(c, V, V, tw, T(1), v); }, &ms));
+    if (ms < best) { best = ms; *rows_choice = v; }
+  }
+  best = 1e30f;
+  for (int v = 0; v < 4; ++v) {
+    float ms = 0.f;
+    KFBI_TRY(time_it([&] { return launch_cols_v<T, N>(c, V, tw, lam, v); }, &ms));
+    if (ms < best) { best = ms; *cols_choice = v; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   return KFBI_OK;
 }
 
 template <typename T, int N>
 kfbi_status box_solve_n(Ctx& c, const T* rhs, T* work, const cx<T>* tw, const T* lam) {
-  const int variant = c.cols_variant[sizeof(T) == 8] > 0 ? 1 : 0;
-  KFBI_TRY((launch_rows<T, N>(c, rhs, work, tw, T(1))));
-  KFBI_TRY((launch_cols_v<T, N>(c, work, tw, lam, variant)));
-  KFBI_TRY((launch_rows<T, N>(c, work, work, tw, T(1))));
+  const int rv = c.rows_variant[sizeof(T) == 8], cv = c.cols_variant[sizeof(T) == 8];
+  KFBI_TRY((launch_rows_v<T, N>(c, rhs, work, tw, T(1), rv)));
+  KFBI_TRY((launch_cols_v<T, N>(c, work, tw, lam, cv)));
+  KFBI_TRY((launch_rows_v<T, N>(c, work, work, tw, T(1), rv)));
   return KFBI_OK;
 }
 
 template <typename T>
 kfbi_status autotune_dispatch(Ctx& c, T* scratch, const cx<T>* tw, const T* lam) {
-  int* choice = &c.cols_variant[sizeof(T) == 8];
+  int* rc = &c.rows_variant[sizeof(T) == 8];
+  int* cc = &c.cols_variant[sizeof(T) == 8];
   switch (c.N) {
 #define KFBI_CASE(n) \
-  case n: return autotune_cols<T, n>(c, scratch, tw, lam, choice);
+  case n: return autotune<T, n>(c, scratch, tw, lam, rc, cc);
     KFBI_CASE(32) KFBI_CASE(48) KFBI_CASE(64) KFBI_CASE(96) KFBI_CASE(128) KFBI_CASE(192)
     KFBI_CASE(256) KFBI_CASE(384) KFBI_CASE(512) KFBI_CASE(768) KFBI_CASE(1024)
     KFBI_CASE(1536) KFBI_CASE(2048) KFBI_CASE(3072) KFBI_CASE(4096) KFBI_CASE(6144)

@@ -123,6 +123,8 @@ struct Ctx {
   float* D32 = nullptr;                             // dense right-hand side, FP32 low part
   BoxTables<float> t32{};
   BoxTables<double> t64{};
+  int rows_variant[2] = {0, 0};                     // row-pass variant per precision (autotuned)
+  void* stw[4] = {nullptr, nullptr, nullptr, nullptr}; // stage twiddle tables (FP32/FP64 x EPT)
   int cols_variant[2] = {0, 0};                     // column-pass variant per precision (autotuned)
 
   // GMRES workspace (FP64)
