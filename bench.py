@@ -119,7 +119,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    h.update(open(os.path.join(ROOT, "paper_2404_15249_gb300", "csrc", "dst.cu"), "rb").read())
+    h.update(open(os.path.join(ROOT, "paper_2404_15249_gb300", "csrc", "dst_impl.cuh"), "rb").read())
     return h.hexdigest()[:12]
 
 
@@ -137,8 +137,8 @@ def traffic_for(kernel, N):
     return None
 
 
-STAGE_KERNEL = {"dst_rows_f32": ("dst_rows_kernel<float>", 4), "dst_cols_f32": ("dst_cols_solve_kernel<float>", 4),
-                "dst_rows_f64": ("dst_rows_kernel<double>", 8), "dst_cols_f64": ("dst_cols_solve_kernel<double>", 8),
+STAGE_KERNEL = {"dst_rows_f32": ("rows_kernel<float>", 4), "dst_cols_f32": ("cols_kernel<float>", 4),
+                "dst_rows_f64": ("rows_kernel<double>", 8), "dst_cols_f64": ("cols_kernel<double>", 8),
                 "refine": ("refine_kernel", 0)}
 
 
