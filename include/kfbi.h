@@ -157,6 +157,37 @@ kfbi_status kfbi_interface_solve(kfbi_ctx ctx, int precision, const double* d_de
 kfbi_status kfbi_box_solve(kfbi_ctx ctx, int precision, const double* d_b_grid,
                            double* d_v_grid, void* stream);
 
+/* ---------------------------------------------------------- allocation-free box solve
+   The paper has no counterpart to this entry point.  It is the box solve above (Alg. 4,
+   same transform kernels, default variants) for callers that cannot allocate device
+   memory when they need it: code running inside a pool that has already reserved the
+   device's memory, or where the implicit device synchronisation of cudaMalloc/cudaFree
+   cannot be tolerated.  kfbi_setup allocates a workspace sized by N and M, so those
+   callers get no context; this call needs none.
+     N, lo, hi, kappa: box [lo, hi]^2 with N cells per side (N = 2^a or 3 * 2^a,
+       32 <= N <= KFBI_STATIC_MAX_N), (Lap_h - kappa^2) v = b.
+     precision: KFBI_FP64 or KFBI_MIXED_FP32 (plain FP32 transforms).
+     d_b_grid, d_v_grid: caller-owned device (N+1)^2 grids as for kfbi_box_solve
+       (boundary entries of b ignored, v = 0 on the boundary); they may alias.
+   Workspace: one static device array of KFBI_STATIC_SCRATCH_BYTES per device inside this
+   library, holding the work grid and the transform tables.  No call ever allocates or
+   frees device or host memory (no cudaMalloc/cudaFree, no allocating library call).
+   Nothing in the array has to start at zero: each call rewrites the tables and the whole
+   work grid before reading them.
+   First call on each device: resolves the array's address (cudaGetSymbolAddress, with
+   that device current) and sets the kernels' shared-memory limits; make this first call
+   on every device before any stream capture begins.  Later calls only launch kernels.
+   Calls on one device share the one array: two calls whose device work overlaps in time
+   (different streams without ordering, or different host threads) race and corrupt
+   each other's results; order them (one stream, or events).
+   Errors: N above KFBI_STATIC_MAX_N or unsupported, null grids, hi <= lo, kappa < 0 or
+   another precision -> KFBI_ERR_ARG (message names the limit), before any device work;
+   a failed CUDA call -> KFBI_ERR_CUDA.  Asynchronous on `stream`. */
+#define KFBI_STATIC_MAX_N 1024
+#define KFBI_STATIC_SCRATCH_BYTES (9u << 20)
+kfbi_status kfbi_box_solve_static(int N, double lo, double hi, double kappa, int precision,
+                                  const double* d_b_grid, double* d_v_grid, void* stream);
+
 /* Dirichlet BVP (Procedures 2-3 of Sec. 4.4): g_hat = g - (Y f)^+, K_D phi = g_hat by
    GMRES(m) (Alg. 5; FP64 Arnoldi with CGS2 and Givens rotations on the device), then
    u = W phi + Y f on the grid (Sec. 2.1).  opt->precision selects plain FP64 or mixed

@@ -23,6 +23,8 @@ KFBI_FP64 = 0
 KFBI_MIXED_FP32 = 1
 KFBI_FP32_REFINED = 2
 KFBI_FP32_REFINED_ONCE = 3
+KFBI_STATIC_MAX_N = 1024                  # limits of kfbi_box_solve_static (kfbi.h)
+KFBI_STATIC_SCRATCH_BYTES = 9 << 20
 KFBI_DOUBLE_LAYER = 0
 KFBI_SINGLE_LAYER = 1
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_GEOMETRY", 3: "ERR_NOMEM", 4: "ERR_CUDA",
@@ -82,6 +84,7 @@ _SIGS = {
     "kfbi_apply_volume": (I, [P, I, P, P, P, P]),
     "kfbi_interface_solve": (I, [P, I, P, P, P, P, P, P, P]),
     "kfbi_box_solve": (I, [P, I, P, P, P]),
+    "kfbi_box_solve_static": (I, [I, D, D, D, I, P, P, P]),
     "kfbi_solve_bvp": (I, [P, P, P, P, P, P, ctypes.POINTER(SolveInfo), P]),
     "kfbi_get_inside_mask": (I, [P, P, P]),
     "kfbi_get_info": (I, [P, ctypes.POINTER(CtxInfo)]),
@@ -258,6 +261,22 @@ class Kfbi2D:
             self.close()
         except Exception:
             pass
+
+
+def box_solve_static(N, b_grid, kappa=0.0, lo=-1.0, hi=1.0, precision=KFBI_FP64, out=None,
+                     stream=None):
+    """kfbi_box_solve_static: the box solve without a context, its workspace in the
+    library's static device array (nothing allocated by the library).  b_grid and out
+    are (N+1, N+1) float64 CUDA tensors (out is created here when None)."""
+    import torch
+    if not (isinstance(b_grid, torch.Tensor) and b_grid.is_cuda and b_grid.dtype == torch.float64
+            and b_grid.is_contiguous()):
+        raise ValueError("b_grid must be a contiguous float64 CUDA tensor")
+    out = torch.empty_like(b_grid) if out is None else out
+    _check(lib().kfbi_box_solve_static(int(N), float(lo), float(hi), float(kappa), int(precision),
+                                       _ptr(b_grid), _ptr(out), _stream_ptr(stream)),
+           "kfbi_box_solve_static")
+    return out
 
 
 def batch_solve(ctxs, f_grids, f_ctrls, g_ctrls, u_grids, nrhs, stream=None):

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkfbi.so")
-SOURCES = ["dst.cu", "dst_f32.cu", "dst_f64.cu", "setup2d.cu", "apply2d.cu", "gmres.cu", "capi.cu"]
+SOURCES = ["dst.cu", "dst_f32.cu", "dst_f64.cu", "setup2d.cu", "apply2d.cu", "gmres.cu", "capi.cu",
+           "box_static.cu"]
 ARCH = os.environ.get("KFBI_ARCH", "103a")
 
 
