@@ -109,7 +109,9 @@ typedef struct {
   int dst_variant[4];    /* box-solver kernel variants picked by the setup-time autotuner:
                             row pass FP32, column pass FP32, row pass FP64, column pass
                             FP64 (row: 0 = 16/24 values per thread, 1 = 8/12; column:
-                            bit 0 = 256-thread blocks, bit 1 = 8/12 values per thread) */
+                            bit 0 = 256-thread blocks, bit 1 = 8/12 values per thread,
+                            bit 2 = transposed pass: transpose, row-wise y-transforms,
+                            transpose back) */
 } kfbi_ctx_info;
 
 /* Fills *opt with dim 2, N 128, box [-1,1], kappa 0, FP64, m 50, 20 restarts,

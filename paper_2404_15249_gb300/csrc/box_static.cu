@@ -75,8 +75,8 @@ struct Launch {
   static constexpr dst::CPlan P = cplan(N, E);
   static constexpr int LPC = P.tpl >= 256 ? 1 : 256 / P.tpl;        // rows per CTA
   static constexpr int L = dst::cols_L<T, N, E, 512>();              // columns per CTA
-  static constexpr size_t rows_smem = (size_t)LPC * 2 * dst::line_len(N) * sizeof(cx<T>);
-  static constexpr size_t cols_smem = (size_t)L * dst::col_line_bytes<T, N>() + (size_t)N * L * sizeof(T);
+  static constexpr size_t rows_smem = dst::rows_smem<T, N, E>(LPC);
+  static constexpr size_t cols_smem = dst::cols_smem<T, N, E, 512>();
 
   static kfbi_status attributes() {
     KFBI_CUDA_TRY(cudaFuncSetAttribute(dst::rows_kernel<T, N, E>,

@@ -47,9 +47,11 @@ static void free_handle(kfbi_ctx_s* hd) {
   for (void* p : c.allocs) cudaFree(p);
   if (c.basis) {
     cudaFree(c.basis); cudaFree(c.hess); cudaFree(c.givens); cudaFree(c.gvec);
-    cudaFree(c.hcol); cudaFree(c.yvec);
+    cudaFree(c.hcol); cudaFree(c.yvec); cudaFree(c.gm_part); cudaFree(c.gm_counter);
   }
   if (c.h_pinned) cudaFreeHost(c.h_pinned);
+  for (int i = 0; i < 2; ++i)
+    if (c.gm_ev[i]) cudaEventDestroy(c.gm_ev[i]);
   delete hd;
 }
 
@@ -155,6 +157,7 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.T32, sizeof(float) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.H32, sizeof(float) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.D32, sizeof(float) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, &c.XT, sizeof(double) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.scal, sizeof(double) * 16));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.vecs, sizeof(double) * 8 * M));
   if (cudaMallocHost((void**)&c.h_pinned, sizeof(double) * 16) != cudaSuccess) {

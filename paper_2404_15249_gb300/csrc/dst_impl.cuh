@@ -164,6 +164,17 @@ __host__ __device__ constexpr CPlan cplan(int N, int EPT) {
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int line_len(int N) { return N + N / 16 + 2; }   // complex slots
 
+// Lines whose raw values and two ping-pong buffers would not fit in shared memory (FP64,
+// N >= 6144) use one buffer: every stage then reads all its inputs into registers, waits
+// at a barrier, and writes its outputs over them.
+template <typename T, int N>
+__host__ __device__ constexpr bool one_buffer() {
+  return ((size_t)(N + 2) * sizeof(T) + 15) / 16 * 16 + 2 * (size_t)line_len(N) * 2 * sizeof(T) >
+         220 * 1024;
+}
+template <typename T, int N>
+__host__ __device__ constexpr int line_buffers() { return one_buffer<T, N>() ? 1 : 2; }
+
 // value m of the packed odd extension z_m of a line x (x_0 = 0, x_N = 0):
 // (x_{2m}, x_{2m+1}) for m < N/2, (-x_{2m'}, -x_{2m'-1}) with m' = N - m otherwise
 template <typename T, int N>
@@ -209,12 +220,14 @@ __device__ __forceinline__ void later_stages(cx<T>* z0, cx<T>* z1, int t,
   if constexpr (S < P.nst) {
     constexpr int R = P.radix[S], NB = P.ept / R, STR = N / R;
     // stage s writes buffer s % 2: stage S reads what stage S-1 wrote, writes the other
+    // (z1 == z0 in single-buffer mode)
     cx<T>* src = ((S - 1) % 2 == 0) ? z0 : z1;
     cx<T>* dst = ((S - 1) % 2 == 0) ? z1 : z0;
 #pragma unroll
     for (int q = 0; q < NB; ++q)
 #pragma unroll
       for (int r = 0; r < R; ++r) v[q * R + r] = src[pad(t + q * P.tpl + r * STR)];
+    if constexpr (one_buffer<T, N>()) __syncthreads();
     butterflies<T, N, EPT, S>(dst, t, stw, v);
     __syncthreads();
     later_stages<T, N, EPT, S + 1>(z0, z1, t, stw, v);
@@ -288,8 +301,9 @@ __global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl :
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lpc = blockDim.x / P.tpl;
   const int line = threadIdx.x / P.tpl, t = threadIdx.x - line * P.tpl;
-  cx<T>* z0 = reinterpret_cast<cx<T>*>(smem_raw) + line * 2 * line_len(N);
-  cx<T>* z1 = z0 + line_len(N);
+  constexpr int NBUF = line_buffers<T, N>();
+  cx<T>* z0 = reinterpret_cast<cx<T>*>(smem_raw) + line * NBUF * line_len(N);
+  cx<T>* z1 = z0 + (NBUF - 1) * line_len(N);
   const int step = gridDim.x * lpc;
   for (int row0 = blockIdx.x * lpc; row0 < N; row0 += step) {
     const int row = row0 + line;
@@ -323,7 +337,14 @@ __device__ __forceinline__ double recip(double d) {
 // shared memory of one column line: raw values (N + 2 reals) and two FFT buffers
 template <typename T, int N>
 __host__ __device__ constexpr size_t col_line_bytes() {
-  return ((size_t)(N + 2) * sizeof(T) + 15) / 16 * 16 + 2 * (size_t)line_len(N) * 2 * sizeof(T);
+  return ((size_t)(N + 2) * sizeof(T) + 15) / 16 * 16 +
+         line_buffers<T, N>() * (size_t)line_len(N) * 2 * sizeof(T);
+}
+
+// the column tile is staged through shared memory unless one line alone fills it
+template <typename T, int N>
+__host__ __device__ constexpr bool cols_staged() {
+  return col_line_bytes<T, N>() + (size_t)N * sizeof(T) <= 220 * 1024;
 }
 
 // column tile width: largest power of two <= 32 dividing N with L * tpl threads within
@@ -361,7 +382,9 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 ? 2 : 1)) cols_kernel(T* V,
   unsigned char* lb = smem_raw + line * LB;
   T* raw = reinterpret_cast<T*>(lb);
   cx<T>* z0 = reinterpret_cast<cx<T>*>(lb + ((size_t)(N + 2) * sizeof(T) + 15) / 16 * 16);
-  cx<T>* z1 = z0 + line_len(N);
+  cx<T>* z1 = z0 + (line_buffers<T, N>() - 1) * line_len(N);
+  constexpr bool STAGED = cols_staged<T, N>();
+  static_assert(STAGED || L == 1, "an unstaged column tile holds one column");
   const int nthr = blockDim.x;
   auto raw_of = [&](int c) { return reinterpret_cast<T*>(smem_raw + c * LB); };
 
@@ -381,20 +404,28 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 ? 2 : 1)) cols_kernel(T* V,
   };
 
   int c0 = blockIdx.x * L;
-  if (c0 < N) prefetch(c0);
+  if constexpr (STAGED) {
+    if (c0 < N) prefetch(c0);
+  }
   for (; c0 < N; c0 += gridDim.x * L) {
-    asm volatile("cp.async.wait_group 0;\n" ::);
-    __syncthreads();
-    // staging tile -> raw lines
-    for (int g = threadIdx.x; g < NCH; g += nthr) {
-      const int r = g / CH, cc = g - r * CH;
-      const Raw pk = stage_buf[g];
-      const T* vals = reinterpret_cast<const T*>(&pk);
+    if constexpr (STAGED) {
+      asm volatile("cp.async.wait_group 0;\n" ::);
+      __syncthreads();
+      // staging tile -> raw lines
+      for (int g = threadIdx.x; g < NCH; g += nthr) {
+        const int r = g / CH, cc = g - r * CH;
+        const Raw pk = stage_buf[g];
+        const T* vals = reinterpret_cast<const T*>(&pk);
 #pragma unroll
-      for (int w = 0; w < W; ++w) raw_of(cc * W + w)[r] = vals[w];
+        for (int w = 0; w < W; ++w) raw_of(cc * W + w)[r] = vals[w];
+      }
+      __syncthreads();
+      if (c0 + gridDim.x * L < N) prefetch(c0 + gridDim.x * L);
+    } else {
+      __syncthreads();                        // previous column written back
+      for (int r = threadIdx.x; r < N; r += nthr) raw[r] = V[(size_t)r * N + c0];
+      __syncthreads();
     }
-    __syncthreads();
-    if (c0 + gridDim.x * L < N) prefetch(c0 + gridDim.x * L);
     const int k = c0 + line;
     const T lk = lam[k] - kappa2;
     T X[P.ept];
@@ -413,16 +444,140 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 ? 2 : 1)) cols_kernel(T* V,
 #pragma unroll
     for (int e = 0; e < P.ept; ++e) raw[out_index<T, N, EPT>(t, e)] = X[e];
     __syncthreads();
-    for (int g = threadIdx.x; g < NCH; g += nthr) {
-      const int r = g / CH, cc = g - r * CH;
-      Raw pk;
-      T* vals = reinterpret_cast<T*>(&pk);
+    if constexpr (STAGED) {
+      for (int g = threadIdx.x; g < NCH; g += nthr) {
+        const int r = g / CH, cc = g - r * CH;
+        Raw pk;
+        T* vals = reinterpret_cast<T*>(&pk);
 #pragma unroll
-      for (int w = 0; w < W; ++w) vals[w] = raw_of(cc * W + w)[r];
-      *reinterpret_cast<Raw*>(V + (size_t)r * N + c0 + cc * W) = pk;
+        for (int w = 0; w < W; ++w) vals[w] = raw_of(cc * W + w)[r];
+        *reinterpret_cast<Raw*>(V + (size_t)r * N + c0 + cc * W) = pk;
+      }
+    } else {
+      for (int r = threadIdx.x; r < N; r += nthr) V[(size_t)r * N + c0] = raw[r];
     }
   }
-  asm volatile("cp.async.wait_group 0;\n" ::);
+  if constexpr (STAGED) asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// ---------------------------------------------------------------------------- pass 2, transposed
+// The column pass on contiguous lines: the work grid is transposed so that x-mode k is
+// row k, every row gets DST-I along y, the spectral division and DST-I again (the
+// product of the inverse scales (2/N)^2 included), and the grid is transposed back.
+// Reads and writes are whole rows (and 32 x 32 tiles in the transposes) instead of the
+// narrow column tiles of cols_kernel.
+template <typename T>
+__global__ void transpose_kernel(const T* __restrict__ in, T* __restrict__ out, int N) {
+  __shared__ T tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int y = by + r, x = bx + threadIdx.x;
+    if (x < N && y < N) tile[r][threadIdx.x] = in[(size_t)y * N + x];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int y = bx + r, x = by + threadIdx.x;     // row y of out = column y of in
+    if (x < N && y < N) out[(size_t)y * N + x] = tile[threadIdx.x][r];
+  }
+}
+
+// 16-byte vectors: 64 x 64 FP32 or 32 x 32 FP64 tiles, 16 x 16 threads, each row of a tile
+// moved by 16 threads as one contiguous 256-byte segment (N a multiple of the tile)
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_vec_kernel(const T* __restrict__ in,
+                                                            T* __restrict__ out, int N) {
+  constexpr int VEC = 16 / sizeof(T), TILE = 16 * VEC;
+  typedef typename RawVec<16>::type V16;
+  __shared__ T tile[TILE][TILE + 1];
+  const int bx = blockIdx.x * TILE, by = blockIdx.y * TILE;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+  for (int r = 0; r < TILE / 16; ++r) {
+    const int y = by + ty + 16 * r;
+    const V16 pk = *reinterpret_cast<const V16*>(in + (size_t)y * N + bx + tx * VEC);
+    const T* vals = reinterpret_cast<const T*>(&pk);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) tile[ty + 16 * r][tx * VEC + e] = vals[e];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < TILE / 16; ++r) {
+    const int y = bx + ty + 16 * r;                 // row y of out = column y of in
+    V16 pk;
+    T* vals = reinterpret_cast<T*>(&pk);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) vals[e] = tile[tx * VEC + e][ty + 16 * r];
+    *reinterpret_cast<V16*>(out + (size_t)y * N + by + tx * VEC) = pk;
+  }
+}
+
+template <typename T>
+kfbi_status launch_transpose(const T* in, T* out, int N, cudaStream_t s) {
+  constexpr int TILE = 16 * (16 / sizeof(T));
+  if (N % TILE == 0) {
+    transpose_vec_kernel<T><<<dim3(N / TILE, N / TILE), dim3(16, 16), 0, s>>>(in, out, N);
+  } else {
+    transpose_kernel<T><<<dim3((N + 31) / 32, (N + 31) / 32), dim3(32, 8), 0, s>>>(in, out, N);
+  }
+  KFBI_CUDA_TRY(cudaGetLastError());
+  return KFBI_OK;
+}
+
+// lines per CTA of the transposed column pass: as many as make 256 threads, within the
+// shared memory of a raw line plus its FFT buffers per line
+template <typename T, int N, int EPT>
+__host__ __device__ constexpr int yline_lpc() {
+  constexpr CPlan P = cplan(N, EPT);
+  int l = P.tpl >= 256 ? 1 : 256 / P.tpl;
+  while (l > 1 && (size_t)l * col_line_bytes<T, N>() > 220 * 1024) l /= 2;
+  return l;
+}
+
+template <typename T, int N, int EPT>
+__global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl : 256),
+                                  ((cplan(N, EPT).tpl > 256 && EPT >= 16) ? 1 : 2))
+    yline_kernel(T* U, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
+                 const T* __restrict__ lam, T kappa2, T scale) {
+  constexpr CPlan P = cplan(N, EPT);
+  constexpr size_t LB = col_line_bytes<T, N>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lpc = blockDim.x / P.tpl;
+  const int line = threadIdx.x / P.tpl, t = threadIdx.x - line * P.tpl;
+  unsigned char* lb = smem_raw + line * LB;
+  T* raw = reinterpret_cast<T*>(lb);
+  cx<T>* z0 = reinterpret_cast<cx<T>*>(lb + ((size_t)(N + 2) * sizeof(T) + 15) / 16 * 16);
+  cx<T>* z1 = z0 + (line_buffers<T, N>() - 1) * line_len(N);
+  for (int k0 = blockIdx.x * lpc; k0 < N; k0 += gridDim.x * lpc) {
+    const int k = k0 + line;
+    const bool active = k < N;
+    T* row = U + (size_t)(active ? k : 0) * N;
+    const T lk = active ? lam[k] - kappa2 : T(0);
+    // forward transform and spectral division into the raw line
+    dst_line<T, N, EPT>([&](int m, bool upper) {
+                          return active ? packed<T, N>(row, m, upper) : cx<T>{T(0), T(0)};
+                        },
+                        z0, z1, t, stw, tw, [&](int, int l, T x) {
+                          raw[l] = (!active || k == 0 || l == 0) ? T(0)
+                                                                 : x * scale * recip(lk + lam[l]);
+                        });
+    __syncthreads();
+    dst_line<T, N, EPT>([&](int m, bool upper) { return packed<T, N>(raw, m, upper); }, z0, z1,
+                        t, stw, tw, [&](int, int j, T x) {
+                          if (active) row[j] = x;
+                        });
+    __syncthreads();
+  }
+}
+
+// dynamic shared memory of the two kernels
+template <typename T, int N, int EPT>
+__host__ __device__ constexpr size_t rows_smem(int lpc) {
+  return (size_t)lpc * line_buffers<T, N>() * line_len(N) * sizeof(cx<T>);
+}
+template <typename T, int N, int EPT, int MAXT>
+__host__ __device__ constexpr size_t cols_smem() {
+  constexpr int L = cols_L<T, N, EPT, MAXT>();
+  return (size_t)L * col_line_bytes<T, N>() + (cols_staged<T, N>() ? (size_t)N * L * sizeof(T) : 0);
 }
 
 // ---------------------------------------------------------------------------- tables
@@ -475,9 +630,10 @@ kfbi_status launch_rows(Ctx& c, const T* in, T* out, const cx<T>* tw, T scale) {
   constexpr CPlan P = cplan(N, EPT);
   const cx<T>* stw = nullptr;
   KFBI_TRY((stage_table<T, N, EPT>(c, tw, &stw)));
-  const int lpc = P.tpl >= 256 ? 1 : 256 / P.tpl;
+  constexpr int lpc = P.tpl >= 256 ? 1 : 256 / P.tpl;
+  static_assert(rows_smem<T, N, EPT>(lpc) <= 227 * 1024, "row pass exceeds shared memory");
   const int threads = lpc * P.tpl;
-  const size_t smem = (size_t)lpc * 2 * line_len(N) * sizeof(cx<T>);
+  const size_t smem = rows_smem<T, N, EPT>(lpc);
   static bool attr = false;
   if (!attr) {
     KFBI_CUDA_TRY(cudaFuncSetAttribute(rows_kernel<T, N, EPT>,
@@ -503,8 +659,9 @@ kfbi_status launch_cols(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   constexpr int L = cols_L<T, N, EPT, MAXT>();
   const cx<T>* stw = nullptr;
   KFBI_TRY((stage_table<T, N, EPT>(c, tw, &stw)));
+  static_assert(cols_smem<T, N, EPT, MAXT>() <= 227 * 1024, "column pass exceeds shared memory");
   const int threads = L * P.tpl;
-  const size_t smem = (size_t)L * col_line_bytes<T, N>() + (size_t)N * L * sizeof(T);
+  const size_t smem = cols_smem<T, N, EPT, MAXT>();
   static bool attr = false;
   if (!attr) {
     KFBI_CUDA_TRY(cudaFuncSetAttribute(cols_kernel<T, N, EPT, MAXT>,
@@ -526,10 +683,43 @@ kfbi_status launch_cols(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   return KFBI_OK;
 }
 
+template <typename T, int N, int EPT>
+kfbi_status launch_ylines(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
+  constexpr CPlan P = cplan(N, EPT);
+  constexpr int lpc = yline_lpc<T, N, EPT>();
+  static_assert((size_t)lpc * col_line_bytes<T, N>() <= 227 * 1024, "transposed column pass exceeds shared memory");
+  const cx<T>* stw = nullptr;
+  KFBI_TRY((stage_table<T, N, EPT>(c, tw, &stw)));
+  T* X = reinterpret_cast<T*>(c.XT);
+  const int threads = lpc * P.tpl;
+  const size_t smem = (size_t)lpc * col_line_bytes<T, N>();
+  static bool attr = false;
+  if (!attr) {
+    KFBI_CUDA_TRY(cudaFuncSetAttribute(yline_kernel<T, N, EPT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr = true;
+  }
+  int per_sm = 0;
+  KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yline_kernel<T, N, EPT>,
+                                                              threads, smem));
+  if (per_sm < 1) per_sm = 1;
+  int blocks = (N + lpc - 1) / lpc;
+  blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
+  const T scale = T((2.0 / N) * (2.0 / N));
+  const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
+  prof_count(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64, 2);
+  KFBI_TRY(launch_transpose<T>(V, X, N, c.stream));
+  yline_kernel<T, N, EPT><<<blocks, threads, smem, c.stream>>>(X, stw, tw, lam, T(c.kappa2), scale);
+  KFBI_CUDA_TRY(cudaGetLastError());
+  KFBI_TRY(launch_transpose<T>(X, V, N, c.stream));
+  prof_end(c, pr);
+  return KFBI_OK;
+}
+
 // Kernel variants chosen by the setup-time autotuner.  Row pass: 0 = default EPT (16 or
 // 24 values per thread), 1 = half (8 or 12).  Column pass: bit 0 = CTAs of at most 256
 // threads (one column tile per 256 threads, two CTAs per SM) instead of 512, bit 1 =
-// half EPT.
+// half EPT, bit 2 = transposed pass (transpose, yline_kernel, transpose; bit 0 unused).
 template <typename T, int N>
 kfbi_status launch_rows_v(Ctx& c, const T* in, T* out, const cx<T>* tw, T scale, int variant) {
   constexpr int E = default_ept(N);
@@ -542,6 +732,10 @@ kfbi_status launch_cols_v(Ctx& c, T* V, const cx<T>* tw, const T* lam, int varia
   constexpr int E = default_ept(N);
   constexpr int EH = E / 2;
   const bool small = variant & 1, half = (variant & 2) != 0;
+  if (variant & 4) {
+    if (half && N / EH <= 512) return launch_ylines<T, N, EH>(c, V, tw, lam);
+    return launch_ylines<T, N, E>(c, V, tw, lam);
+  }
   if (half && N / EH <= 512) {
     if (small && N / EH <= 256) return launch_cols<T, N, EH, 256>(c, V, tw, lam);
     return launch_cols<T, N, EH, 512>(c, V, tw, lam);
@@ -574,7 +768,7 @@ kfbi_status autotune(Ctx& c, T* V, const cx<T>* tw, const T* lam, int* rows_choi
     if (ms < best) { best = ms; *rows_choice = v; }
   }
   best = 1e30f;
-  for (int v = 0; v < 4; ++v) {
+  for (int v : {0, 1, 2, 3, 4, 6}) {
     float ms = 0.f;
     KFBI_TRY(time_it([&] { return launch_cols_v<T, N>(c, V, tw, lam, v); }, &ms));
     if (ms < best) { best = ms; *cols_choice = v; }

@@ -1,10 +1,11 @@
 // Restarted GMRES for K_D phi = g_hat (Alg. 5) with every vector operation on the GPU in
 // FP64: Arnoldi by classical Gram-Schmidt applied twice (CGS2), Givens rotations and the
 // triangular least-squares solve on the device (the paper moves the least-squares step
-// to the host every iteration; here only the residual estimate, 16 bytes, is read back).
-// Mixed precision (GMRES-IR): the outer loop forms the true residual r = g_hat - K_D phi
-// with an FP64 apply, an inner GMRES with FP32 box solves (FP64 Arnoldi) solves
-// K_D d = r to a loose tolerance, and phi += d, until ||r|| <= tol ||g_hat||.
+// to the host every iteration; here only 32 bytes of flags per step are read back, one
+// step behind the device).  Mixed precision: one FP64 Arnoldi process whose matvec
+// precision is relaxed as the residual drops (inexact Krylov), every restart cycle ending
+// with the true residual from an FP64-accurate apply (an iterative-refinement step).
+#include <algorithm>
 #include <cmath>
 
 #include "kfbi_internal.cuh"
@@ -26,25 +27,89 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return v;   // valid in thread 0
 }
 
-// h[b] = <V_b, w> for b < blocks
-__global__ void multidot_kernel(const double* __restrict__ V, int ld, int M,
-                                const double* __restrict__ w, double* __restrict__ h) {
+// h[b] = <V_b, w> for b < nb.  Block (s, b) forms the partial dot product of V_b and w
+// over the chunk [s DOT_CHUNK, (s+1) DOT_CHUNK) (eight independent loads per thread), the
+// partial sums part[s * pld + b] are added in chunk order by the last block to finish (a
+// counter, reset by that block), so the result does not depend on scheduling.
+constexpr int DOT_CHUNK = 2048;
+constexpr int DOT_T = 256;
+
+static inline int dot_blocks(int M) { return (M + DOT_CHUNK - 1) / DOT_CHUNK; }
+
+__global__ void __launch_bounds__(DOT_T) multidot_kernel(const double* __restrict__ V, int ld,
+                                                         int M, int nb,
+                                                         const double* __restrict__ w,
+                                                         double* part, int pld,
+                                                         unsigned* counter,
+                                                         double* __restrict__ h) {
   __shared__ double sh[32];
-  const double* v = V + (size_t)blockIdx.x * ld;
-  double s = 0.0;
-  for (int x = threadIdx.x; x < M; x += blockDim.x) s += v[x] * w[x];
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) h[blockIdx.x] = s;
+  __shared__ bool last;
+  const int b = blockIdx.y, x0 = blockIdx.x * DOT_CHUNK;
+  const double* v = V + (size_t)b * ld;
+  double a[DOT_CHUNK / DOT_T];
+#pragma unroll
+  for (int q = 0; q < DOT_CHUNK / DOT_T; ++q) {
+    const int x = x0 + threadIdx.x + q * DOT_T;
+    a[q] = x < M ? v[x] * w[x] : 0.0;
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int q = 0; q < DOT_CHUNK / DOT_T; ++q) t += a[q];
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) part[(size_t)blockIdx.x * pld + b] = t;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int bb = threadIdx.x; bb < nb; bb += blockDim.x) {
+    double u = 0.0;
+    for (int s = 0; s < (int)gridDim.x; ++s) u += __ldcg(part + (size_t)s * pld + bb);
+    h[bb] = u;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
 }
 
-// w += sign * sum_{b < cnt} h[b] V_b
+// w += sign * sum_{b < cnt} h[b] V_b  (coefficients staged in shared memory, eight
+// independent loads in flight per thread).  With nrm_out: also ||w||_2 of the updated w,
+// from per-block partial sums added in block order by the last block to finish.
 __global__ void mv_update_kernel(double* __restrict__ w, const double* __restrict__ V, int ld,
-                                 int M, const double* __restrict__ h, int cnt, double sign) {
+                                 int M, const double* __restrict__ h, int cnt, double sign,
+                                 double* part, unsigned* counter, double* nrm_out) {
+  extern __shared__ double hs[];
+  __shared__ double sh[32];
+  __shared__ bool last;
+  for (int b = threadIdx.x; b < cnt; b += blockDim.x) hs[b] = h[b];
+  __syncthreads();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= M) return;
-  double s = 0.0;
-  for (int b = 0; b < cnt; ++b) s += h[b] * V[(size_t)b * ld + x];
-  w[x] += sign * s;
+  double wn = 0.0;
+  if (x < M) {
+    double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int b = 0;
+    for (; b + 7 < cnt; b += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s[u] += hs[b + u] * V[(size_t)(b + u) * ld + x];
+    }
+    for (; b < cnt; ++b) s[0] += hs[b] * V[(size_t)b * ld + x];
+    wn = w[x] + sign * (((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])));
+    w[x] = wn;
+  }
+  if (!nrm_out) return;                      // uniform over the grid
+  double t = block_sum(wn * wn, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int q = 0; q < (int)gridDim.x; ++q) u += __ldcg(part + q);
+    *nrm_out = sqrt(u);
+    *counter = 0u;
+  }
 }
 
 // scal[slot] = ||v||
@@ -82,30 +147,32 @@ __global__ void cycle_start_kernel(double* V0, const double* r, int M, double* g
   if (x <= m) gvec[x] = (x == 0) ? beta : 0.0;
 }
 
-// Finish Arnoldi step j: column j of the Hessenberg matrix (h1 + h2 from the two CGS
-// passes), its subdiagonal ||w||, V_{j+1} = w / ||w||, Givens rotation of the column and
-// update of the least-squares right-hand side g.
+// Finish Arnoldi step j (nrm = ||w||, formed by the second update): V_{j+1} = w / nrm
+// by every block; block 0 also forms column j of the Hessenberg matrix (h1 + h2 from the
+// two CGS passes, subdiagonal nrm), applies the earlier Givens rotations and the new one,
+// and updates the least-squares right-hand side g.  The column and the rotations are
+// staged in shared memory (dynamic: (m + 1) + 2m doubles) so the sequential rotation loop
+// runs on shared-memory operands.
 __global__ void finish_kernel(int j, int m, int M, const double* __restrict__ w, double* V, int ld,
                               const double* __restrict__ h1, const double* __restrict__ h2,
-                              double* hess, double* giv, double* gvec, double* scal) {
-  __shared__ double sh[32];
-  __shared__ double nrm_s;
-  double s = 0.0;
-  for (int x = threadIdx.x; x < M; x += blockDim.x) s += w[x] * w[x];
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) nrm_s = sqrt(s);
-  __syncthreads();
-  const double nrm = nrm_s;
+                              const double* __restrict__ nrm_in, double* hess, double* giv,
+                              double* gvec, double* scal) {
+  extern __shared__ double dyn[];
+  const double nrm = *nrm_in;
   const double beta = scal[2];
   const bool breakdown = !(nrm > 1e-14 * beta);
-  if (!breakdown)
-    for (int x = threadIdx.x; x < M; x += blockDim.x) V[(size_t)(j + 1) * ld + x] = w[x] / nrm;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!breakdown && x < M) V[(size_t)(j + 1) * ld + x] = w[x] / nrm;
+  if (blockIdx.x != 0) return;
+  double* col = dyn;                 // m + 1
+  double* gs = dyn + (m + 1);        // 2m
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = h1[i] + h2[i];
+  for (int i = threadIdx.x; i < 2 * j; i += blockDim.x) gs[i] = giv[i];
+  __syncthreads();
   if (threadIdx.x == 0) {
-    double* col = hess + (size_t)j * (m + 1);
-    for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
     col[j + 1] = nrm;
     for (int i = 0; i < j; ++i) {
-      const double cs = giv[2 * i], sn = giv[2 * i + 1];
+      const double cs = gs[2 * i], sn = gs[2 * i + 1];
       const double t = cs * col[i] + sn * col[i + 1];
       col[i + 1] = -sn * col[i] + cs * col[i + 1];
       col[i] = t;
@@ -116,21 +183,44 @@ __global__ void finish_kernel(int j, int m, int M, const double* __restrict__ w,
     giv[2 * j + 1] = sn;
     col[j] = den;
     col[j + 1] = 0.0;
-    gvec[j + 1] = -sn * gvec[j];
-    gvec[j] = cs * gvec[j];
-    scal[0] = fabs(gvec[j + 1]);
+    const double gj = gvec[j];
+    gvec[j + 1] = -sn * gj;
+    gvec[j] = cs * gj;
+    scal[0] = fabs(sn * gj);
     scal[1] = breakdown ? 1.0 : 0.0;
     scal[3] = (isfinite(nrm) && isfinite(den)) ? 0.0 : 1.0;
   }
+  __syncthreads();
+  double* hc = hess + (size_t)j * (m + 1);
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hc[i] = col[i];
 }
 
-// back substitution R y = g (k x k, R upper triangular in hess)
-__global__ void lsq_kernel(int k, int m, const double* hess, const double* gvec, double* y) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// back substitution R y = g (k x k, R upper triangular in hess), R and g staged in
+// shared memory when they fit (dynamic: k (k + 1) doubles), else read from global memory
+__global__ void lsq_kernel(int k, int m, const double* hess, const double* gvec, double* y,
+                           int staged) {
+  extern __shared__ double dyn[];
+  const double* R = hess;
+  int ldr = m + 1;
+  const double* g = gvec;
+  if (staged) {
+    double* Rs = dyn;                 // k x k, column l at Rs[l * k]
+    double* gsh = dyn + (size_t)k * k;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+      const int l = e / k, i = e - l * k;
+      Rs[e] = hess[(size_t)l * (m + 1) + i];
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) gsh[i] = gvec[i];
+    __syncthreads();
+    R = Rs;
+    ldr = k;
+    g = gsh;
+  }
+  if (threadIdx.x != 0) return;
   for (int i = k - 1; i >= 0; --i) {
-    double s = gvec[i];
-    for (int l = i + 1; l < k; ++l) s -= hess[(size_t)l * (m + 1) + i] * y[l];
-    y[i] = s / hess[(size_t)i * (m + 1) + i];
+    double s = g[i];
+    for (int l = i + 1; l < k; ++l) s -= R[(size_t)l * ldr + i] * y[l];
+    y[i] = s / R[(size_t)i * ldr + i];
   }
 }
 
@@ -145,7 +235,7 @@ kfbi_status alloc_gmres(Ctx& c, int m) {
   if (c.gm_m >= m && c.basis) return KFBI_OK;
   if (c.basis) {
     cudaFree(c.basis); cudaFree(c.hess); cudaFree(c.givens); cudaFree(c.gvec);
-    cudaFree(c.hcol); cudaFree(c.yvec);
+    cudaFree(c.hcol); cudaFree(c.yvec); cudaFree(c.gm_part); cudaFree(c.gm_counter);
   }
   const int M = c.M;
   KFBI_CUDA_TRY(cudaMalloc((void**)&c.basis, sizeof(double) * (size_t)(m + 1) * M));
@@ -154,6 +244,12 @@ kfbi_status alloc_gmres(Ctx& c, int m) {
   KFBI_CUDA_TRY(cudaMalloc((void**)&c.gvec, sizeof(double) * (m + 1)));
   KFBI_CUDA_TRY(cudaMalloc((void**)&c.hcol, sizeof(double) * 2 * (m + 1)));
   KFBI_CUDA_TRY(cudaMalloc((void**)&c.yvec, sizeof(double) * m));
+  const size_t nparts = std::max((size_t)dot_blocks(M) * (m + 1), (size_t)vb(M));
+  KFBI_CUDA_TRY(cudaMalloc((void**)&c.gm_part, sizeof(double) * nparts));
+  KFBI_CUDA_TRY(cudaMalloc((void**)&c.gm_counter, sizeof(unsigned)));
+  KFBI_CUDA_TRY(cudaMemset(c.gm_counter, 0, sizeof(unsigned)));
+  for (int i = 0; i < 2; ++i)
+    if (!c.gm_ev[i]) KFBI_CUDA_TRY(cudaEventCreateWithFlags(&c.gm_ev[i], cudaEventDisableTiming));
   c.gm_m = m;
   return KFBI_OK;
 }
@@ -167,6 +263,21 @@ static kfbi_status read_scal(Ctx& c, int n) {
   KFBI_CUDA_TRY(cudaMemcpyAsync(c.h_pinned, c.scal, sizeof(double) * n, cudaMemcpyDeviceToHost,
                                 c.stream));
   KFBI_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  return KFBI_OK;
+}
+
+// Arnoldi-step flags through two pinned slots (h_pinned[8..11], [12..15]) and two events
+static kfbi_status post_flags(Ctx& c, int j) {
+  double* slot = c.h_pinned + 8 + 4 * (j & 1);
+  KFBI_CUDA_TRY(cudaMemcpyAsync(slot, c.scal, sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                                c.stream));
+  KFBI_CUDA_TRY(cudaEventRecord(c.gm_ev[j & 1], c.stream));
+  return KFBI_OK;
+}
+
+static kfbi_status wait_flags(Ctx& c, int j, const double** flags) {
+  KFBI_CUDA_TRY(cudaEventSynchronize(c.gm_ev[j & 1]));
+  *flags = c.h_pinned + 8 + 4 * (j & 1);
   return KFBI_OK;
 }
 
@@ -186,7 +297,7 @@ struct Relax {
 static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const double* rhs,
                              double* x, bool x_zero, double tol_abs, int max_cycles,
                              Counters& cnt, double* res_out, int* cycles_out) {
-  const int M = c.M, m = c.gm_m;
+  const int M = c.M, m = c.opt.gmres_m;   // workspace is sized for c.gm_m >= m
   cudaStream_t st = c.stream;
   double* r = c.vecs;            // residual
   double* w = c.vecs + M;        // Krylov image
@@ -210,29 +321,65 @@ static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const do
   for (; cyc < max_cycles && beta > tol_abs; ++cyc) {
     prof_count(c, ST_KRYLOV);
     cycle_start_kernel<<<vb(M > m + 1 ? M : m + 1), 256, 0, st>>>(c.basis, r, M, c.gvec, m, c.scal);
+    // The host runs one Arnoldi step ahead of the device: the flags of step j (residual
+    // estimate, breakdown, NaN) are copied to a pinned slot behind step j's kernels and
+    // read only after step j + 1 has been enqueued, so the device never idles on a host
+    // round trip.  The matvec precision of step j is picked from the estimate of step
+    // j - 2 (estimates only decrease, so an older one errs towards higher precision).
+    // When step p reports convergence or breakdown, the step p + 1 already enqueued is
+    // kept if it is finite and did not break down itself (one more Arnoldi step only
+    // lowers the GMRES residual).
     int k = 0;
     double est = beta;
+    int pending = -1;
     for (int j = 0; j < m; ++j) {
       const int prec = relax.pick(est);
       KFBI_TRY(apply_K(c, prec, c.basis + (size_t)j * M, w, cnt));
       ++cnt.iters;
-      prof_count(c, ST_KRYLOV, 5);
-      multidot_kernel<<<j + 1, RED_T, 0, st>>>(c.basis, M, M, w, h1);
-      mv_update_kernel<<<vb(M), 256, 0, st>>>(w, c.basis, M, M, h1, j + 1, -1.0);
-      multidot_kernel<<<j + 1, RED_T, 0, st>>>(c.basis, M, M, w, h2);
-      mv_update_kernel<<<vb(M), 256, 0, st>>>(w, c.basis, M, M, h2, j + 1, -1.0);
-      finish_kernel<<<1, 1024, 0, st>>>(j, m, M, w, c.basis, M, h1, h2, c.hess, c.givens,
-                                        c.gvec, c.scal);
+      const int pk = prof_begin(c, ST_KRYLOV);
+      prof_count(c, ST_KRYLOV, 4);
+      const size_t hsm = sizeof(double) * (j + 1);
+      const dim3 dg(dot_blocks(M), j + 1);
+      multidot_kernel<<<dg, DOT_T, 0, st>>>(c.basis, M, M, j + 1, w, c.gm_part, m + 1,
+                                            c.gm_counter, h1);
+      mv_update_kernel<<<vb(M), 256, hsm, st>>>(w, c.basis, M, M, h1, j + 1, -1.0, nullptr,
+                                                nullptr, nullptr);
+      multidot_kernel<<<dg, DOT_T, 0, st>>>(c.basis, M, M, j + 1, w, c.gm_part, m + 1,
+                                            c.gm_counter, h2);
+      mv_update_kernel<<<vb(M), 256, hsm, st>>>(w, c.basis, M, M, h2, j + 1, -1.0, c.gm_part,
+                                                c.gm_counter, c.scal + 5);
+      finish_kernel<<<vb(M), 256, sizeof(double) * (3 * m + 1), st>>>(
+          j, m, M, w, c.basis, M, h1, h2, c.scal + 5, c.hess, c.givens, c.gvec, c.scal);
+      prof_end(c, pk);
       KFBI_CUDA_TRY(cudaGetLastError());
-      KFBI_TRY(read_scal(c, 4));
+      KFBI_TRY(post_flags(c, j));
       k = j + 1;
-      if (c.h_pinned[3] != 0.0) return KFBI_ERR_NUMERIC;
-      est = c.h_pinned[0];
-      if (est <= tol_abs || c.h_pinned[1] != 0.0) break;
+      if (pending >= 0) {
+        const double* f = nullptr;
+        KFBI_TRY(wait_flags(c, pending, &f));
+        if (f[3] != 0.0) return KFBI_ERR_NUMERIC;
+        est = f[0];
+        if (est <= tol_abs || f[1] != 0.0) {
+          const bool broke = f[1] != 0.0;
+          KFBI_TRY(wait_flags(c, j, &f));
+          k = (!broke && f[3] == 0.0 && f[1] == 0.0) ? j + 1 : j;
+          pending = -1;
+          break;
+        }
+      }
+      pending = j;
+    }
+    if (pending >= 0) {             // the last step's flags (cycle ended at m steps)
+      const double* f = nullptr;
+      KFBI_TRY(wait_flags(c, pending, &f));
+      if (f[3] != 0.0) return KFBI_ERR_NUMERIC;
     }
     prof_count(c, ST_KRYLOV, 2);
-    lsq_kernel<<<1, 32, 0, st>>>(k, m, c.hess, c.gvec, c.yvec);
-    mv_update_kernel<<<vb(M), 256, 0, st>>>(x, c.basis, M, M, c.yvec, k, 1.0);
+    const size_t lsm = sizeof(double) * (size_t)k * (k + 1);
+    const bool staged = lsm <= 48 * 1024;
+    lsq_kernel<<<1, 256, staged ? lsm : 0, st>>>(k, m, c.hess, c.gvec, c.yvec, staged ? 1 : 0);
+    mv_update_kernel<<<vb(M), 256, sizeof(double) * k, st>>>(x, c.basis, M, M, c.yvec, k, 1.0,
+                                                            nullptr, nullptr, nullptr);
     KFBI_CUDA_TRY(cudaGetLastError());
     KFBI_TRY(apply_K(c, prec_true, x, tmp, cnt));
     prof_count(c, ST_KRYLOV, 2);

@@ -121,6 +121,7 @@ struct Ctx {
   float* T32 = nullptr;                             // third FP32 solve (two refinement steps)
   float* H32 = nullptr;                             // dense right-hand side, FP32 high part
   float* D32 = nullptr;                             // dense right-hand side, FP32 low part
+  void* XT = nullptr;                               // transposed work grid (N x N, FP64 size)
   BoxTables<float> t32{};
   BoxTables<double> t64{};
   int rows_variant[2] = {0, 0};                     // row-pass variant per precision (autotuned)
@@ -137,7 +138,10 @@ struct Ctx {
   double* scal = nullptr;      // 16 scalars
   double* vecs = nullptr;      // 6 x M scratch vectors
   double* yvec = nullptr;      // m
-  double* h_pinned = nullptr;  // pinned host mirror of scal
+  double* h_pinned = nullptr;  // pinned host mirror of scal (16 doubles)
+  cudaEvent_t gm_ev[2] = {nullptr, nullptr};   // Arnoldi-step flag copies done
+  double* gm_part = nullptr;       // per-block partial dot products
+  unsigned* gm_counter = nullptr;  // blocks done in the current multi-dot
   int* err_flag = nullptr;     // device error flag
 
   int64_t bytes = 0;

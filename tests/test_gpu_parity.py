@@ -214,3 +214,27 @@ def test_full_size_apply_parity(N):
     assert rel(ctx.apply_layer_potential(phi, 0, K.KFBI_FP32_REFINED_ONCE).cpu().numpy(), ref) < 1e-10
     assert rel(ctx.apply_layer_potential(phi, 0, K.KFBI_MIXED_FP32).cpu().numpy(), ref) < 1e-4
     ctx.close()
+
+
+@pytest.mark.parametrize("N", [6144, 8192])
+def test_largest_grid_box_solve_manufactured(N):
+    """The largest compiled grids (FP64 lines of N = 8192 run the transforms with one
+    shared-memory buffer and an unstaged column pass): a discrete solution v is chosen,
+    b = (Lap_h - kappa^2) v is formed in FP64 with the 5-point stencil, and the box solve
+    must give v back."""
+    kappa = 2.0
+    iface = W.circle(2 * N, 0.45)
+    ctx = K.Kfbi2D(iface.pts, iface.normals, iface.curv, N, kappa)
+    h = 2.0 / N
+    g = torch.Generator(device="cuda").manual_seed(N)
+    v = torch.zeros((N + 1, N + 1), dtype=torch.float64, device="cuda")
+    v[1:N, 1:N] = torch.rand((N - 1, N - 1), generator=g, device="cuda", dtype=torch.float64) - 0.5
+    b = torch.zeros_like(v)
+    b[1:N, 1:N] = ((v[2:, 1:N] + v[:-2, 1:N] + v[1:N, 2:] + v[1:N, :-2] - 4.0 * v[1:N, 1:N]) / (h * h)
+                   - kappa * kappa * v[1:N, 1:N])
+    scale = float(v.abs().max())
+    # FP32: rounding the right-hand side alone costs about 2e-5 at N = 2048
+    for prec, tol in ((K.KFBI_FP64, 1e-11), (K.KFBI_MIXED_FP32, 1e-3)):
+        out = ctx.box_solve(b, prec)
+        assert float((out - v).abs().max()) / scale < tol, prec
+    ctx.close()
