@@ -18,3 +18,4 @@ __all__ = ["GeometryError", "Geometry2D", "jumps_cartesian", "box_solve_dst",
            "box_solve_dense", "correct_rhs", "interpolate_plus", "apply_interface",
            "apply_double_layer", "apply_volume", "combined_grid_solution", "gmres",
            "richardson", "solve_bvp", "error_norms", "lagrange_basis"]
+from . import kfbi3d  # noqa: E402  (3-D oracle: oracle.kfbi3d)
