@@ -74,8 +74,9 @@ typedef enum {
 } kfbi_layer;
 
 typedef struct {
-  int dim;              /* 2                                                            */
-  int N;                /* cells per side, N = 2^a or 3*2^a, 32 <= N <= 8192            */
+  int dim;              /* 2 or 3                                                       */
+  int N;                /* cells per side, N = 2^a or 3*2^a, 32 <= N <= 8192 (2-D),
+                           <= 512 (3-D)                                                */
   double lo, hi;        /* box [lo, hi]^dim                                             */
   double kappa;         /* >= 0; PDE Lap u - kappa^2 u = f                               */
   int precision;        /* kfbi_precision used by kfbi_solve_bvp: FP64 (plain FP64 GMRES),
@@ -101,8 +102,9 @@ typedef struct {
 
 typedef struct {
   int N, M;
-  int n_crossings_x;     /* crossings of Gamma with the lines x = x_i                     */
-  int n_crossings_y;     /* crossings of Gamma with the lines y = y_j                     */
+  int n_crossings_x;     /* 2-D: crossings of Gamma with the lines x = x_i; 3-D: points on
+                            x-lines (y, z on grid values)                                */
+  int n_crossings_y;     /* 2-D: crossings with the lines y = y_j; 3-D: points on y-lines */
   int n_irregular;       /* interior nodes with a 5-point neighbour across Gamma          */
   int n_inside;          /* grid nodes inside Omega                                      */
   int64_t device_bytes;  /* workspace held by the context                                */
@@ -112,6 +114,8 @@ typedef struct {
                             bit 0 = 256-thread blocks, bit 1 = 8/12 values per thread,
                             bit 2 = transposed pass: transpose, row-wise y-transforms,
                             transpose back) */
+  int dim;               /* 2 or 3                                                        */
+  int n_crossings_z;     /* 3-D: points on z-lines; 0 in 2-D                              */
 } kfbi_ctx_info;
 
 /* Fills *opt with dim 2, N 128, box [-1,1], kappa 0, FP64, m 50, 20 restarts,
@@ -124,8 +128,21 @@ void kfbi_default_options(kfbi_options* opt);
    of irregular nodes with their crossed arms (Sec. 2.2, Fig. of irregular nodes), and
    the FP64 linear maps density -> corrected right-hand side (Alg. 2) and grid values
    -> v^+ at the control points (Alg. 3).  All geometry is computed in FP64 on the GPU.
-   d_pts, d_normals: M x 2; d_curv: M.  Synchronises the stream (reads back counts).
-   Returns KFBI_ERR_GEOMETRY for an under-resolved interface; *out is NULL on error. */
+   dim = 2: d_pts, d_normals: M x 2; d_curv: M signed curvatures.
+   dim = 3 (N <= 512; the paper describes 3-D only by analogy with 2-D): the M control
+   points are the intersections of Gamma with the grid lines, each with two coordinates
+   on grid values (x-, y- and z-lines in any order); d_pts, d_normals: M x 3 (outward
+   unit normals); d_curv: M x 6 packed symmetric shape operators (Sxx, Syy, Szz, Sxy,
+   Sxz, Syz; dn = S dx on tangent vectors).  Points are tagged and sorted per line on
+   the host; labels by line parity, irregular nodes with their arms, least-squares
+   surface-derivative weights (quadratic over the points within 2.5 h, 3.5 h when fewer
+   than 10) and the 10-node interpolation stencils are built on the GPU in FP64.  The
+   3-D double-layer apply uses the least-squares value of the density in the jumps and
+   adds half the difference to the point value (the second-kind identity part acts on
+   the point values); grids are (N+1)^3 with x fastest.  3-D supports the double layer
+   and the volume potential; the refined precisions run FP64 transforms.
+   Synchronises the stream (reads back counts).  Returns KFBI_ERR_GEOMETRY for an
+   under-resolved interface or a point off the grid lines; *out is NULL on error. */
 kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
                        const double* d_normals, const double* d_curv, void* stream,
                        kfbi_ctx* out);

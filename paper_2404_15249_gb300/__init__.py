@@ -57,7 +57,8 @@ class CtxInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("n_crossings_x", ctypes.c_int),
                 ("n_crossings_y", ctypes.c_int), ("n_irregular", ctypes.c_int),
                 ("n_inside", ctypes.c_int), ("device_bytes", ctypes.c_int64),
-                ("dst_variant", ctypes.c_int * 4)]
+                ("dst_variant", ctypes.c_int * 4), ("dim", ctypes.c_int),
+                ("n_crossings_z", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -152,6 +153,8 @@ class Kfbi2D:
     pts, normals: (M, 2) and curv: (M,) arrays (numpy or torch); they are copied to the
     device, then kfbi_setup builds the geometry on the GPU."""
 
+    dim = 2
+
     def __init__(self, pts, normals, curv, N, kappa=0.0, lo=-1.0, hi=1.0, precision=KFBI_FP64,
                  gmres_m=50, max_restarts=20, tol=1e-10, inner_tol=1e-5, stream=None):
         import torch
@@ -163,6 +166,7 @@ class Kfbi2D:
         self.N = int(N)
         self.stream = stream
         o = default_options()
+        o.dim = self.dim
         o.N, o.lo, o.hi, o.kappa = int(N), float(lo), float(hi), float(kappa)
         o.precision, o.gmres_m, o.max_restarts = int(precision), int(gmres_m), int(max_restarts)
         o.tol, o.inner_tol = float(tol), float(inner_tol)
@@ -176,8 +180,9 @@ class Kfbi2D:
     def _vec(self, a):
         return self.torch.as_tensor(a, dtype=self.torch.float64).contiguous().to(self.dev)
 
-    def _grid(self):
-        return self.torch.empty((self.N + 1, self.N + 1), dtype=self.torch.float64, device=self.dev)
+    def _grid(self, dtype=None):
+        return self.torch.empty((self.N + 1,) * self.dim, dtype=dtype or self.torch.float64,
+                                device=self.dev)
 
     def _new(self, n):
         return self.torch.empty(n, dtype=self.torch.float64, device=self.dev)
@@ -231,7 +236,7 @@ class Kfbi2D:
         return u, phi, info.as_dict()
 
     def inside_mask(self):
-        m = self.torch.empty((self.N + 1, self.N + 1), dtype=self.torch.uint8, device=self.dev)
+        m = self._grid(self.torch.uint8)
         _check(lib().kfbi_get_inside_mask(self.handle, _ptr(m), _stream_ptr(self.stream)),
                "kfbi_get_inside_mask")
         return m
@@ -261,6 +266,19 @@ class Kfbi2D:
             self.close()
         except Exception:
             pass
+
+
+class Kfbi3D(Kfbi2D):
+    """One 3-D KFBI context: the interface is given by its intersections with the grid lines
+    of the box [lo, hi]^3 (pts, normals: (P, 3); shape: (P, 6) packed symmetric shape
+    operators Sxx, Syy, Szz, Sxy, Sxz, Syz with dn = S dx), which are also the control
+    points; grids are (N+1)^3 indexed [k, j, i].  Same methods as Kfbi2D (double layer
+    and volume potentials, interface/box solves, the Dirichlet BVP)."""
+
+    dim = 3
+
+    def __init__(self, pts, normals, shape, N, kappa=0.0, **kw):
+        super().__init__(pts, normals, shape, N, kappa, **kw)
 
 
 def box_solve_static(N, b_grid, kappa=0.0, lo=-1.0, hi=1.0, precision=KFBI_FP64, out=None,

@@ -302,6 +302,7 @@ static kfbi_status refined_solve(Ctx& c, const float* b32, const float* bhi, con
 
 // ------------------------------------------------------------------ apply
 kfbi_status apply_potential(Ctx& c, Layer layer, int precision, const double* dens, double* out) {
+  if (c.dim == 3) return apply_potential3(c, layer, precision, dens, out);
   const double* d = layer == Layer::Double ? dens : nullptr;
   const double* s = layer == Layer::Single ? dens : nullptr;
   if (precision == KFBI_FP64) {
@@ -342,6 +343,7 @@ static kfbi_status refined_dense(Ctx& c, int steps) {
 kfbi_status interface_solve(Ctx& c, int precision, const double* dens, const double* f_grid,
                             const double* f_ctrl, double* rhs_grid, double* v_grid,
                             double* out) {
+  if (c.dim == 3) return interface_solve3(c, precision, dens, f_grid, f_ctrl, rhs_grid, v_grid, out);
   const int steps = refine_steps_of(precision);
   if (precision == KFBI_FP64 || steps > 0) {
     KFBI_TRY(dense_rhs64(c, dens, f_grid, f_ctrl));
@@ -374,6 +376,7 @@ kfbi_status interface_solve(Ctx& c, int precision, const double* dens, const dou
 // u on the grid: inside nodes of the combined solve (Phi = phi, F = f~), zero elsewhere
 kfbi_status combined_u(Ctx& c, int precision, const double* dens, const double* f_grid,
                        const double* f_ctrl, double* u_grid) {
+  if (c.dim == 3) return combined_u3(c, precision, dens, f_grid, f_ctrl, u_grid);
   KFBI_TRY(dense_rhs64(c, dens, f_grid, f_ctrl));
   if (precision == KFBI_FP64) {
     KFBI_TRY(box_solve_f64(c, c.V64, c.V64));
@@ -385,6 +388,7 @@ kfbi_status combined_u(Ctx& c, int precision, const double* dens, const double* 
 }
 
 kfbi_status box_solve_grid(Ctx& c, int precision, const double* b_grid, double* v_grid) {
+  if (c.dim == 3) return box_solve_grid3(c, precision, b_grid, v_grid);
   const int steps = refine_steps_of(precision);
   if (precision == KFBI_FP64 || steps > 0) {
     prof_count(c, ST_GRID);
@@ -411,6 +415,7 @@ __global__ void copy_mask_kernel(long n, const uint8_t* in, uint8_t* out) {
 }
 
 kfbi_status inside_mask(Ctx& c, uint8_t* mask) {
+  if (c.dim == 3) return inside_mask3(c, mask);
   const long n = (long)(c.N + 1) * (c.N + 1);
   prof_count(c, ST_GRID);
   copy_mask_kernel<<<gs_blocks(n), 256, 0, c.stream>>>(n, c.inside, mask);

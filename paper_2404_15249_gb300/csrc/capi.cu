@@ -96,13 +96,15 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
     kfbi::set_error("kfbi_setup: null argument");
     return KFBI_ERR_ARG;
   }
-  if (opt->dim != 2) {
-    kfbi::set_error("kfbi_setup: only dim = 2 is implemented");
+  if (opt->dim != 2 && opt->dim != 3) {
+    kfbi::set_error("kfbi_setup: dim = %d (2 or 3)", opt->dim);
     return KFBI_ERR_UNSUPPORTED;
   }
+  const int dim = opt->dim;
+  const int nmax = dim == 2 ? 8192 : 512;
   kfbi::FftPlan plan;
-  if (!kfbi::make_fft_plan(opt->N, &plan) || opt->N > 8192) {
-    kfbi::set_error("kfbi_setup: N = %d must be 2^a or 3*2^a with 32 <= N <= 8192", opt->N);
+  if (!kfbi::make_fft_plan(opt->N, &plan) || opt->N > nmax) {
+    kfbi::set_error("kfbi_setup: N = %d must be 2^a or 3*2^a with 32 <= N <= %d", opt->N, nmax);
     return KFBI_ERR_ARG;
   }
   if (M < 8 || M > (1 << 22) || !(opt->hi > opt->lo) || !(opt->kappa >= 0.0) ||
@@ -123,8 +125,9 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
   c.kappa2 = opt->kappa * opt->kappa;
   c.stream = (cudaStream_t)stream;
   c.plan = plan;
+  c.dim = dim;
   kfbi_status s = KFBI_OK;
-  const size_t grid = (size_t)c.N * c.N;
+  const size_t grid = (size_t)c.N * c.N * (dim == 3 ? (size_t)c.N : 1);
 #define SETUP_TRY(expr)       \
   do {                        \
     s = (expr);               \
@@ -134,15 +137,18 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
     }                         \
   } while (0)
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.err_flag, sizeof(int) * 4));
-  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.pts, sizeof(double) * 2 * M));
-  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.nrm, sizeof(double) * 2 * M));
-  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.curv, sizeof(double) * M));
-  if (cudaMemcpyAsync(c.pts, d_pts, sizeof(double) * 2 * M, cudaMemcpyDeviceToDevice, c.stream) !=
+  // per point: dim coordinates, dim normal components, 1 curvature (2-D) or 6 packed
+  // shape-operator entries (3-D)
+  const size_t ncurv = dim == 2 ? 1 : 6;
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.pts, sizeof(double) * dim * M));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.nrm, sizeof(double) * dim * M));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.curv, sizeof(double) * ncurv * M));
+  if (cudaMemcpyAsync(c.pts, d_pts, sizeof(double) * dim * M, cudaMemcpyDeviceToDevice, c.stream) !=
           cudaSuccess ||
-      cudaMemcpyAsync(c.nrm, d_normals, sizeof(double) * 2 * M, cudaMemcpyDeviceToDevice,
+      cudaMemcpyAsync(c.nrm, d_normals, sizeof(double) * dim * M, cudaMemcpyDeviceToDevice,
                       c.stream) != cudaSuccess ||
-      cudaMemcpyAsync(c.curv, d_curv, sizeof(double) * M, cudaMemcpyDeviceToDevice, c.stream) !=
-          cudaSuccess) {
+      cudaMemcpyAsync(c.curv, d_curv, sizeof(double) * ncurv * M, cudaMemcpyDeviceToDevice,
+                      c.stream) != cudaSuccess) {
     kfbi::set_error("kfbi_setup: copying the interface failed: %s",
                     cudaGetErrorString(cudaGetLastError()));
     free_handle(hd);
@@ -152,11 +158,13 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.V32, sizeof(float) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.B64, sizeof(double) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.V64, sizeof(double) * grid));
-  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.W32, sizeof(float) * grid));
-  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.U32, sizeof(float) * grid));
-  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.T32, sizeof(float) * grid));
-  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.H32, sizeof(float) * grid));
-  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.D32, sizeof(float) * grid));
+  if (dim == 2) {      // refinement grids (the 3-D path refines with FP64 transforms)
+    SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.W32, sizeof(float) * grid));
+    SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.U32, sizeof(float) * grid));
+    SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.T32, sizeof(float) * grid));
+    SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.H32, sizeof(float) * grid));
+    SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.D32, sizeof(float) * grid));
+  }
   SETUP_TRY(kfbi::alloc_bytes(c, &c.XT, sizeof(double) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.scal, sizeof(double) * 16));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.vecs, sizeof(double) * 8 * M));
@@ -166,9 +174,13 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
     return KFBI_ERR_NOMEM;
   }
   SETUP_TRY(kfbi::init_box_tables(c));
-  SETUP_TRY(kfbi::autotune_f32(c));
-  SETUP_TRY(kfbi::autotune_f64(c));
-  SETUP_TRY(kfbi::setup_geometry(c));
+  if (dim == 2) {
+    SETUP_TRY(kfbi::autotune_f32(c));
+    SETUP_TRY(kfbi::autotune_f64(c));
+    SETUP_TRY(kfbi::setup_geometry(c));
+  } else {
+    SETUP_TRY(kfbi::setup_geometry3(c));
+  }
   SETUP_TRY(kfbi::alloc_gmres(c, c.opt.gmres_m));
   if (cudaStreamSynchronize(c.stream) != cudaSuccess) {
     kfbi::set_error("kfbi_setup: %s", cudaGetErrorString(cudaGetLastError()));
@@ -256,8 +268,10 @@ kfbi_status kfbi_get_info(kfbi_ctx ctx, kfbi_ctx_info* info) {
   const Ctx& c = ctx->c;
   info->N = c.N;
   info->M = c.M;
-  info->n_crossings_x = c.ncross[0];
-  info->n_crossings_y = c.ncross[1];
+  info->dim = c.dim;
+  info->n_crossings_x = c.dim == 2 ? c.ncross[0] : c.npts_axis[0];
+  info->n_crossings_y = c.dim == 2 ? c.ncross[1] : c.npts_axis[1];
+  info->n_crossings_z = c.dim == 2 ? 0 : c.npts_axis[2];
   info->n_irregular = c.nirr;
   info->n_inside = c.n_inside;
   info->device_bytes = c.bytes + (int64_t)sizeof(double) * ((int64_t)(c.gm_m + 1) * c.M);

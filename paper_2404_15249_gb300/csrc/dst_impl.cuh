@@ -289,14 +289,15 @@ __device__ __forceinline__ void dst_line(Raw&& load_pair, cx<T>* z0, cx<T>* z1, 
 }
 
 // ---------------------------------------------------------------------------- pass 1/3
-// DST-I along every row: out[row] = scale * DST(in[row]); in may equal out.  LPC lines per
-// CTA, persistent grid-stride loop.  Stage 0 reads the row straight from global memory
+// DST-I along every row: out[row] = scale * DST(in[row]) for the nlines contiguous rows of
+// length N (N rows of a 2-D grid, N^2 x-lines of a 3-D grid); in may equal out.  LPC lines
+// per CTA, persistent grid-stride loop.  Stage 0 reads the row straight from global memory
 // (the odd-extension mirror is address arithmetic), outputs go straight to global memory.
 template <typename T, int N, int EPT>
 __global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl : 256),
                                   ((cplan(N, EPT).tpl > 256 && EPT >= 16) ? 1 : 2))
     rows_kernel(const T* in, T* out, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
-                T scale) {
+                T scale, int nlines) {
   constexpr CPlan P = cplan(N, EPT);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lpc = blockDim.x / P.tpl;
@@ -305,9 +306,9 @@ __global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl :
   cx<T>* z0 = reinterpret_cast<cx<T>*>(smem_raw) + line * NBUF * line_len(N);
   cx<T>* z1 = z0 + (NBUF - 1) * line_len(N);
   const int step = gridDim.x * lpc;
-  for (int row0 = blockIdx.x * lpc; row0 < N; row0 += step) {
+  for (int row0 = blockIdx.x * lpc; row0 < nlines; row0 += step) {
     const int row = row0 + line;
-    const bool active = row < N;
+    const bool active = row < nlines;
     const T* src = in + (size_t)(active ? row : 0) * N;
     T* dst = out + (size_t)row * N;
     dst_line<T, N, EPT>([&](int m, bool upper) {
@@ -466,35 +467,43 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 ? 2 : 1)) cols_kernel(T* V,
 // product of the inverse scales (2/N)^2 included), and the grid is transposed back.
 // Reads and writes are whole rows (and 32 x 32 tiles in the transposes) instead of the
 // narrow column tiles of cols_kernel.
+// out = in^T for an R x C matrix (out is C x R); blockIdx.z walks a batch of such
+// matrices stored back to back.  32 x 32 tiles through shared memory, any R and C.
 template <typename T>
-__global__ void transpose_kernel(const T* __restrict__ in, T* __restrict__ out, int N) {
+__global__ void transpose_kernel(const T* __restrict__ in, T* __restrict__ out, int R, int C) {
   __shared__ T tile[32][33];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  const size_t base = (size_t)blockIdx.z * R * C;
+  in += base;
+  out += base;
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;   // column, row of the input tile
   for (int r = threadIdx.y; r < 32; r += 8) {
     const int y = by + r, x = bx + threadIdx.x;
-    if (x < N && y < N) tile[r][threadIdx.x] = in[(size_t)y * N + x];
+    if (x < C && y < R) tile[r][threadIdx.x] = in[(size_t)y * C + x];
   }
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += 8) {
-    const int y = bx + r, x = by + threadIdx.x;     // row y of out = column y of in
-    if (x < N && y < N) out[(size_t)y * N + x] = tile[threadIdx.x][r];
+    const int y = bx + r, x = by + threadIdx.x;           // row y of out = column y of in
+    if (x < R && y < C) out[(size_t)y * R + x] = tile[threadIdx.x][r];
   }
 }
 
 // 16-byte vectors: 64 x 64 FP32 or 32 x 32 FP64 tiles, 16 x 16 threads, each row of a tile
-// moved by 16 threads as one contiguous 256-byte segment (N a multiple of the tile)
+// moved by 16 threads as one contiguous 256-byte segment (R and C multiples of the tile)
 template <typename T>
 __global__ void __launch_bounds__(256) transpose_vec_kernel(const T* __restrict__ in,
-                                                            T* __restrict__ out, int N) {
+                                                            T* __restrict__ out, int R, int C) {
   constexpr int VEC = 16 / sizeof(T), TILE = 16 * VEC;
   typedef typename RawVec<16>::type V16;
   __shared__ T tile[TILE][TILE + 1];
+  const size_t base = (size_t)blockIdx.z * R * C;
+  in += base;
+  out += base;
   const int bx = blockIdx.x * TILE, by = blockIdx.y * TILE;
   const int tx = threadIdx.x, ty = threadIdx.y;
 #pragma unroll
   for (int r = 0; r < TILE / 16; ++r) {
     const int y = by + ty + 16 * r;
-    const V16 pk = *reinterpret_cast<const V16*>(in + (size_t)y * N + bx + tx * VEC);
+    const V16 pk = *reinterpret_cast<const V16*>(in + (size_t)y * C + bx + tx * VEC);
     const T* vals = reinterpret_cast<const T*>(&pk);
 #pragma unroll
     for (int e = 0; e < VEC; ++e) tile[ty + 16 * r][tx * VEC + e] = vals[e];
@@ -507,17 +516,18 @@ __global__ void __launch_bounds__(256) transpose_vec_kernel(const T* __restrict_
     T* vals = reinterpret_cast<T*>(&pk);
 #pragma unroll
     for (int e = 0; e < VEC; ++e) vals[e] = tile[tx * VEC + e][ty + 16 * r];
-    *reinterpret_cast<V16*>(out + (size_t)y * N + by + tx * VEC) = pk;
+    *reinterpret_cast<V16*>(out + (size_t)y * R + by + tx * VEC) = pk;
   }
 }
 
+// batch x (R x C) -> batch x (C x R)
 template <typename T>
-kfbi_status launch_transpose(const T* in, T* out, int N, cudaStream_t s) {
+kfbi_status launch_transpose(const T* in, T* out, int R, int C, int batch, cudaStream_t s) {
   constexpr int TILE = 16 * (16 / sizeof(T));
-  if (N % TILE == 0) {
-    transpose_vec_kernel<T><<<dim3(N / TILE, N / TILE), dim3(16, 16), 0, s>>>(in, out, N);
+  if (R % TILE == 0 && C % TILE == 0) {
+    transpose_vec_kernel<T><<<dim3(C / TILE, R / TILE, batch), dim3(16, 16), 0, s>>>(in, out, R, C);
   } else {
-    transpose_kernel<T><<<dim3((N + 31) / 32, (N + 31) / 32), dim3(32, 8), 0, s>>>(in, out, N);
+    transpose_kernel<T><<<dim3((C + 31) / 32, (R + 31) / 32, batch), dim3(32, 8), 0, s>>>(in, out, R, C);
   }
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
@@ -533,11 +543,14 @@ __host__ __device__ constexpr int yline_lpc() {
   return l;
 }
 
-template <typename T, int N, int EPT>
+// DIM = 2: line k of U is x-mode k (divisor lam[k] + lam[l] - kappa^2);
+// DIM = 3: line L = i N + j holds x-mode i, y-mode j (divisor lam[i] + lam[j] + lam[l] -
+// kappa^2); nlines = N^(DIM-1); scale = (2/N)^DIM
+template <typename T, int N, int EPT, int DIM>
 __global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl : 256),
                                   ((cplan(N, EPT).tpl > 256 && EPT >= 16) ? 1 : 2))
     yline_kernel(T* U, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
-                 const T* __restrict__ lam, T kappa2, T scale) {
+                 const T* __restrict__ lam, T kappa2, T scale, int nlines) {
   constexpr CPlan P = cplan(N, EPT);
   constexpr size_t LB = col_line_bytes<T, N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -547,23 +560,32 @@ __global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl :
   T* raw = reinterpret_cast<T*>(lb);
   cx<T>* z0 = reinterpret_cast<cx<T>*>(lb + ((size_t)(N + 2) * sizeof(T) + 15) / 16 * 16);
   cx<T>* z1 = z0 + (line_buffers<T, N>() - 1) * line_len(N);
-  for (int k0 = blockIdx.x * lpc; k0 < N; k0 += gridDim.x * lpc) {
+  for (int k0 = blockIdx.x * lpc; k0 < nlines; k0 += gridDim.x * lpc) {
     const int k = k0 + line;
-    const bool active = k < N;
+    bool active = k < nlines;
     T* row = U + (size_t)(active ? k : 0) * N;
-    const T lk = active ? lam[k] - kappa2 : T(0);
+    T lk = T(0);
+    if (active) {
+      if constexpr (DIM == 2) {
+        lk = lam[k] - kappa2;
+      } else {
+        const int i = k / N, j = k - (k / N) * N;
+        lk = lam[i] + lam[j] - kappa2;
+        active = active && i > 0 && j > 0;          // boundary modes stay zero
+      }
+    }
+    const bool zero_line = !active || (DIM == 2 && k == 0);
     // forward transform and spectral division into the raw line
     dst_line<T, N, EPT>([&](int m, bool upper) {
                           return active ? packed<T, N>(row, m, upper) : cx<T>{T(0), T(0)};
                         },
                         z0, z1, t, stw, tw, [&](int, int l, T x) {
-                          raw[l] = (!active || k == 0 || l == 0) ? T(0)
-                                                                 : x * scale * recip(lk + lam[l]);
+                          raw[l] = (zero_line || l == 0) ? T(0) : x * scale * recip(lk + lam[l]);
                         });
     __syncthreads();
     dst_line<T, N, EPT>([&](int m, bool upper) { return packed<T, N>(raw, m, upper); }, z0, z1,
                         t, stw, tw, [&](int, int j, T x) {
-                          if (active) row[j] = x;
+                          if (k < nlines) row[j] = x;
                         });
     __syncthreads();
   }
@@ -626,7 +648,7 @@ kfbi_status stage_table(Ctx& c, const cx<T>* tw, const cx<T>** out) {
 }
 
 template <typename T, int N, int EPT>
-kfbi_status launch_rows(Ctx& c, const T* in, T* out, const cx<T>* tw, T scale) {
+kfbi_status launch_rows(Ctx& c, const T* in, T* out, const cx<T>* tw, T scale, int nlines = N) {
   constexpr CPlan P = cplan(N, EPT);
   const cx<T>* stw = nullptr;
   KFBI_TRY((stage_table<T, N, EPT>(c, tw, &stw)));
@@ -644,10 +666,10 @@ kfbi_status launch_rows(Ctx& c, const T* in, T* out, const cx<T>* tw, T scale) {
   KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_kernel<T, N, EPT>,
                                                               threads, smem));
   if (per_sm < 1) per_sm = 1;
-  int blocks = (N + lpc - 1) / lpc;
+  int blocks = (nlines + lpc - 1) / lpc;
   blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
   const int pr = prof_begin(c, sizeof(T) == 4 ? ST_ROWS32 : ST_ROWS64);
-  rows_kernel<T, N, EPT><<<blocks, threads, smem, c.stream>>>(in, out, stw, tw, scale);
+  rows_kernel<T, N, EPT><<<blocks, threads, smem, c.stream>>>(in, out, stw, tw, scale, nlines);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
@@ -695,12 +717,12 @@ kfbi_status launch_ylines(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   const size_t smem = (size_t)lpc * col_line_bytes<T, N>();
   static bool attr = false;
   if (!attr) {
-    KFBI_CUDA_TRY(cudaFuncSetAttribute(yline_kernel<T, N, EPT>,
+    KFBI_CUDA_TRY(cudaFuncSetAttribute(yline_kernel<T, N, EPT, 2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     attr = true;
   }
   int per_sm = 0;
-  KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yline_kernel<T, N, EPT>,
+  KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yline_kernel<T, N, EPT, 2>,
                                                               threads, smem));
   if (per_sm < 1) per_sm = 1;
   int blocks = (N + lpc - 1) / lpc;
@@ -708,10 +730,11 @@ kfbi_status launch_ylines(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   const T scale = T((2.0 / N) * (2.0 / N));
   const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
   prof_count(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64, 2);
-  KFBI_TRY(launch_transpose<T>(V, X, N, c.stream));
-  yline_kernel<T, N, EPT><<<blocks, threads, smem, c.stream>>>(X, stw, tw, lam, T(c.kappa2), scale);
+  KFBI_TRY(launch_transpose<T>(V, X, N, N, 1, c.stream));
+  yline_kernel<T, N, EPT, 2><<<blocks, threads, smem, c.stream>>>(X, stw, tw, lam, T(c.kappa2),
+                                                                  scale, N);
   KFBI_CUDA_TRY(cudaGetLastError());
-  KFBI_TRY(launch_transpose<T>(X, V, N, c.stream));
+  KFBI_TRY(launch_transpose<T>(X, V, N, N, 1, c.stream));
   prof_end(c, pr);
   return KFBI_OK;
 }

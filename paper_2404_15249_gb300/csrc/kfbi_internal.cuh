@@ -74,7 +74,8 @@ struct Prof {
 
 // ------------------------------------------------------------------ context
 struct Ctx {
-  // problem
+  // problem (dim 2: M control points on a curve; dim 3: M grid-line intersection points)
+  int dim = 2;
   int N = 0, M = 0;
   double lo = -1, hi = 1, h = 0, kappa = 0, kappa2 = 0;
   kfbi_options opt{};
@@ -113,7 +114,26 @@ struct Ctx {
   double* ctrl_cS = nullptr;                  // M x 6 (single layer)
   double* ctrl_eF = nullptr;                  // M   f(z) weight of the jump Taylor terms
 
-  // work grids (N x N, row 0 and column 0 identically zero)
+  // 3-D interface: line CSR per axis, least-squares stencils, interpolation stencils
+  int npts_axis[3] = {0, 0, 0};
+  int* l3_ptr[3] = {nullptr, nullptr, nullptr};   // (N+1)^2 + 1 offsets per axis
+  int* l3_pts[3] = {nullptr, nullptr, nullptr};   // points sorted by (line, coordinate)
+  int* pt_edge = nullptr;                     // M: edge of the point on its line
+  double* frame = nullptr;                    // M x 6: tangents t1, t2
+  int* ls_ptr = nullptr;                      // M + 1
+  int* ls_idx = nullptr;                      // neighbour points
+  double* ls_w = nullptr;                     // 6 weights per neighbour (c0..c5)
+  int* ip_node = nullptr;                     // M x 10 work-grid nodes
+  double* ip_w = nullptr;                     // M x 10 interpolation weights
+  double* ip_mom = nullptr;                   // M x 10 outside-node Taylor moments
+  double* irr_sigma = nullptr;                // nirr: -1 inside, +1 outside
+  int* arm3_pt = nullptr;                     // narms: point on the arm
+  int* arm3_axis = nullptr;
+  double* arm3_delta = nullptr;               // neighbour coordinate - point coordinate
+  double* jmp3 = nullptr;                     // M x 10 jumps (J, G, H) scratch
+  double* fit3 = nullptr;                     // M fitted density scratch
+
+  // work grids (N^dim, index 0 along every axis identically zero)
   float* B32 = nullptr;  float* V32 = nullptr;     // sparse RHS (irregular entries only), work
   double* B64 = nullptr; double* V64 = nullptr;
   float* W32 = nullptr;                             // refinement residual (FP32)
@@ -183,6 +203,18 @@ inline bool valid_precision(int p) {
   return p == KFBI_FP64 || p == KFBI_MIXED_FP32 || p == KFBI_FP32_REFINED ||
          p == KFBI_FP32_REFINED_ONCE;
 }
+
+// 3-D (kfbi3d.cu, dst3d.cu): setup and the same stages on the N^3 work grid
+kfbi_status setup_geometry3(Ctx& c);
+kfbi_status box_solve3_f32(Ctx& c, const float* rhs, float* work);
+kfbi_status box_solve3_f64(Ctx& c, const double* rhs, double* work);
+kfbi_status apply_potential3(Ctx& c, Layer layer, int precision, const double* dens, double* out);
+kfbi_status interface_solve3(Ctx& c, int precision, const double* dens, const double* f_grid,
+                             const double* f_ctrl, double* rhs_grid, double* v_grid, double* out);
+kfbi_status combined_u3(Ctx& c, int precision, const double* dens, const double* f_grid,
+                        const double* f_ctrl, double* u_grid);
+kfbi_status box_solve_grid3(Ctx& c, int precision, const double* b_grid, double* v_grid);
+kfbi_status inside_mask3(Ctx& c, uint8_t* mask);
 
 // solver (gmres.cu)
 kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const double* g_ctrl,

@@ -43,8 +43,13 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     assert lib.kfbi_setup(ctypes.byref(o), 64, dummy, dummy, dummy, None, ctypes.byref(h)) == 1
     assert b"N = 100" in lib.kfbi_last_error()
     o.N = 128
-    o.dim = 3
+    o.dim = 4
     assert lib.kfbi_setup(ctypes.byref(o), 64, dummy, dummy, dummy, None, ctypes.byref(h)) == 8
+    assert not h.value
+    # 3-D grids stop at N = 512
+    o.dim, o.N = 3, 1024
+    assert lib.kfbi_setup(ctypes.byref(o), 64, dummy, dummy, dummy, None, ctypes.byref(h)) == 1
+    assert b"512" in lib.kfbi_last_error()
     assert not h.value
     assert lib.kfbi_apply_layer_potential(None, 0, 0, dummy, dummy, None) == 1
     assert lib.kfbi_destroy(None) == 1
