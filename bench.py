@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--n3d", type=int, default=256,
+                    help="grid size of the 3-D companion measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -356,6 +358,10 @@ def run_kfbi(a):
                "sample": f"{n} FP64 oracle double-layer applies of this N={N} problem "
                          f"({dt:.1f} s, numpy on the host cores); unit as value"}
 
+    companion = None
+    if rank == 0 and a.n3d > 0:
+        companion = run_3d_companion(a, dev, flush)
+
     launches = int(sum(v[1] for v in stages.values()))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -377,13 +383,71 @@ def run_kfbi(a):
             "err_inf_mixed": err_mixed,
             "stage_ms": {k: round(v[0] / a.steps, 4) for k, v in stages.items() if v[1]},
             "stage_launches": {k: int(v[1]) for k, v in stages.items() if v[1]},
-            **fp64}
+            **fp64,
+            "companion_3d": companion}
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_3d_companion(a, dev, flush):
+    """The 3-D configuration (ellipsoid 0.7 x 0.5 x 0.4, u = sin x sin y sin z, kappa = 0)
+    at one grid size: setup, mixed and FP64 Dirichlet solves timed with CUDA events
+    (L2 flushed before each), errors against the exact solution.  Reported beside the
+    2-D line, not folded into its value."""
+    import numpy as np
+    import torch
+    import kfbi_workloads.surfaces3d as S3
+    import paper_2404_15249_gb300 as K
+
+    N = a.n3d
+    prob = S3.config_poisson3d(N, "ellipsoid")
+    I = prob.iface
+    fg = torch.as_tensor(prob.f_grid(), device=dev)
+    fc = torch.as_tensor(prob.f_ctrl(), device=dev)
+    gc = torch.as_tensor(prob.g_ctrl(), device=dev)
+    u = torch.empty((N + 1,) * 3, dtype=torch.float64, device=dev)
+    phi = torch.empty(I.P, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = K.Kfbi3D(I.pts, I.normals, I.shape, N, 0.0, precision=K.KFBI_MIXED_FP32, tol=1e-10)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    inside = ctx.inside_mask().cpu().numpy().astype(bool)
+    u_exact = prob.u_grid()
+    st = torch.cuda.current_stream()
+
+    def timed(n):
+        out, info = [], None
+        for _ in range(n):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _, _, info = ctx.solve_bvp(fg, fc, gc, u_out=u, dens_out=phi)
+            e1.record(st)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        err = float(np.max(np.abs(u.cpu().numpy() - u_exact)[inside]))
+        return statistics.mean(out), info, err
+
+    ctx.solve_bvp(fg, fc, gc, u_out=u, dens_out=phi)
+    ms_mixed, info, err_mixed = timed(3)
+    applies = info["applies_fp64"] + info["applies_low"]
+    ctx.set_solver(K.KFBI_FP64, 50, 20, 1e-10, 1e-5)
+    ctx.solve_bvp(fg, fc, gc, u_out=u, dens_out=phi)
+    ms64, info64, err64 = timed(2)
+    ctx.close()
+    return {"workload": f"3-D Dirichlet Poisson, ellipsoid (0.7, 0.5, 0.4), N={N} "
+                        f"({N + 1}^3 nodes), {I.P} grid-line intersection points, "
+                        f"u = sin x sin y sin z, GMRES(50) to 1e-10",
+            "N": N, "points": I.P, "setup_ms": setup_ms,
+            "mixed_solve_ms": ms_mixed, "grid_pts_per_s_per_apply": (N + 1) ** 3 * applies / (ms_mixed / 1e3),
+            "applies_per_solve": applies, "iterations": info["iterations"],
+            "err_inf_mixed": err_mixed, "fp64_solve_ms": ms64, "err_inf_fp64": err64,
+            "fp64_iterations": info64["iterations"], "speedup_vs_fp64": ms64 / ms_mixed}
 
 
 def main():

@@ -140,7 +140,8 @@ void kfbi_default_options(kfbi_options* opt);
    3-D double-layer apply uses the least-squares value of the density in the jumps and
    adds half the difference to the point value (the second-kind identity part acts on
    the point values); grids are (N+1)^3 with x fastest.  3-D supports the double layer
-   and the volume potential; the refined precisions run FP64 transforms.
+   and the volume potential in every precision (the refinement residual uses the
+   7-point operator).
    Synchronises the stream (reads back counts).  Returns KFBI_ERR_GEOMETRY for an
    under-resolved interface or a point off the grid lines; *out is NULL on error. */
 kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,

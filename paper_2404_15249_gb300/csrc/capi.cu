@@ -158,13 +158,11 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.V32, sizeof(float) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.B64, sizeof(double) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.V64, sizeof(double) * grid));
-  if (dim == 2) {      // refinement grids (the 3-D path refines with FP64 transforms)
-    SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.W32, sizeof(float) * grid));
-    SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.U32, sizeof(float) * grid));
-    SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.T32, sizeof(float) * grid));
-    SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.H32, sizeof(float) * grid));
-    SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.D32, sizeof(float) * grid));
-  }
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.W32, sizeof(float) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.U32, sizeof(float) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.T32, sizeof(float) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.H32, sizeof(float) * grid));
+  SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.D32, sizeof(float) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, &c.XT, sizeof(double) * grid));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.scal, sizeof(double) * 16));
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.vecs, sizeof(double) * 8 * M));

@@ -435,18 +435,122 @@ __global__ void correction3_kernel(int nirr, double inv_h2, const int* __restric
 template <typename T>
 __global__ void interp3_kernel(int P, const int* __restrict__ nodes, const double* __restrict__ w,
                                const double* __restrict__ mom, const double* __restrict__ jmp,
-                               const T* __restrict__ V, const double* __restrict__ dens,
+                               const T* __restrict__ V, const float* __restrict__ V2,
+                               const float* __restrict__ V3, const double* __restrict__ dens,
                                const double* __restrict__ fit, double* out) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   double acc = 0.0;
-  for (int t = 0; t < 10; ++t) acc += w[10 * (long)p + t] * (double)V[nodes[10 * (long)p + t]];
+  for (int t = 0; t < 10; ++t) {
+    const int q = nodes[10 * (long)p + t];
+    double v = (double)V[q];
+    if (V2) v += (double)V2[q];
+    if (V3) v += (double)V3[q];
+    acc += w[10 * (long)p + t] * v;
+  }
   const double* e = mom + 10 * (long)p;
   const double* J = jmp + 10 * (long)p;
   acc += e[0] * J[0] + e[1] * J[1] + e[2] * J[2] + e[3] * J[3] +
          0.5 * (e[4] * J[4] + e[5] * J[5] + e[6] * J[6]) + e[7] * J[7] + e[8] * J[8] + e[9] * J[9];
   if (dens) acc += 0.5 * (dens[p] - fit[p]);
   out[p] = acc;
+}
+
+// ------------------------------------------------------------------- refinement
+__device__ __forceinline__ void two_sum3(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+struct Pair3 {
+  float hi, lo;
+};
+__device__ __forceinline__ Pair3 at3(const float* c1, const float* c2, long q) {
+  if (!c2) return {c1[q], 0.f};
+  Pair3 p;
+  two_sum3(c1[q], c2[q], p.hi, p.lo);
+  return p;
+}
+
+// r = b - (Lap_h - kappa^2) v on the N^3 work grid, v = c1 (+ c2), b = bhi + blo (dense)
+// or 0 (bhi == nullptr), kappa^2 = k2hi + k2lo exactly: the 7-point sum and every product
+// that can cancel are carried as exact FP32 pairs (6 v_c = 4 v_c + 2 v_c, both exact);
+// only the final residual is rounded.
+__global__ void ds_residual3_kernel(int N, float inv_h2, float k2hi, float k2lo,
+                                    const float* __restrict__ bhi, const float* __restrict__ blo,
+                                    const float* __restrict__ c1, const float* __restrict__ c2,
+                                    float* __restrict__ r) {
+  const long n = (long)N * N * N, NN = (long)N * N;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % N), j = (int)((q / N) % N), k = (int)(q / NN);
+    if (i == 0 || j == 0 || k == 0) {
+      r[q] = 0.f;
+      continue;
+    }
+    const Pair3 z = {0.f, 0.f};
+    const Pair3 vc = at3(c1, c2, q);
+    const Pair3 v0 = (i + 1 < N) ? at3(c1, c2, q + 1) : z, v1 = at3(c1, c2, q - 1);
+    const Pair3 v2 = (j + 1 < N) ? at3(c1, c2, q + N) : z, v3 = at3(c1, c2, q - N);
+    const Pair3 v4 = (k + 1 < N) ? at3(c1, c2, q + NN) : z, v5 = at3(c1, c2, q - NN);
+    float s1, t1, s2, t2, s3, t3, s4, t4, s5, t5, s6, t6, s7, t7;
+    two_sum3(v0.hi, v1.hi, s1, t1);
+    two_sum3(v2.hi, v3.hi, s2, t2);
+    two_sum3(v4.hi, v5.hi, s3, t3);
+    two_sum3(s1, s2, s4, t4);
+    two_sum3(s4, s3, s5, t5);
+    two_sum3(s5, -4.f * vc.hi, s6, t6);
+    two_sum3(s6, -2.f * vc.hi, s7, t7);
+    const float lo = (((t1 + t2) + (t3 + t4)) + ((t5 + t6) + t7)) +
+                     (((v0.lo + v1.lo) + (v2.lo + v3.lo)) + (v4.lo + v5.lo) - 6.f * vc.lo);
+    const float p1 = s7 * inv_h2;
+    const float e1 = fmaf(s7, inv_h2, -p1) + lo * inv_h2;
+    const float p2 = k2hi * vc.hi;
+    const float e2 = fmaf(k2hi, vc.hi, -p2) + (k2hi * vc.lo + k2lo * vc.hi);
+    float d, de;
+    two_sum3(p2, -p1, d, de);
+    float tail = de - e1 + e2;
+    if (bhi) {
+      float d2, de2;
+      two_sum3(bhi[q], d, d2, de2);
+      d = d2;
+      tail += de2 + blo[q];
+    }
+    r[q] = d + tail;
+  }
+}
+
+// the residual at the irregular nodes in FP64 against the sparse FP64 right-hand side
+__global__ void residual_fix3_kernel(int nirr, int N, double inv_h2, double kappa2,
+                                     const int* __restrict__ irr_node, const double* __restrict__ b,
+                                     const float* __restrict__ c1, const float* __restrict__ c2,
+                                     float* __restrict__ r) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nirr) return;
+  const long q = irr_node[t], NN = (long)N * N;
+  const int i = (int)(q % N), j = (int)((q / N) % N), k = (int)(q / NN);
+  auto v = [&](long p) { return (double)c1[p] + (c2 ? (double)c2[p] : 0.0); };
+  const double s = (i + 1 < N ? v(q + 1) : 0.0) + v(q - 1) + (j + 1 < N ? v(q + N) : 0.0) +
+                   v(q - N) + (k + 1 < N ? v(q + NN) : 0.0) + v(q - NN);
+  const double vc = v(q);
+  r[q] = (float)(b[q] - ((s - 6.0 * vc) * inv_h2 - kappa2 * vc));
+}
+
+__global__ void split3_kernel(long n, const double* __restrict__ b, float* __restrict__ hi,
+                              float* __restrict__ lo) {
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    const double x = b[q];
+    const float h = (float)x;
+    hi[q] = h;
+    lo[q] = (float)(x - (double)h);
+  }
+}
+
+// v = w1 (+ w2 + w3) summed in FP64
+__global__ void sum3_kernel(long n, const float* __restrict__ w1, const float* __restrict__ w2,
+                            const float* __restrict__ w3, double* __restrict__ out) {
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x)
+    out[q] = (double)w1[q] + (w2 ? (double)w2[q] : 0.0) + (w3 ? (double)w3[q] : 0.0);
 }
 
 // dense right-hand side: F~ (f inside Omega, 0 outside) on the N^3 work grid
@@ -667,29 +771,59 @@ static kfbi_status jumps3(Ctx& c, const double* dens, const double* fctl, bool f
 }
 
 template <typename T>
-static kfbi_status correct3(Ctx& c, T* B, int add) {
+static kfbi_status correct3(Ctx& c, T* B, int add, double* B64 = nullptr) {
   if (c.nirr == 0) return KFBI_OK;
   const int pr = prof_begin(c, ST_CORR);
   correction3_kernel<T><<<nblk(c.nirr, 128), 128, 0, c.stream>>>(
       c.nirr, 1.0 / (c.h * c.h), c.irr_node, c.irr_sigma, c.arm_ptr, c.arm3_pt, c.arm3_axis,
-      c.arm3_delta, c.jmp3, B, add, nullptr);
+      c.arm3_delta, c.jmp3, B, add, B64);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
 }
 
 template <typename T>
-static kfbi_status interp3(Ctx& c, const T* V, const double* dens, double* out) {
+static kfbi_status interp3(Ctx& c, const T* V, const double* dens, double* out,
+                           const float* V2 = nullptr, const float* V3 = nullptr) {
   const int pr = prof_begin(c, ST_INTERP);
   interp3_kernel<T><<<nblk(c.M, 128), 128, 0, c.stream>>>(c.M, c.ip_node, c.ip_w, c.ip_mom, c.jmp3,
-                                                         V, dens, c.fit3, out);
+                                                         V, V2, V3, dens, c.fit3, out);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
 }
 
-// FP64 transforms for the FP64 and refined precisions, FP32 for the plain mixed one
-static bool use_fp32(int precision) { return precision == KFBI_MIXED_FP32; }
+static int steps_of(int precision) {
+  return precision == KFBI_FP32_REFINED ? 2 : (precision == KFBI_FP32_REFINED_ONCE ? 1 : 0);
+}
+
+// FP32 solve of b32, then `steps` corrections from the residual of the 7-point system in
+// double-single arithmetic against the exact pair (bhi, blo), or (bhi null) against the
+// sparse right-hand side, FP64 copy in B64, at the irregular nodes.  v = V32 + U32 (+ T32).
+static kfbi_status refined_solve3(Ctx& c, const float* b32, const float* bhi, const float* blo,
+                                  int steps) {
+  KFBI_TRY(box_solve3_f32(c, b32, c.V32));
+  const float inv_h2 = (float)(1.0 / (c.h * c.h));
+  const float k2hi = (float)c.kappa2, k2lo = (float)(c.kappa2 - (double)k2hi);
+  const long nw = (long)c.N * c.N * c.N;
+  for (int s = 0; s < steps; ++s) {
+    const float* c2 = s == 0 ? nullptr : c.U32;
+    const int pr = prof_begin(c, ST_REFINE);
+    ds_residual3_kernel<<<grid_blocks(nw), 256, 0, c.stream>>>(c.N, inv_h2, k2hi, k2lo, bhi, blo,
+                                                               c.V32, c2, c.W32);
+    if (!bhi && c.nirr > 0)
+      residual_fix3_kernel<<<nblk(c.nirr, 128), 128, 0, c.stream>>>(
+          c.nirr, c.N, 1.0 / (c.h * c.h), c.kappa2, c.irr_node, c.B64, c.V32, c2, c.W32);
+    prof_end(c, pr);
+    if (!bhi && c.nirr > 0) prof_count(c, ST_REFINE);
+    KFBI_CUDA_TRY(cudaGetLastError());
+    KFBI_TRY(box_solve3_f32(c, c.W32, s == 0 ? c.U32 : c.T32));
+  }
+  return KFBI_OK;
+}
+
+// FP64 transforms for FP64, FP32 transforms (refined or not) otherwise
+static bool use_fp32(int precision) { return precision != KFBI_FP64; }
 
 kfbi_status apply_potential3(Ctx& c, Layer layer, int precision, const double* dens, double* out) {
   if (layer != Layer::Double) {
@@ -697,10 +831,15 @@ kfbi_status apply_potential3(Ctx& c, Layer layer, int precision, const double* d
     return KFBI_ERR_UNSUPPORTED;
   }
   KFBI_TRY(jumps3(c, dens, nullptr, true));
+  const int steps = steps_of(precision);
   if (use_fp32(precision)) {
-    KFBI_TRY(correct3<float>(c, c.B32, 0));
-    KFBI_TRY(box_solve3_f32(c, c.B32, c.V32));
-    return interp3<float>(c, c.V32, dens, out);
+    KFBI_TRY(correct3<float>(c, c.B32, 0, steps ? c.B64 : nullptr));
+    if (steps == 0) {
+      KFBI_TRY(box_solve3_f32(c, c.B32, c.V32));
+      return interp3<float>(c, c.V32, dens, out);
+    }
+    KFBI_TRY(refined_solve3(c, c.B32, nullptr, nullptr, steps));
+    return interp3<float>(c, c.V32, dens, out, c.U32, steps > 1 ? c.T32 : nullptr);
   }
   KFBI_TRY(correct3<double>(c, c.B64, 0));
   KFBI_TRY(box_solve3_f64(c, c.B64, c.V64));
@@ -726,7 +865,8 @@ kfbi_status interface_solve3(Ctx& c, int precision, const double* dens, const do
     work_to_grid3_kernel<double><<<grid_blocks(ng), 256, 0, c.stream>>>(N, B, nullptr, rhs_grid);
     KFBI_CUDA_TRY(cudaGetLastError());
   }
-  if (use_fp32(precision)) {
+  const int steps = steps_of(precision);
+  if (use_fp32(precision) && steps == 0) {
     prof_count(c, ST_GRID);
     convert_kernel3<<<grid_blocks(nw), 256, 0, c.stream>>>(nw, B, c.V32);
     KFBI_CUDA_TRY(cudaGetLastError());
@@ -738,7 +878,19 @@ kfbi_status interface_solve3(Ctx& c, int precision, const double* dens, const do
     }
     return out ? interp3<float>(c, c.V32, nullptr, out) : KFBI_OK;
   }
-  KFBI_TRY(box_solve3_f64(c, B, B));
+  if (use_fp32(precision)) {
+    // exact FP32 pair of the dense FP64 right-hand side, refined FP32 solves, v summed
+    // back into the FP64 work grid
+    prof_count(c, ST_GRID);
+    split3_kernel<<<grid_blocks(nw), 256, 0, c.stream>>>(nw, B, c.H32, c.D32);
+    KFBI_CUDA_TRY(cudaGetLastError());
+    KFBI_TRY(refined_solve3(c, c.H32, c.H32, c.D32, steps));
+    prof_count(c, ST_GRID);
+    sum3_kernel<<<grid_blocks(nw), 256, 0, c.stream>>>(nw, c.V32, c.U32, steps > 1 ? c.T32 : nullptr, B);
+    KFBI_CUDA_TRY(cudaGetLastError());
+  } else {
+    KFBI_TRY(box_solve3_f64(c, B, B));
+  }
   if (v_grid) {
     prof_count(c, ST_GRID);
     work_to_grid3_kernel<double><<<grid_blocks(ng), 256, 0, c.stream>>>(N, B, nullptr, v_grid);
@@ -753,7 +905,7 @@ kfbi_status combined_u3(Ctx& c, int precision, const double* dens, const double*
   const long ng = (long)(N + 1) * (N + 1) * (N + 1);
   KFBI_TRY(interface_solve3(c, precision, dens, f_grid, f_ctrl, nullptr, nullptr, nullptr));
   prof_count(c, ST_GRID);
-  if (use_fp32(precision))
+  if (use_fp32(precision) && steps_of(precision) == 0)
     work_to_grid3_kernel<float><<<grid_blocks(ng), 256, 0, c.stream>>>(N, c.V32, c.inside, u_grid);
   else
     work_to_grid3_kernel<double><<<grid_blocks(ng), 256, 0, c.stream>>>(N, c.V64, c.inside, u_grid);
@@ -764,8 +916,20 @@ kfbi_status combined_u3(Ctx& c, int precision, const double* dens, const double*
 kfbi_status box_solve_grid3(Ctx& c, int precision, const double* b_grid, double* v_grid) {
   const int N = c.N;
   const long nw = (long)N * N * N, ng = (long)(N + 1) * (N + 1) * (N + 1);
+  const int steps = steps_of(precision);
+  if (steps > 0) {                    // refined: exact FP32 pair of b, refined FP32 solves
+    prof_count(c, ST_GRID, 4);
+    grid_to_work3_kernel<double><<<grid_blocks(nw), 256, 0, c.stream>>>(N, b_grid, c.V64);
+    split3_kernel<<<grid_blocks(nw), 256, 0, c.stream>>>(nw, c.V64, c.H32, c.D32);
+    KFBI_CUDA_TRY(cudaGetLastError());
+    KFBI_TRY(refined_solve3(c, c.H32, c.H32, c.D32, steps));
+    sum3_kernel<<<grid_blocks(nw), 256, 0, c.stream>>>(nw, c.V32, c.U32, steps > 1 ? c.T32 : nullptr, c.V64);
+    work_to_grid3_kernel<double><<<grid_blocks(ng), 256, 0, c.stream>>>(N, c.V64, nullptr, v_grid);
+    KFBI_CUDA_TRY(cudaGetLastError());
+    return KFBI_OK;
+  }
   prof_count(c, ST_GRID, 2);
-  if (use_fp32(precision)) {
+  if (precision != KFBI_FP64) {
     grid_to_work3_kernel<float><<<grid_blocks(nw), 256, 0, c.stream>>>(N, b_grid, c.V32);
     KFBI_CUDA_TRY(cudaGetLastError());
     KFBI_TRY(box_solve3_f32(c, c.V32, c.V32));

@@ -63,8 +63,10 @@ def test_box_solve_parity(N, kappa):
     ref = O3.box_solve_dst(b, N, geom.h, kappa * kappa)
     v64 = ctx.box_solve(b, K.KFBI_FP64).cpu().numpy()
     v32 = ctx.box_solve(b, K.KFBI_MIXED_FP32).cpu().numpy()
+    vr = ctx.box_solve(b, K.KFBI_FP32_REFINED).cpu().numpy()
     assert rel(v64, ref) < 1e-12
     assert rel(v32, ref) < 2e-5
+    assert rel(vr, ref) < 1e-11
     assert np.all(v64[-1] == 0) and np.all(v64[:, -1] == 0) and np.all(v64[:, :, 0] == 0)
     ctx.close()
 
@@ -77,8 +79,12 @@ def test_double_layer_apply_parity(case):
     ref = O3.apply_double_layer(geom, phi)
     a64 = ctx.apply_layer_potential(phi, 0, K.KFBI_FP64).cpu().numpy()
     a32 = ctx.apply_layer_potential(phi, 0, K.KFBI_MIXED_FP32).cpu().numpy()
+    ar = ctx.apply_layer_potential(phi, 0, K.KFBI_FP32_REFINED).cpu().numpy()
+    a1 = ctx.apply_layer_potential(phi, 0, K.KFBI_FP32_REFINED_ONCE).cpu().numpy()
     assert rel(a64, ref) < 1e-11
     assert rel(a32, ref) < 1e-4
+    assert rel(ar, ref) < 1e-11
+    assert rel(a1, ref) < 1e-9
     again = ctx.apply_layer_potential(phi, 0, K.KFBI_FP64).cpu().numpy()
     assert np.array_equal(a64, again)
     ctx.close()
@@ -114,6 +120,19 @@ def test_constant_density_indicator_kappa0():
     assert np.abs(out - 1.0).max() < 1e-12
     _, v, _ = ctx.interface_solve(np.ones(geom.P), None, None, K.KFBI_FP64)
     assert np.abs(v.cpu().numpy() - geom.inside).max() < 1e-12
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", ["ellipsoid32_k0", "sphere48_k2"])
+def test_interface_solve_refined_fp32(case):
+    prob = CASES[case]()
+    ctx, geom = make(prob)
+    phi = S3.random_density3(geom.P, prob.iface.pts, seed=4)
+    f, fc = prob.f_grid(), prob.f_ctrl()
+    out_ref, _, v_ref = O3.apply_interface(geom, phi=phi, f_ctrl=fc, F_grid=f, return_all=True)
+    _, v, out = ctx.interface_solve(phi, f, fc, K.KFBI_FP32_REFINED)
+    assert rel(v.cpu().numpy(), v_ref) < 1e-11
+    assert rel(out.cpu().numpy(), out_ref) < 1e-11
     ctx.close()
 
 
