@@ -141,18 +141,25 @@ def traffic_for(kernel, N):
 
 STAGE_KERNEL = {"dst_rows_f32": ("rows_kernel<float>", 4), "dst_cols_f32": ("cols_kernel<float>", 4),
                 "dst_rows_f64": ("rows_kernel<double>", 8), "dst_cols_f64": ("cols_kernel<double>", 8),
-                "refine": ("refine_kernel", 0)}
+                "transpose": ("transpose_vec_kernel<float>", 4)}
 
 
-def roofline(stage_ms, N):
-    """Dominant stage of the timed region -> roofline entry for its kernel."""
-    cand = {k: v for k, v in stage_ms.items() if k in STAGE_KERNEL and v[1] > 0 and v[0] > 0}
+def roofline(stage_ms, N, variants):
+    """Dominant stage of the timed region -> roofline entry for its kernel.  The column
+    stage is yline_kernel when the autotuner chose the transposed column pass (variant bit
+    2; the transposes are then their own stage), else cols_kernel."""
+    kernels = dict(STAGE_KERNEL)
+    if variants[1] & 4:
+        kernels["dst_cols_f32"] = ("yline_kernel<float>", 4)
+    if variants[3] & 4:
+        kernels["dst_cols_f64"] = ("yline_kernel<double>", 8)
+    cand = {k: v for k, v in stage_ms.items() if k in kernels and v[1] > 0 and v[0] > 0}
     if not cand:
         return None
     name = max(cand, key=lambda k: cand[k][0])
     ms, launches = cand[name]
     avg_s = ms / launches / 1e3
-    kernel, esize = STAGE_KERNEL[name]
+    kernel, esize = kernels[name]
     if name.endswith("f64"):
         # FP64 transforms are bound by the FP64 ALU: 5 N log2 N flops per complex FFT of
         # length N per line (rows: 1 FFT per line, columns: 2)
@@ -370,7 +377,8 @@ def run_kfbi(a):
                        "precision": "FP32 box solves, FP64 geometry/Krylov/refinement",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "replicas": world},
-            "roofline": roofline(stages, N),
+            "roofline": roofline(stages, N, ctx.info()["dst_variant"]),
+            "dst_variant": ctx.info()["dst_variant"],
             "cpu_baseline": cpu,
             "clocks": clk,
             "e2e": e2e,

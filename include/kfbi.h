@@ -142,6 +142,9 @@ void kfbi_default_options(kfbi_options* opt);
    the point values); grids are (N+1)^3 with x fastest.  3-D supports the double layer
    and the volume potential in every precision (the refinement residual uses the
    7-point operator).
+   2-D setup times the transform variants on the context's grids and keeps the fastest
+   (kfbi_ctx_info.dst_variant); the environment variable KFBI_DST_VARIANTS="r32,c32,r64,c64"
+   fixes them instead (for profiling runs, whose timings would mislead the autotuner).
    Synchronises the stream (reads back counts).  Returns KFBI_ERR_GEOMETRY for an
    under-resolved interface or a point off the grid lines; *out is NULL on error. */
 kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
@@ -236,9 +239,11 @@ kfbi_status kfbi_set_solver(kfbi_ctx ctx, int precision, int gmres_m, int max_re
 /* ---------------------------------------------------------------- stage timers
    Per-stage device time (CUDA events recorded on the context's stream around each
    launch of the apply pipeline) and launch counts of every kernel the library issues.
-   Stages: 0 setup, 1 correction gather, 2 DST rows FP32, 3 DST columns FP32, 4 DST rows
-   FP64, 5 DST columns FP64, 6 interpolation, 7 dense grid build/copy, 8 Krylov vector
-   kernels, 9 FP64 residual refinement of FP32 box solves.  Launch counts are always
+   Stages: 0 setup, 1 correction gather (3-D: jumps and correction), 2 DST rows FP32,
+   3 DST columns FP32 (the y-transform pair with the spectral division; in 3-D the
+   z-transform pair), 4 DST rows FP64, 5 DST columns FP64, 6 interpolation, 7 dense grid
+   build/copy, 8 Krylov vector kernels, 9 residual refinement of FP32 box solves,
+   10 tile transposes of the work grid.  Launch counts are always
    kept; times only while profiling is on (enabling clears both). */
 #define KFBI_NSTAGES 16
 typedef struct {

@@ -173,8 +173,21 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
   }
   SETUP_TRY(kfbi::init_box_tables(c));
   if (dim == 2) {
-    SETUP_TRY(kfbi::autotune_f32(c));
-    SETUP_TRY(kfbi::autotune_f64(c));
+    // KFBI_DST_VARIANTS="r32,c32,r64,c64" fixes the transform variants (profiling runs,
+    // where the autotuner's timings would be distorted by the profiler)
+    const char* fixed = std::getenv("KFBI_DST_VARIANTS");
+    int v[4];
+    if (fixed && std::sscanf(fixed, "%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3]) == 4 &&
+        v[0] >= 0 && v[0] <= 1 && v[2] >= 0 && v[2] <= 1 && v[1] >= 0 && v[1] <= 7 &&
+        v[3] >= 0 && v[3] <= 7) {
+      c.rows_variant[0] = v[0];
+      c.cols_variant[0] = v[1];
+      c.rows_variant[1] = v[2];
+      c.cols_variant[1] = v[3];
+    } else {
+      SETUP_TRY(kfbi::autotune_f32(c));
+      SETUP_TRY(kfbi::autotune_f64(c));
+    }
     SETUP_TRY(kfbi::setup_geometry(c));
   } else {
     SETUP_TRY(kfbi::setup_geometry3(c));
@@ -421,7 +434,7 @@ kfbi_status kfbi_profile_read(kfbi_ctx ctx, kfbi_stage_times* out) {
 const char* kfbi_stage_name(int s) {
   static const char* names[] = {"setup", "correction", "dst_rows_f32", "dst_cols_f32",
                                 "dst_rows_f64", "dst_cols_f64", "interpolation", "grid",
-                                "krylov", "refine"};
+                                "krylov", "refine", "transpose"};
   return (s >= 0 && s < kfbi::ST_COUNT) ? names[s] : "unused";
 }
 

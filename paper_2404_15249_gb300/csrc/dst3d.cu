@@ -19,9 +19,9 @@ kfbi_status box_solve3_n(Ctx& c, const T* rhs, T* A, const cx<T>* tw, const T* l
   T* X = reinterpret_cast<T*>(c.XT);
   const int n2 = N * N;
   KFBI_TRY((launch_rows<T, N, E>(c, rhs, A, tw, T(1), n2)));
-  KFBI_TRY(launch_transpose<T>(A, X, N, N, N, c.stream));
+  KFBI_TRY(launch_transpose<T>(c, A, X, N, N, N));
   KFBI_TRY((launch_rows<T, N, E>(c, X, X, tw, T(1), n2)));
-  KFBI_TRY(launch_transpose<T>(X, A, N, n2, 1, c.stream));
+  KFBI_TRY(launch_transpose<T>(c, X, A, N, n2, 1));
   {
     const cx<T>* stw = nullptr;
     KFBI_TRY((stage_table<T, N, E>(c, tw, &stw)));
@@ -46,9 +46,9 @@ kfbi_status box_solve3_n(Ctx& c, const T* rhs, T* A, const cx<T>* tw, const T* l
     prof_end(c, pr);
     KFBI_CUDA_TRY(cudaGetLastError());
   }
-  KFBI_TRY(launch_transpose<T>(A, X, n2, N, 1, c.stream));
+  KFBI_TRY(launch_transpose<T>(c, A, X, n2, N, 1));
   KFBI_TRY((launch_rows<T, N, E>(c, X, X, tw, T(1), n2)));
-  KFBI_TRY(launch_transpose<T>(X, A, N, N, N, c.stream));
+  KFBI_TRY(launch_transpose<T>(c, X, A, N, N, N));
   KFBI_TRY((launch_rows<T, N, E>(c, A, A, tw, T(1), n2)));
   return KFBI_OK;
 }

@@ -522,13 +522,15 @@ __global__ void __launch_bounds__(256) transpose_vec_kernel(const T* __restrict_
 
 // batch x (R x C) -> batch x (C x R)
 template <typename T>
-kfbi_status launch_transpose(const T* in, T* out, int R, int C, int batch, cudaStream_t s) {
+kfbi_status launch_transpose(Ctx& c, const T* in, T* out, int R, int C, int batch) {
   constexpr int TILE = 16 * (16 / sizeof(T));
+  const int pr = prof_begin(c, ST_TRANS);
   if (R % TILE == 0 && C % TILE == 0) {
-    transpose_vec_kernel<T><<<dim3(C / TILE, R / TILE, batch), dim3(16, 16), 0, s>>>(in, out, R, C);
+    transpose_vec_kernel<T><<<dim3(C / TILE, R / TILE, batch), dim3(16, 16), 0, c.stream>>>(in, out, R, C);
   } else {
-    transpose_kernel<T><<<dim3((C + 31) / 32, (R + 31) / 32, batch), dim3(32, 8), 0, s>>>(in, out, R, C);
+    transpose_kernel<T><<<dim3((C + 31) / 32, (R + 31) / 32, batch), dim3(32, 8), 0, c.stream>>>(in, out, R, C);
   }
+  prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
 }
@@ -728,14 +730,13 @@ kfbi_status launch_ylines(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   int blocks = (N + lpc - 1) / lpc;
   blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
   const T scale = T((2.0 / N) * (2.0 / N));
+  KFBI_TRY(launch_transpose<T>(c, V, X, N, N, 1));
   const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
-  prof_count(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64, 2);
-  KFBI_TRY(launch_transpose<T>(V, X, N, N, 1, c.stream));
   yline_kernel<T, N, EPT, 2><<<blocks, threads, smem, c.stream>>>(X, stw, tw, lam, T(c.kappa2),
                                                                   scale, N);
-  KFBI_CUDA_TRY(cudaGetLastError());
-  KFBI_TRY(launch_transpose<T>(X, V, N, N, 1, c.stream));
   prof_end(c, pr);
+  KFBI_CUDA_TRY(cudaGetLastError());
+  KFBI_TRY(launch_transpose<T>(c, X, V, N, N, 1));
   return KFBI_OK;
 }
 

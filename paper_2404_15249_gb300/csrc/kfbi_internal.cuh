@@ -60,7 +60,7 @@ struct BoxTables {
 // ------------------------------------------------------------------ stage timers
 enum Stage : int {
   ST_SETUP = 0, ST_CORR = 1, ST_ROWS32 = 2, ST_COLS32 = 3, ST_ROWS64 = 4, ST_COLS64 = 5,
-  ST_INTERP = 6, ST_GRID = 7, ST_KRYLOV = 8, ST_REFINE = 9, ST_COUNT = 10
+  ST_INTERP = 6, ST_GRID = 7, ST_KRYLOV = 8, ST_REFINE = 9, ST_TRANS = 10, ST_COUNT = 11
 };
 
 struct Prof {
