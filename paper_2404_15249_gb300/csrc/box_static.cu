@@ -105,12 +105,12 @@ struct Launch {
     load_kernel<T><<<dim3(gg.x, N), 256, 0, s>>>(N, b, work);
     KFBI_CUDA_TRY(cudaGetLastError());
     const int row_blocks = (N + LPC - 1) / LPC;
-    dst::rows_kernel<T, N, E><<<row_blocks, LPC * P.tpl, rows_smem, s>>>(work, work, stw, tw, T(1), N);
+    dst::rows_kernel<T, N, E><<<row_blocks, LPC * P.tpl, rows_smem, s>>>(work, work, stw, tw, T(1), N, nullptr);
     KFBI_CUDA_TRY(cudaGetLastError());
     dst::cols_kernel<T, N, E, 512><<<N / L, L * P.tpl, cols_smem, s>>>(
         work, stw, tw, lam, T(kappa2), T((2.0 / N) * (2.0 / N)));
     KFBI_CUDA_TRY(cudaGetLastError());
-    dst::rows_kernel<T, N, E><<<row_blocks, LPC * P.tpl, rows_smem, s>>>(work, work, stw, tw, T(1), N);
+    dst::rows_kernel<T, N, E><<<row_blocks, LPC * P.tpl, rows_smem, s>>>(work, work, stw, tw, T(1), N, nullptr);
     KFBI_CUDA_TRY(cudaGetLastError());
     store_kernel<T><<<gg, 256, 0, s>>>(N, work, v);
     KFBI_CUDA_TRY(cudaGetLastError());

@@ -26,11 +26,11 @@ kfbi_status box_solve3_n(Ctx& c, const T* rhs, T* A, const cx<T>* tw, const T* l
     const cx<T>* stw = nullptr;
     KFBI_TRY((stage_table<T, N, E>(c, tw, &stw)));
     const int threads = lpc * P.tpl;
-    const size_t smem = (size_t)lpc * col_line_bytes<T, N>();
+    const size_t smem = yline_smem<T, N, E>();
     static bool attr = false;
     if (!attr) {
       KFBI_CUDA_TRY(cudaFuncSetAttribute(yline_kernel<T, N, E, 3>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr = true;
     }
     int per_sm = 0;
@@ -42,7 +42,7 @@ kfbi_status box_solve3_n(Ctx& c, const T* rhs, T* A, const cx<T>* tw, const T* l
     const T scale = T((2.0 / N) * (2.0 / N) * (2.0 / N));
     const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
     yline_kernel<T, N, E, 3><<<blocks, threads, smem, c.stream>>>(A, stw, tw, lam, T(c.kappa2),
-                                                                  scale, n2);
+                                                                  scale, n2, c.err_flag + 2);
     prof_end(c, pr);
     KFBI_CUDA_TRY(cudaGetLastError());
   }

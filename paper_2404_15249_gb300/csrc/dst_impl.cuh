@@ -271,10 +271,15 @@ __device__ __forceinline__ int out_index(int t, int e) {
 // the packed odd extension from the raw values directly, the remaining stages run in
 // shared memory, the outputs are handed to f(e, k, X_k).  Ends with a barrier-free read of
 // the last buffer; the caller synchronises before the buffers are reused.
-template <typename T, int N, int EPT, typename Raw, typename F>
+struct NoHook {
+  __device__ void operator()() const {}
+};
+
+// after0() runs once the raw values have been consumed (after stage 0's barrier)
+template <typename T, int N, int EPT, typename Raw, typename F, typename A = NoHook>
 __device__ __forceinline__ void dst_line(Raw&& load_pair, cx<T>* z0, cx<T>* z1, int t,
                                          const cx<T>* __restrict__ stw,
-                                         const cx<T>* __restrict__ tw, F&& f) {
+                                         const cx<T>* __restrict__ tw, F&& f, A&& after0 = A{}) {
   constexpr CPlan P = cplan(N, EPT);
   constexpr int R = P.radix[0], NB = P.ept / R, STR = N / R;
   cx<T> v[P.ept];
@@ -284,39 +289,127 @@ __device__ __forceinline__ void dst_line(Raw&& load_pair, cx<T>* z0, cx<T>* z1, 
     for (int r = 0; r < R; ++r) v[q * R + r] = load_pair(t + q * P.tpl + r * STR, 2 * r >= R);
   butterflies<T, N, EPT, 0>(z0, t, stw, v);
   __syncthreads();
+  after0();
   later_stages<T, N, EPT, 1>(z0, z1, t, stw, v);
   dst_outputs<T, N, EPT>(last_buffer<T, N, EPT>(z0, z1), t, tw, v, f);
+}
+
+// ---------------------------------------------------------------------------- line staging
+// The next block of contiguous lines is brought into shared memory by one bulk
+// asynchronous copy (completion counted on an mbarrier) while the current block is
+// transformed.  Waits are bounded: after 2^20 polls the kernel records a timeout in *err
+// (when given) and goes on, so a lost copy cannot hang the GPU.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void stage_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// one thread: copy `bytes` (a multiple of 16, both addresses 16-byte aligned) to dst
+__device__ __forceinline__ void stage_issue(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void stage_wait(uint64_t* bar, uint32_t parity, int* err) {
+  const uint32_t a = smem_addr(bar);
+  for (int i = 0; i < (1 << 20); ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return;
+  }
+  if (err) atomicOr(err, 1);
+}
+
+// shared-memory bytes: FFT buffers of the row pass, and whether a staging line fits
+template <typename T, int N, int EPT>
+__host__ __device__ constexpr int rows_lpc() {
+  return cplan(N, EPT).tpl >= 256 ? 1 : 256 / cplan(N, EPT).tpl;
+}
+template <typename T, int N, int EPT>
+__host__ __device__ constexpr size_t rows_fft_bytes() {
+  return ((size_t)rows_lpc<T, N, EPT>() * line_buffers<T, N>() * line_len(N) * sizeof(cx<T>) + 15) / 16 * 16;
+}
+template <typename T, int N, int EPT>
+__host__ __device__ constexpr bool rows_staged() {
+  return rows_fft_bytes<T, N, EPT>() + (size_t)rows_lpc<T, N, EPT>() * N * sizeof(T) <= 220 * 1024;
 }
 
 // ---------------------------------------------------------------------------- pass 1/3
 // DST-I along every row: out[row] = scale * DST(in[row]) for the nlines contiguous rows of
 // length N (N rows of a 2-D grid, N^2 x-lines of a 3-D grid); in may equal out.  LPC lines
-// per CTA, persistent grid-stride loop.  Stage 0 reads the row straight from global memory
-// (the odd-extension mirror is address arithmetic), outputs go straight to global memory.
+// per CTA, persistent grid-stride loop.  Stage 0 reads the rows from a shared-memory
+// staging block filled by a bulk asynchronous copy issued while the previous block was
+// transformed (straight from global memory where the staging block does not fit); the
+// odd-extension mirror is address arithmetic; outputs go straight to global memory.
 template <typename T, int N, int EPT>
 __global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl : 256),
                                   ((cplan(N, EPT).tpl > 256 && EPT >= 16) ? 1 : 2))
     rows_kernel(const T* in, T* out, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
-                T scale, int nlines) {
+                T scale, int nlines, int* err) {
   constexpr CPlan P = cplan(N, EPT);
+  constexpr bool STG = rows_staged<T, N, EPT>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
   const int lpc = blockDim.x / P.tpl;
   const int line = threadIdx.x / P.tpl, t = threadIdx.x - line * P.tpl;
   constexpr int NBUF = line_buffers<T, N>();
   cx<T>* z0 = reinterpret_cast<cx<T>*>(smem_raw) + line * NBUF * line_len(N);
   cx<T>* z1 = z0 + (NBUF - 1) * line_len(N);
+  T* stage = reinterpret_cast<T*>(smem_raw + rows_fft_bytes<T, N, EPT>());   // lpc lines
   const int step = gridDim.x * lpc;
-  for (int row0 = blockIdx.x * lpc; row0 < nlines; row0 += step) {
+  auto issue = [&](int r0) {
+    const int cnt = min(lpc, nlines - r0);
+    stage_issue(stage, in + (size_t)r0 * N, (uint32_t)(cnt * N * sizeof(T)), &bar);
+  };
+  int row0 = blockIdx.x * lpc;
+  if constexpr (STG) {
+    if (threadIdx.x == 0) stage_init(&bar);
+    __syncthreads();
+    if (threadIdx.x == 0 && row0 < nlines) issue(row0);
+  }
+  for (int it = 0; row0 < nlines; row0 += step, ++it) {
     const int row = row0 + line;
     const bool active = row < nlines;
-    const T* src = in + (size_t)(active ? row : 0) * N;
     T* dst = out + (size_t)row * N;
-    dst_line<T, N, EPT>([&](int m, bool upper) {
-                          return active ? packed<T, N>(src, m, upper) : cx<T>{T(0), T(0)};
-                        },
-                        z0, z1, t, stw, tw, [&](int, int k, T x) {
-                          if (active) dst[k] = x * scale;
-                        });
+    if constexpr (STG) {
+      stage_wait(&bar, (uint32_t)(it & 1), err);
+      const T* src = stage + (size_t)line * N;
+      dst_line<T, N, EPT>(
+          [&](int m, bool upper) {
+            return active ? packed<T, N>(src, m, upper) : cx<T>{T(0), T(0)};
+          },
+          z0, z1, t, stw, tw,
+          [&](int, int k, T x) {
+            if (active) dst[k] = x * scale;
+          },
+          [&] {                               // staging consumed: fetch the next block
+            if (threadIdx.x == 0 && row0 + step < nlines) issue(row0 + step);
+          });
+    } else {
+      const T* src = in + (size_t)(active ? row : 0) * N;
+      dst_line<T, N, EPT>([&](int m, bool upper) {
+                            return active ? packed<T, N>(src, m, upper) : cx<T>{T(0), T(0)};
+                          },
+                          z0, z1, t, stw, tw, [&](int, int k, T x) {
+                            if (active) dst[k] = x * scale;
+                          });
+    }
     __syncthreads();
   }
 }
@@ -548,21 +641,45 @@ __host__ __device__ constexpr int yline_lpc() {
 // DIM = 2: line k of U is x-mode k (divisor lam[k] + lam[l] - kappa^2);
 // DIM = 3: line L = i N + j holds x-mode i, y-mode j (divisor lam[i] + lam[j] + lam[l] -
 // kappa^2); nlines = N^(DIM-1); scale = (2/N)^DIM
+template <typename T, int N, int EPT>
+__host__ __device__ constexpr bool yline_staged() {
+  return (size_t)yline_lpc<T, N, EPT>() * (col_line_bytes<T, N>() + N * sizeof(T)) <= 220 * 1024;
+}
+template <typename T, int N, int EPT>
+__host__ __device__ constexpr size_t yline_smem() {
+  return (size_t)yline_lpc<T, N, EPT>() *
+         (col_line_bytes<T, N>() + (yline_staged<T, N, EPT>() ? N * sizeof(T) : 0));
+}
+
 template <typename T, int N, int EPT, int DIM>
 __global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl : 256),
                                   ((cplan(N, EPT).tpl > 256 && EPT >= 16) ? 1 : 2))
     yline_kernel(T* U, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
-                 const T* __restrict__ lam, T kappa2, T scale, int nlines) {
+                 const T* __restrict__ lam, T kappa2, T scale, int nlines, int* err) {
   constexpr CPlan P = cplan(N, EPT);
   constexpr size_t LB = col_line_bytes<T, N>();
+  constexpr bool STG = yline_staged<T, N, EPT>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
   const int lpc = blockDim.x / P.tpl;
   const int line = threadIdx.x / P.tpl, t = threadIdx.x - line * P.tpl;
   unsigned char* lb = smem_raw + line * LB;
   T* raw = reinterpret_cast<T*>(lb);
   cx<T>* z0 = reinterpret_cast<cx<T>*>(lb + ((size_t)(N + 2) * sizeof(T) + 15) / 16 * 16);
   cx<T>* z1 = z0 + (line_buffers<T, N>() - 1) * line_len(N);
-  for (int k0 = blockIdx.x * lpc; k0 < nlines; k0 += gridDim.x * lpc) {
+  T* stage = reinterpret_cast<T*>(smem_raw + (size_t)lpc * LB);        // lpc lines
+  const int step = gridDim.x * lpc;
+  auto issue = [&](int r0) {
+    const int cnt = min(lpc, nlines - r0);
+    stage_issue(stage, U + (size_t)r0 * N, (uint32_t)(cnt * N * sizeof(T)), &bar);
+  };
+  if constexpr (STG) {
+    if (threadIdx.x == 0) stage_init(&bar);
+    __syncthreads();
+    if (threadIdx.x == 0 && blockIdx.x * lpc < nlines) issue(blockIdx.x * lpc);
+  }
+  int it = 0;
+  for (int k0 = blockIdx.x * lpc; k0 < nlines; k0 += step, ++it) {
     const int k = k0 + line;
     bool active = k < nlines;
     T* row = U + (size_t)(active ? k : 0) * N;
@@ -578,12 +695,25 @@ __global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl :
     }
     const bool zero_line = !active || (DIM == 2 && k == 0);
     // forward transform and spectral division into the raw line
-    dst_line<T, N, EPT>([&](int m, bool upper) {
-                          return active ? packed<T, N>(row, m, upper) : cx<T>{T(0), T(0)};
-                        },
-                        z0, z1, t, stw, tw, [&](int, int l, T x) {
-                          raw[l] = (zero_line || l == 0) ? T(0) : x * scale * recip(lk + lam[l]);
-                        });
+    auto divide = [&](int, int l, T x) {
+      raw[l] = (zero_line || l == 0) ? T(0) : x * scale * recip(lk + lam[l]);
+    };
+    if constexpr (STG) {
+      stage_wait(&bar, (uint32_t)(it & 1), err);
+      const T* src = stage + (size_t)line * N;
+      dst_line<T, N, EPT>(
+          [&](int m, bool upper) {
+            return active ? packed<T, N>(src, m, upper) : cx<T>{T(0), T(0)};
+          },
+          z0, z1, t, stw, tw, divide, [&] {
+            if (threadIdx.x == 0 && k0 + step < nlines) issue(k0 + step);
+          });
+    } else {
+      dst_line<T, N, EPT>([&](int m, bool upper) {
+                            return active ? packed<T, N>(row, m, upper) : cx<T>{T(0), T(0)};
+                          },
+                          z0, z1, t, stw, tw, divide);
+    }
     __syncthreads();
     dst_line<T, N, EPT>([&](int m, bool upper) { return packed<T, N>(raw, m, upper); }, z0, z1,
                         t, stw, tw, [&](int, int j, T x) {
@@ -596,7 +726,8 @@ __global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl :
 // dynamic shared memory of the two kernels
 template <typename T, int N, int EPT>
 __host__ __device__ constexpr size_t rows_smem(int lpc) {
-  return (size_t)lpc * line_buffers<T, N>() * line_len(N) * sizeof(cx<T>);
+  return rows_fft_bytes<T, N, EPT>() +
+         (rows_staged<T, N, EPT>() ? (size_t)lpc * N * sizeof(T) : 0);
 }
 template <typename T, int N, int EPT, int MAXT>
 __host__ __device__ constexpr size_t cols_smem() {
@@ -661,7 +792,7 @@ kfbi_status launch_rows(Ctx& c, const T* in, T* out, const cx<T>* tw, T scale, i
   static bool attr = false;
   if (!attr) {
     KFBI_CUDA_TRY(cudaFuncSetAttribute(rows_kernel<T, N, EPT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
   int per_sm = 0;
@@ -671,7 +802,8 @@ kfbi_status launch_rows(Ctx& c, const T* in, T* out, const cx<T>* tw, T scale, i
   int blocks = (nlines + lpc - 1) / lpc;
   blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
   const int pr = prof_begin(c, sizeof(T) == 4 ? ST_ROWS32 : ST_ROWS64);
-  rows_kernel<T, N, EPT><<<blocks, threads, smem, c.stream>>>(in, out, stw, tw, scale, nlines);
+  rows_kernel<T, N, EPT><<<blocks, threads, smem, c.stream>>>(in, out, stw, tw, scale, nlines,
+                                                              c.err_flag + 2);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
@@ -689,7 +821,7 @@ kfbi_status launch_cols(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   static bool attr = false;
   if (!attr) {
     KFBI_CUDA_TRY(cudaFuncSetAttribute(cols_kernel<T, N, EPT, MAXT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
   int per_sm = 0;
@@ -711,16 +843,16 @@ template <typename T, int N, int EPT>
 kfbi_status launch_ylines(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   constexpr CPlan P = cplan(N, EPT);
   constexpr int lpc = yline_lpc<T, N, EPT>();
-  static_assert((size_t)lpc * col_line_bytes<T, N>() <= 227 * 1024, "transposed column pass exceeds shared memory");
+  static_assert(yline_smem<T, N, EPT>() <= 227 * 1024, "transposed column pass exceeds shared memory");
   const cx<T>* stw = nullptr;
   KFBI_TRY((stage_table<T, N, EPT>(c, tw, &stw)));
   T* X = reinterpret_cast<T*>(c.XT);
   const int threads = lpc * P.tpl;
-  const size_t smem = (size_t)lpc * col_line_bytes<T, N>();
+  const size_t smem = yline_smem<T, N, EPT>();
   static bool attr = false;
   if (!attr) {
     KFBI_CUDA_TRY(cudaFuncSetAttribute(yline_kernel<T, N, EPT, 2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
   int per_sm = 0;
@@ -733,7 +865,7 @@ kfbi_status launch_ylines(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   KFBI_TRY(launch_transpose<T>(c, V, X, N, N, 1));
   const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
   yline_kernel<T, N, EPT, 2><<<blocks, threads, smem, c.stream>>>(X, stw, tw, lam, T(c.kappa2),
-                                                                  scale, N);
+                                                                  scale, N, c.err_flag + 2);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   KFBI_TRY(launch_transpose<T>(c, X, V, N, N, 1));

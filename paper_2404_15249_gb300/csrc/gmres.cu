@@ -437,7 +437,13 @@ kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const 
   }
   if (dens_out)
     KFBI_CUDA_TRY(cudaMemcpyAsync(dens_out, phi, sizeof(double) * M, cudaMemcpyDeviceToDevice, st));
+  int timeout = 0;           // a bounded wait of a transform kernel that gave up
+  KFBI_CUDA_TRY(cudaMemcpyAsync(&timeout, c.err_flag + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
   KFBI_CUDA_TRY(cudaStreamSynchronize(st));
+  if (timeout) {
+    set_error("kfbi_solve_bvp: a staged line copy did not complete (bounded wait expired)");
+    return KFBI_ERR_TIMEOUT;
+  }
   const double rel = gnorm > 0 ? res / gnorm : 0.0;
   if (info) {
     info->iterations = cnt.iters;
