@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--n3d", type=int, default=256,
                     help="grid size of the 3-D companion measurement (0: skip)")
+    ap.add_argument("--batch", type=int, default=256,
+                    help="problems in the batched companion measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -368,6 +370,9 @@ def run_kfbi(a):
     companion = None
     if rank == 0 and a.n3d > 0:
         companion = run_3d_companion(a, dev, flush)
+    batch = None
+    if rank == 0 and a.batch > 0:
+        batch = run_batch_companion(a, dev)
 
     launches = int(sum(v[1] for v in stages.values()))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -392,7 +397,8 @@ def run_kfbi(a):
             "stage_ms": {k: round(v[0] / a.steps, 4) for k, v in stages.items() if v[1]},
             "stage_launches": {k: int(v[1]) for k, v in stages.items() if v[1]},
             **fp64,
-            "companion_3d": companion}
+            "companion_3d": companion,
+            "companion_batch": batch}
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -456,6 +462,63 @@ def run_3d_companion(a, dev, flush):
             "applies_per_solve": applies, "iterations": info["iterations"],
             "err_inf_mixed": err_mixed, "fp64_solve_ms": ms64, "err_inf_fp64": err64,
             "fp64_iterations": info64["iterations"], "speedup_vs_fp64": ms64 / ms_mixed}
+
+
+def run_batch_companion(a, dev):
+    """The batched configuration (random star curves, N from {64, ..., 1024}, kappa ~ U(0,5),
+    4 right-hand sides per problem, mixed precision) through kfbi_batch_solve: setup of all
+    contexts, then the whole batch timed with CUDA events; errors against the exact
+    solutions.  Reported beside the 2-D line."""
+    import numpy as np
+    import torch
+    import kfbi_workloads as W
+    import paper_2404_15249_gb300 as K
+
+    nrhs = 4
+    cfg = W.config_batch(a.batch, nrhs)
+    t0 = time.perf_counter()
+    ctxs = [K.Kfbi2D(p.iface.pts, p.iface.normals, p.iface.curv, p.N, p.kappa,
+                     precision=K.KFBI_MIXED_FP32, gmres_m=100) for p, _ in cfg]
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    fg, fc, gc, ub, exact = [], [], [], [], []
+    for p, sols in cfg:
+        for sol in sols:
+            q = W.Problem(p.iface, p.N, p.kappa, sol)
+            fg.append(torch.as_tensor(q.f_grid(), device=dev))
+            fc.append(torch.as_tensor(q.f_ctrl(), device=dev))
+            gc.append(torch.as_tensor(q.g_ctrl(), device=dev))
+            ub.append(torch.empty((p.N + 1, p.N + 1), dtype=torch.float64, device=dev))
+            exact.append(q.u_grid())
+    K.batch_solve(ctxs, fg, fc, gc, ub, nrhs)          # warm-up
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    infos = K.batch_solve(ctxs, fg, fc, gc, ub, nrhs)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    pts_applies = 0.0
+    err = 0.0
+    for k, (p, _) in enumerate(cfg):
+        inside = ctxs[k].inside_mask().cpu().numpy().astype(bool)
+        for r in range(nrhs):
+            q = k * nrhs + r
+            i = infos[q]
+            pts_applies += (p.N + 1) ** 2 * (i["applies_fp64"] + i["applies_low"])
+            err = max(err, float(np.abs(ub[q].cpu().numpy() - exact[q])[inside].max()))
+    for c in ctxs:
+        c.close()
+    return {"workload": f"batched 2-D Poisson/Helmholtz: {a.batch} random star curves, "
+                        f"N from {{64..1024}}, M = 2N, kappa ~ U(0,5), {nrhs} right-hand sides "
+                        f"each, mixed precision, GMRES(100) to 1e-10 (with a restart of 50 a "
+                        f"few of these geometries stagnate near 1e-9)",
+            "problems": a.batch, "rhs": nrhs, "setup_s": setup_s, "batch_ms": ms,
+            "solves_per_s": a.batch * nrhs / (ms / 1e3),
+            "grid_pts_per_s_per_apply": pts_applies / (ms / 1e3),
+            "converged": sum(1 for i in infos if i["converged"]),
+            "max_rel_residual": max(i["rel_residual"] for i in infos),
+            "total_iterations": sum(i["iterations"] for i in infos), "max_err_inf": err}
 
 
 def main():

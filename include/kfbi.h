@@ -264,17 +264,22 @@ const char* kfbi_status_string(kfbi_status s);
 const char* kfbi_last_error(void);
 
 /* ---------------------------------------------------------------- batched problems
-   Many independent 2-D problems (uneven N and M) solved together: every GMRES step
-   runs one apply per problem with the problems' kernels launched back to back on the
-   same stream and the small Arnoldi kernels of all problems fused into single launches.
-   The contexts stay owned by the caller and must outlive the batch. */
+   Many independent problems (uneven N and M, 2-D or 3-D) solved together: a pool of up
+   to 8 host workers, each driving its own CUDA stream, takes problems from a shared queue
+   in decreasing order of cost ((N+1)^dim log N; longest first) and solves all right-hand
+   sides of a problem in turn, each with the context's own solver options, so up to 8
+   problems run concurrently on the device.  Each context is used by one worker at a
+   time.  The contexts stay owned by the caller and must outlive the batch. */
 typedef struct kfbi_batch_s* kfbi_batch;
 
 kfbi_status kfbi_batch_create(const kfbi_ctx* ctxs, int count, kfbi_batch* out);
 
 /* Solves count x nrhs BVPs: problem p, right-hand side r uses d_f_grid[p*nrhs + r],
    d_f_ctrl[...], d_g_ctrl[...] and writes d_u_grid[p*nrhs + r] (device pointers, layout
-   as in kfbi_solve_bvp).  h_info: count*nrhs structs or NULL.  Synchronising. */
+   as in kfbi_solve_bvp).  h_info: count*nrhs structs or NULL.  The work starts after
+   everything already queued on `stream` and is finished when the call returns
+   (synchronising).  The first failing solve stops the batch and its status is returned;
+   KFBI_ERR_NOT_CONVERGED if some solve hit its iteration limit. */
 kfbi_status kfbi_batch_solve(kfbi_batch b, int nrhs, const double* const* d_f_grid,
                              const double* const* d_f_ctrl, const double* const* d_g_ctrl,
                              double* const* d_u_grid, kfbi_solve_info* h_info, void* stream);

@@ -26,8 +26,11 @@ CPU predecessor; the readings used here (derived from the interface conditions) 
       iff an odd number of row-j crossings have x_q <= x_i (a node on Gamma joins the
       side to its right); on every grid line (row or column) the k-th crossing in
       increasing order belongs to the k-th arm whose end labels differ and must lie on
-      that arm (1e-8 h slack), else GeometryError (tangency, double crossing); no node
-      within two cells of the box boundary may be inside;
+      that arm (1e-8 h slack), else GeometryError; two consecutive crossings strictly
+      inside one arm whose end labels agree (a grid line grazing Gamma where its radius
+      of curvature exceeds 2 h) are dropped first: they carry no correction; no node
+      within two cells of the box boundary may be inside; the interface is rejected as
+      under-resolved when |curvature| h > 4 at a control point (radius below h/4);
   R6  jumps in the local frame (xi = n, eta = tau):
         [v] = Phi, [v_xi] = psi, [v_eta] = Phi_s, [v_eta eta] = Phi_ss + chi psi,
         [v_xi eta] = psi_s - chi Phi_s, [v_xi xi] = [F] + kappa^2 Phi - Phi_ss - chi psi;
@@ -49,6 +52,8 @@ SUBSAMPLES = 8           # R4
 BISECTION_STEPS = 64     # bracket shrinks to 2^-67 of a segment: below FP64 resolution
 SNAP = 1e-10             # a crossing this close (in units of h) to a node lies on it (R5)
 ARM_TOL = 1e-8           # slack (units of h) when matching crossings to arms (R5)
+GRAZE_CURV = 0.5         # a grazing pair is accepted where |curvature| h <= this (R5)
+MAX_CURV_H = 4.0         # |curvature| h above this at a control point: under-resolved (R5)
 
 
 class GeometryError(ValueError):
@@ -121,6 +126,8 @@ class Geometry2D:
         self.xs = self.lo + np.arange(self.N + 1, dtype=np.float64) * self.h
         self.dt = 2.0 * np.pi / self.M
         self._stencil_idx = (np.arange(self.M)[:, None] + np.arange(-2, 4)[None, :]) % self.M
+        if np.max(np.abs(self.curv)) * self.h > MAX_CURV_H:
+            raise GeometryError("radius of curvature below a quarter cell (under-resolved interface)")
         self._find_crossings()
         self._classify()
         self._arms()
@@ -216,10 +223,28 @@ class Geometry2D:
         self.inside = inside
 
     # ------------------------------------------------------------ arms (R5, R7)
-    def _match_line(self, labels, lst, coord):
-        """k-th crossing (sorted) on a grid line <-> k-th arm whose end labels differ."""
+    def _match_line(self, labels, lst, coord, curv):
+        """k-th crossing (sorted) on a grid line <-> k-th arm whose end labels differ, after
+        dropping grazing pairs: two consecutive crossings strictly inside one arm (more
+        than ARM_TOL h from its nodes) whose end labels agree, where the curve is resolved
+        (|curvature| h <= GRAZE_CURV at both), carry no correction (R5)."""
         flips = np.nonzero(labels[1:] != labels[:-1])[0]
         order = lst[np.argsort(coord[lst], kind="stable")]
+        tol = ARM_TOL * self.h
+        keep, q = [], 0
+        while q < order.size:
+            if q + 1 < order.size:
+                a0, a1 = coord[order[q]], coord[order[q + 1]]
+                t = int(np.floor((a0 - self.lo) / self.h))
+                if (0 <= t < self.N and a0 > self.xs[t] + tol and a1 < self.xs[t + 1] - tol
+                        and labels[t] == labels[t + 1]
+                        and curv[order[q]] * self.h <= GRAZE_CURV
+                        and curv[order[q + 1]] * self.h <= GRAZE_CURV):
+                    q += 2
+                    continue
+            keep.append(order[q])
+            q += 1
+        order = np.asarray(keep, dtype=np.int64)
         if flips.size != order.size:
             raise GeometryError("a grid line meets the interface at a point where the "
                                 "node labels do not change (tangency or under-resolution)")
@@ -233,8 +258,12 @@ class Geometry2D:
         N, ins = self.N, self.inside
         xq_rows = self.crossings[1]["pos"][:, 0]
         yq_cols = self.crossings[0]["pos"][:, 1]
-        harm = [self._match_line(ins[j, :], self.row_lists[j], xq_rows) for j in range(N + 1)]
-        varm = [self._match_line(ins[:, i], self.col_lists[i], yq_cols) for i in range(N + 1)]
+        def abs_curv(cr):
+            X1, X2 = cr["X1"], cr["X2"]
+            return np.abs(X1[:, 0] * X2[:, 1] - X1[:, 1] * X2[:, 0]) / np.hypot(X1[:, 0], X1[:, 1]) ** 3
+        kr, kc = abs_curv(self.crossings[1]), abs_curv(self.crossings[0])
+        harm = [self._match_line(ins[j, :], self.row_lists[j], xq_rows, kr) for j in range(N + 1)]
+        varm = [self._match_line(ins[:, i], self.col_lists[i], yq_cols, kc) for i in range(N + 1)]
         h_diff = ins[:, 1:] != ins[:, :-1]
         v_diff = ins[1:, :] != ins[:-1, :]
         irr = np.zeros_like(ins)

@@ -11,6 +11,8 @@ namespace kfbi {
 
 static thread_local char g_err[512] = "";
 
+const char* last_error_message() { return g_err; }
+
 void set_error(const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);

@@ -26,6 +26,8 @@
 // partner value Z_{N-k} from shared memory.
 #pragma once
 
+#include <atomic>
+
 #include "kfbi_internal.cuh"
 
 namespace kfbi {
@@ -752,13 +754,12 @@ __global__ void stage_twiddles_kernel(const cx<T>* __restrict__ tw, cx<T>* __res
 
 // ---------------------------------------------------------------------------- launch
 inline int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
+  static const int n = [] {            // initialised once, thread-safe
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
   return n;
 }
 
@@ -789,7 +790,7 @@ kfbi_status launch_rows(Ctx& c, const T* in, T* out, const cx<T>* tw, T scale, i
   static_assert(rows_smem<T, N, EPT>(lpc) <= 227 * 1024, "row pass exceeds shared memory");
   const int threads = lpc * P.tpl;
   const size_t smem = rows_smem<T, N, EPT>(lpc);
-  static bool attr = false;
+  static std::atomic<bool> attr{false};   // set once per process (any host thread)
   if (!attr) {
     KFBI_CUDA_TRY(cudaFuncSetAttribute(rows_kernel<T, N, EPT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -818,7 +819,7 @@ kfbi_status launch_cols(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   static_assert(cols_smem<T, N, EPT, MAXT>() <= 227 * 1024, "column pass exceeds shared memory");
   const int threads = L * P.tpl;
   const size_t smem = cols_smem<T, N, EPT, MAXT>();
-  static bool attr = false;
+  static std::atomic<bool> attr{false};   // set once per process (any host thread)
   if (!attr) {
     KFBI_CUDA_TRY(cudaFuncSetAttribute(cols_kernel<T, N, EPT, MAXT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -849,7 +850,7 @@ kfbi_status launch_ylines(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   T* X = reinterpret_cast<T*>(c.XT);
   const int threads = lpc * P.tpl;
   const size_t smem = yline_smem<T, N, EPT>();
-  static bool attr = false;
+  static std::atomic<bool> attr{false};   // set once per process (any host thread)
   if (!attr) {
     KFBI_CUDA_TRY(cudaFuncSetAttribute(yline_kernel<T, N, EPT, 2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -6,13 +6,19 @@
 // precision is relaxed as the residual drops (inexact Krylov), every restart cycle ending
 // with the true residual from an FP64-accurate apply (an iterative-refinement step).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <numeric>
+#include <string>
+#include <thread>
+#include <vector>
 
 #include "kfbi_internal.cuh"
 
 namespace kfbi {
 
 constexpr int RED_T = 256;
+constexpr int kBatchWorkers = 8;     // concurrent problems of a batch
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -456,24 +462,78 @@ kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const 
   return rel <= c.opt.tol ? KFBI_OK : KFBI_ERR_NOT_CONVERGED;
 }
 
-// Batched BVPs: problems in turn on one stream, every right-hand side solved with the
-// context's own options.
+// Batched BVPs: a pool of host workers, each with its own CUDA stream, takes problems from
+// a shared queue in decreasing order of cost ((N+1)^dim log N per apply; longest first)
+// and solves all right-hand sides of a problem in turn.  Problems never share a context,
+// so their solves run concurrently on the device; the caller's stream is joined at both
+// ends (the batch starts after work already on it and is complete when the call returns).
 kfbi_status batch_solve(kfbi_ctx* ctxs, int count, int nrhs, const double* const* f_grid,
                         const double* const* f_ctrl, const double* const* g_ctrl,
                         double* const* u_grid, kfbi_solve_info* info, cudaStream_t stream) {
-  kfbi_status worst = KFBI_OK;
-  for (int p = 0; p < count; ++p) {
-    Ctx& c = ctxs[p]->c;
-    c.stream = stream;
-    for (int r = 0; r < nrhs; ++r) {
-      const int q = p * nrhs + r;
-      kfbi_status s = solve_bvp(c, f_grid[q], f_ctrl[q], g_ctrl[q], u_grid[q], nullptr,
-                                info ? info + q : nullptr);
-      if (s != KFBI_OK && s != KFBI_ERR_NOT_CONVERGED) return s;
-      if (s != KFBI_OK) worst = s;
+  int dev = 0;
+  KFBI_CUDA_TRY(cudaGetDevice(&dev));
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  auto cost = [&](int p) {
+    const Ctx& c = ctxs[p]->c;
+    const double n = c.N + 1.0;
+    return (c.dim == 3 ? n * n * n : n * n) * std::log2((double)c.N);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  const int workers = std::max(1, std::min(count, kBatchWorkers));
+  cudaEvent_t start;
+  KFBI_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  KFBI_CUDA_TRY(cudaEventRecord(start, stream));
+  std::atomic<int> next{0};
+  std::vector<kfbi_status> wstatus(workers, KFBI_OK);
+  std::vector<std::string> wmsg(workers);
+  std::vector<int> not_converged(workers, 0);
+  auto work = [&](int w) {
+    cudaSetDevice(dev);
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamWaitEvent(st, start, 0) != cudaSuccess) {
+      wstatus[w] = KFBI_ERR_CUDA;
+      wmsg[w] = "kfbi_batch_solve: stream creation failed";
+      if (st) cudaStreamDestroy(st);
+      return;
     }
-  }
-  return worst;
+    for (int k = next.fetch_add(1); k < count; k = next.fetch_add(1)) {
+      const int p = order[k];
+      Ctx& c = ctxs[p]->c;
+      c.stream = st;
+      for (int r = 0; r < nrhs; ++r) {
+        const int q = p * nrhs + r;
+        const kfbi_status s = solve_bvp(c, f_grid[q], f_ctrl[q], g_ctrl[q], u_grid[q], nullptr,
+                                        info ? info + q : nullptr);
+        if (s == KFBI_ERR_NOT_CONVERGED) {
+          not_converged[w] = 1;
+        } else if (s != KFBI_OK) {
+          wstatus[w] = s;
+          wmsg[w] = last_error_message();
+          next.store(count);               // stop the other workers at their next problem
+          break;
+        }
+      }
+      c.stream = stream;
+      if (wstatus[w] != KFBI_OK) break;
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < workers; ++w) pool.emplace_back(work, w);
+  work(0);
+  for (auto& t : pool) t.join();
+  cudaEventDestroy(start);
+  for (int w = 0; w < workers; ++w)
+    if (wstatus[w] != KFBI_OK) {
+      set_error("%s", wmsg[w].c_str());
+      return wstatus[w];
+    }
+  for (int w = 0; w < workers; ++w)
+    if (not_converged[w]) return KFBI_ERR_NOT_CONVERGED;
+  return KFBI_OK;
 }
 
 }  // namespace kfbi

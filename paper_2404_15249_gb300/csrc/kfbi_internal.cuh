@@ -11,6 +11,7 @@
 namespace kfbi {
 
 void set_error(const char* fmt, ...);
+const char* last_error_message();          // this thread's last set_error text
 
 #define KFBI_CUDA_TRY(expr)                                                          \
   do {                                                                               \

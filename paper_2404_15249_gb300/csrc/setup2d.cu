@@ -20,11 +20,15 @@
 #include <cstdarg>
 #include <cstring>
 
+#include <vector>
+
 #include "kfbi_internal.cuh"
 
 namespace kfbi {
 
 enum : int { ERR_GEOM_EDGE = 1, ERR_GEOM_MATCH = 2, ERR_GEOM_TOL = 4, ERR_GEOM_ARM = 8 };
+constexpr double GRAZE_CURV = 0.5;   // |curvature| h of an accepted grazing pair
+constexpr double MAX_CURV_H = 4.0;   // |curvature| h above this at a control point: rejected
 
 constexpr int SUB = 8;
 constexpr int BISECT = 64;
@@ -224,18 +228,59 @@ __global__ void labels_kernel(int N, double lo, double h, const int* row_ptr,
 }
 
 // one thread per grid line: the k-th crossing <-> the k-th arm with a label change
+// |curvature| of the interpolant at (seg, tau): |X' x X''| / |X'|^3 (the t-scaling cancels)
+__device__ double abs_curvature(const double* pts, int M, int seg, double tau) {
+  double L0[6], L1[6], L2[6];
+  lagrange6(tau, L0, L1, L2);
+  double x1 = 0, y1 = 0, x2 = 0, y2 = 0;
+  for (int r = 0; r < 6; ++r) {
+    int k = seg - 2 + r;
+    k = (k % M + M) % M;
+    x1 += L1[r] * pts[2 * k];
+    y1 += L1[r] * pts[2 * k + 1];
+    x2 += L2[r] * pts[2 * k];
+    y2 += L2[r] * pts[2 * k + 1];
+  }
+  const double s = sqrt(x1 * x1 + y1 * y1);
+  return fabs(x1 * y2 - y1 * x2) / (s * s * s);
+}
+
 __global__ void match_kernel(int N, double lo, double h, int axis, const int* ptr,
-                             const double* along, const uint8_t* inside, int* flip, int* err) {
+                             const double* along, const int* seg, const double* tau,
+                             const double* pts, int M, const uint8_t* inside, int* flip, int* err) {
   const int L = blockIdx.x * blockDim.x + threadIdx.x;
   if (L > N) return;
-  int r = ptr[L];
-  const int e = ptr[L + 1];
+  const int b = ptr[L], e = ptr[L + 1];
   const double tol = ARM_TOL * h;
   // axis 1 crossings lie on row L (walk i); axis 0 crossings on column L (walk j)
-  uint8_t prev = axis ? inside[L * (N + 1)] : inside[L];
+  auto label = [&](int t) -> uint8_t {
+    return axis ? inside[L * (N + 1) + t] : inside[t * (N + 1) + L];
+  };
+  // grazing pairs: two consecutive crossings strictly inside one arm whose end labels
+  // agree, on a part of the curve resolved by the grid (radius of curvature above 2 h),
+  // carry no correction; marked -2 - arm until the end
+  for (int q = b; q < e;) {
+    if (q + 1 < e) {
+      const double a0 = along[q], a1 = along[q + 1];
+      const int t = (int)floor((a0 - lo) / h);
+      if (t >= 0 && t < N && a0 > grid_coord(lo, t, h) + tol && a1 < grid_coord(lo, t + 1, h) - tol &&
+          label(t) == label(t + 1) && abs_curvature(pts, M, seg[q], tau[q]) * h <= GRAZE_CURV &&
+          abs_curvature(pts, M, seg[q + 1], tau[q + 1]) * h <= GRAZE_CURV) {
+        flip[q] = flip[q + 1] = -2 - t;
+        q += 2;
+        continue;
+      }
+    }
+    flip[q] = -1;
+    ++q;
+  }
+  // every other crossing, in order, belongs to the next arm whose end labels differ
+  int r = b;
+  uint8_t prev = label(0);
   for (int t = 0; t < N; ++t) {
-    const uint8_t next = axis ? inside[L * (N + 1) + t + 1] : inside[(t + 1) * (N + 1) + L];
+    const uint8_t next = label(t + 1);
     if (next != prev) {
+      while (r < e && flip[r] <= -2) ++r;
       if (r >= e) { atomicOr(err, ERR_GEOM_MATCH); return; }
       const double a = along[r];
       if (a < grid_coord(lo, t, h) - tol || a > grid_coord(lo, t + 1, h) + tol) {
@@ -247,7 +292,10 @@ __global__ void match_kernel(int N, double lo, double h, int axis, const int* pt
     }
     prev = next;
   }
-  if (r != e) atomicOr(err, ERR_GEOM_MATCH);
+  while (r < e && flip[r] <= -2) ++r;
+  if (r != e) { atomicOr(err, ERR_GEOM_MATCH); return; }
+  for (int q = b; q < e; ++q)
+    if (flip[q] <= -2) flip[q] = -2 - flip[q];     // arm of the grazing pair (never looked up)
 }
 
 __global__ void count_inside_kernel(int n, const uint8_t* inside, int* out) {
@@ -503,6 +551,19 @@ kfbi_status setup_geometry(Ctx& c) {
   cudaStream_t st = c.stream;
   int* tmp_i = nullptr;
   KFBI_CUDA_TRY(cudaMemsetAsync(c.err_flag, 0, sizeof(int), st));
+  {
+    // the grid must resolve the curve: radius of curvature of at least a quarter cell
+    std::vector<double> curv(M);
+    KFBI_CUDA_TRY(cudaMemcpyAsync(curv.data(), c.curv, sizeof(double) * M, cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA_TRY(cudaStreamSynchronize(st));
+    double kmax = 0.0;
+    for (double k : curv) kmax = fmax(kmax, fabs(k));
+    if (!(kmax * c.h <= MAX_CURV_H)) {
+      set_error("kfbi_setup: interface geometry rejected: radius of curvature below a quarter cell "
+                "(max |curvature| h = %.3g, under-resolved interface)", kmax * c.h);
+      return KFBI_ERR_GEOMETRY;
+    }
+  }
 
   // samples and crossings
   double* samp = nullptr;
@@ -583,8 +644,8 @@ kfbi_status setup_geometry(Ctx& c) {
   for (int ax = 0; ax < 2; ++ax) {
     prof_count(c, ST_SETUP);
     match_kernel<<<nblk(N + 1, 64), 64, 0, st>>>(N, c.lo, c.h, ax, c.line_ptr[ax],
-                                                 c.cr_along[ax], c.inside, c.cr_flip[ax],
-                                                 c.err_flag);
+                                                 c.cr_along[ax], c.cr_seg[ax], c.cr_tau[ax],
+                                                 c.pts, M, c.inside, c.cr_flip[ax], c.err_flag);
   }
   KFBI_CUDA_TRY(cudaGetLastError());
   int* d_inside_cnt = counts;   // reuse scratch
