@@ -243,7 +243,8 @@ kfbi_status kfbi_set_solver(kfbi_ctx ctx, int precision, int gmres_m, int max_re
    3 DST columns FP32 (the y-transform pair with the spectral division; in 3-D the
    z-transform pair), 4 DST rows FP64, 5 DST columns FP64, 6 interpolation, 7 dense grid
    build/copy, 8 Krylov vector kernels, 9 residual refinement of FP32 box solves,
-   10 tile transposes of the work grid.  Launch counts are always
+   10 tile transposes of the work grid, 11 the sparse first x-transform of the plain FP32
+   2-D apply (evaluated from the irregular nodes straight into the transposed layout).  Launch counts are always
    kept; times only while profiling is on (enabling clears both). */
 #define KFBI_NSTAGES 16
 typedef struct {

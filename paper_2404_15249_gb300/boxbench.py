@@ -1,4 +1,5 @@
-"""Box-solve micro-benchmark: kfbi_box_solve (Alg. 4) alone, on a flower context.
+"""Box-solve micro-benchmark: kfbi_box_solve (Alg. 4) alone (or, with --apply, one
+double-layer apply), on a flower context.
 
     python -m paper_2404_15249_gb300.boxbench --N 8192 --precision 1 --reps 5
 
@@ -26,6 +27,8 @@ def main(argv=None):
     ap.add_argument("--kappa", type=float, default=1.0)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--apply", action="store_true",
+                    help="time kfbi_apply_layer_potential (double layer) instead of the box solve")
     a = ap.parse_args(argv)
 
     import torch
@@ -40,10 +43,16 @@ def main(argv=None):
     v = torch.empty_like(b)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=b.device)
 
+    dens = torch.as_tensor(W.random_density(iface.M), dtype=torch.float64).cuda()
+    out = torch.empty_like(dens)
+
     def solve():
-        st = lib().kfbi_box_solve(ctx.handle, a.precision, _ptr(b), _ptr(v), None)
+        if a.apply:
+            st = lib().kfbi_apply_layer_potential(ctx.handle, 0, a.precision, _ptr(dens), _ptr(out), None)
+        else:
+            st = lib().kfbi_box_solve(ctx.handle, a.precision, _ptr(b), _ptr(v), None)
         if st != 0:
-            raise RuntimeError(f"kfbi_box_solve failed with status {st}")
+            raise RuntimeError(f"kfbi call failed with status {st}")
 
     for _ in range(a.warmup):
         solve()
@@ -61,7 +70,9 @@ def main(argv=None):
     ms = statistics.median(times)
     # plain solves only: a refined solve runs several transforms plus residual passes
     nbytes = 3 * 2.0 * N * N * (8 if a.precision == 0 else 4) if a.precision in (0, 1) else None
-    print(json.dumps({"N": N, "precision": a.precision, "ms_per_solve": ms,
+    if a.apply:
+        nbytes = None
+    print(json.dumps({"N": N, "precision": a.precision, "apply": a.apply, "ms_per_solve": ms,
                       "times_ms": times, "dst_variant": list(info["dst_variant"]),
                       "transform_bytes": nbytes,
                       "transform_GBps": nbytes / ms / 1e6 if nbytes else None}))

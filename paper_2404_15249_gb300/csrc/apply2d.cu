@@ -146,6 +146,48 @@ __global__ void split_kernel(long n, const double* __restrict__ b, float* __rest
   }
 }
 
+// ------------------------------------------------------------------ sparse plain apply
+// The double-layer right-hand side is nonzero only at irregular nodes, so the plain FP32
+// apply evaluates the first sine transform (along x) directly on them (the same DST-I sums,
+// in another order), written straight into the transposed layout of the column pass:
+// X[k][j] = sum over irregular (i, j) of b_ij sin(pi i k / N), in the transposed layout
+// of the column pass.  A thread takes one row j and 32 consecutive modes k; along k the
+// sine follows by rotation from the table value at the first mode (32 steps).
+constexpr int SPARSE_KB = 32;
+
+__global__ void sparse_rows_t_kernel(int N, const int* __restrict__ irr_node,
+                                     const int* __restrict__ rowptr, const float* __restrict__ B,
+                                     const float2* __restrict__ tw, float* __restrict__ X) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k0 = blockIdx.y * SPARSE_KB;
+  if (j >= N) return;
+  float acc[SPARSE_KB];
+#pragma unroll
+  for (int kk = 0; kk < SPARSE_KB; ++kk) acc[kk] = 0.f;
+  if (j > 0) {
+    for (int n = rowptr[j - 1]; n < rowptr[j]; ++n) {
+      const int node = irr_node[n];
+      const int i = node - j * N;
+      const float b = B[node];
+      const float2 t0 = tw[(int)(((long)i * k0) % (2 * N))], ti = tw[i];
+      float cs = t0.x, sn = -t0.y;
+      const float C = ti.x, S = -ti.y;
+#pragma unroll
+      for (int kk = 0; kk < SPARSE_KB; ++kk) {
+        acc[kk] = fmaf(b, sn, acc[kk]);
+        const float cn = cs * C - sn * S;
+        sn = fmaf(sn, C, cs * S);
+        cs = cn;
+      }
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < SPARSE_KB; ++kk) {
+    const int k = k0 + kk;
+    if (k < N) X[(size_t)k * N + j] = (k == 0) ? 0.f : acc[kk];
+  }
+}
+
 // ------------------------------------------------------------------ grid kernels
 // dense right-hand side on the N x N work grid: F at inside interior nodes, else 0
 template <typename T>
@@ -312,6 +354,19 @@ kfbi_status apply_potential(Ctx& c, Layer layer, int precision, const double* de
   }
   const int steps = refine_steps_of(precision);
   KFBI_TRY(correct<float>(c, d, s, nullptr, c.B32, 0, steps ? c.B64 : nullptr));
+  if (steps == 0 && c.irr_rowptr && c.dim == 2) {
+    // sparse first x-transform, then the dense y-transform pair and the last x-transform
+    float* X = reinterpret_cast<float*>(c.XT);
+    const float2* tw = reinterpret_cast<const float2*>(c.t32.tw);
+    int pr = prof_begin(c, ST_SPARSE);
+    sparse_rows_t_kernel<<<dim3((c.N + 127) / 128, (c.N + SPARSE_KB - 1) / SPARSE_KB), 128, 0,
+                           c.stream>>>(c.N, c.irr_node, c.irr_rowptr, c.B32, tw, X);
+    prof_end(c, pr);
+    KFBI_CUDA_TRY(cudaGetLastError());
+    KFBI_TRY(ylines_f32(c, X));
+    KFBI_TRY(x_pass_f32(c, X, c.V32));
+    return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out);
+  }
   if (steps == 0) {
     KFBI_TRY(box_solve_f32(c, c.B32, c.V32));
     return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out);

@@ -436,7 +436,7 @@ kfbi_status kfbi_profile_read(kfbi_ctx ctx, kfbi_stage_times* out) {
 const char* kfbi_stage_name(int s) {
   static const char* names[] = {"setup", "correction", "dst_rows_f32", "dst_cols_f32",
                                 "dst_rows_f64", "dst_cols_f64", "interpolation", "grid",
-                                "krylov", "refine", "transpose"};
+                                "krylov", "refine", "transpose", "sparse_x_f32"};
   return (s >= 0 && s < kfbi::ST_COUNT) ? names[s] : "unused";
 }
 

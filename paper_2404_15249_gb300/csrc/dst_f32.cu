@@ -14,4 +14,13 @@ kfbi_status autotune_f32(Ctx& c) {
                                      c.t32.lam);
 }
 
+kfbi_status x_pass_f32(Ctx& c, const float* X, float* V) {
+  return dst::x_pass_dispatch<float>(c, X, V, reinterpret_cast<const dst::cx<float>*>(c.t32.tw));
+}
+
+kfbi_status ylines_f32(Ctx& c, float* X) {
+  return dst::ylines_dispatch<float>(c, X, reinterpret_cast<const dst::cx<float>*>(c.t32.tw),
+                                     c.t32.lam);
+}
+
 }  // namespace kfbi

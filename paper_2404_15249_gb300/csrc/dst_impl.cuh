@@ -873,6 +873,60 @@ kfbi_status launch_ylines(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   return KFBI_OK;
 }
 
+// the y-transform pair alone on an already transposed grid (2-D, N lines)
+template <typename T, int N, int EPT>
+kfbi_status launch_ylines_only(Ctx& c, T* X, const cx<T>* tw, const T* lam) {
+  constexpr CPlan P = cplan(N, EPT);
+  constexpr int lpc = yline_lpc<T, N, EPT>();
+  const cx<T>* stw = nullptr;
+  KFBI_TRY((stage_table<T, N, EPT>(c, tw, &stw)));
+  const int threads = lpc * P.tpl;
+  const size_t smem = yline_smem<T, N, EPT>();
+  static std::atomic<bool> attr{false};
+  if (!attr) {
+    KFBI_CUDA_TRY(cudaFuncSetAttribute(yline_kernel<T, N, EPT, 2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  int per_sm = 0;
+  KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yline_kernel<T, N, EPT, 2>,
+                                                              threads, smem));
+  if (per_sm < 1) per_sm = 1;
+  int blocks = (N + lpc - 1) / lpc;
+  blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
+  const T scale = T((2.0 / N) * (2.0 / N));
+  const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
+  yline_kernel<T, N, EPT, 2><<<blocks, threads, smem, c.stream>>>(X, stw, tw, lam, T(c.kappa2),
+                                                                  scale, N, c.err_flag + 2);
+  prof_end(c, pr);
+  KFBI_CUDA_TRY(cudaGetLastError());
+  return KFBI_OK;
+}
+
+template <typename T>
+kfbi_status ylines_dispatch(Ctx& c, T* X, const cx<T>* tw, const T* lam) {
+  const bool half = (c.cols_variant[sizeof(T) == 8] & 2) != 0;
+  switch (c.N) {
+#define KFBI_CASE(n)                                                                          \
+  case n:                                                                                     \
+    if (half && n / (default_ept(n) / 2) <= 512)                                              \
+      return launch_ylines_only<T, n, default_ept(n) / 2>(c, X, tw, lam);                     \
+    return launch_ylines_only<T, n, default_ept(n)>(c, X, tw, lam);
+    KFBI_CASE(32) KFBI_CASE(48) KFBI_CASE(64) KFBI_CASE(96) KFBI_CASE(128) KFBI_CASE(192)
+    KFBI_CASE(256) KFBI_CASE(384) KFBI_CASE(512) KFBI_CASE(768) KFBI_CASE(1024)
+    KFBI_CASE(1536) KFBI_CASE(2048) KFBI_CASE(3072) KFBI_CASE(4096) KFBI_CASE(6144)
+    KFBI_CASE(8192)
+#undef KFBI_CASE
+  }
+  set_error("y-transform pass: no compiled plan for N = %d", c.N);
+  return KFBI_ERR_UNSUPPORTED;
+}
+
+// transpose X (x-modes as rows) back into V and DST-I its rows (the last pass of a box
+// solve whose column pass ran on X)
+template <typename T>
+kfbi_status x_pass_dispatch(Ctx& c, const T* X, T* V, const cx<T>* tw);
+
 // Kernel variants chosen by the setup-time autotuner.  Row pass: 0 = default EPT (16 or
 // 24 values per thread), 1 = half (8 or 12).  Column pass: bit 0 = CTAs of at most 256
 // threads (one column tile per 256 threads, two CTAs per SM) instead of 512, bit 1 =
@@ -942,6 +996,23 @@ kfbi_status box_solve_n(Ctx& c, const T* rhs, T* work, const cx<T>* tw, const T*
   KFBI_TRY((launch_cols_v<T, N>(c, work, tw, lam, cv)));
   KFBI_TRY((launch_rows_v<T, N>(c, work, work, tw, T(1), rv)));
   return KFBI_OK;
+}
+
+template <typename T>
+kfbi_status x_pass_dispatch(Ctx& c, const T* X, T* V, const cx<T>* tw) {
+  KFBI_TRY(launch_transpose<T>(c, X, V, c.N, c.N, 1));
+  const int rv = c.rows_variant[sizeof(T) == 8];
+  switch (c.N) {
+#define KFBI_CASE(n) \
+  case n: return launch_rows_v<T, n>(c, V, V, tw, T(1), rv);
+    KFBI_CASE(32) KFBI_CASE(48) KFBI_CASE(64) KFBI_CASE(96) KFBI_CASE(128) KFBI_CASE(192)
+    KFBI_CASE(256) KFBI_CASE(384) KFBI_CASE(512) KFBI_CASE(768) KFBI_CASE(1024)
+    KFBI_CASE(1536) KFBI_CASE(2048) KFBI_CASE(3072) KFBI_CASE(4096) KFBI_CASE(6144)
+    KFBI_CASE(8192)
+#undef KFBI_CASE
+  }
+  set_error("row pass: no compiled plan for N = %d", c.N);
+  return KFBI_ERR_UNSUPPORTED;
 }
 
 template <typename T>

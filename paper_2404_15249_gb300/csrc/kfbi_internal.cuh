@@ -61,7 +61,8 @@ struct BoxTables {
 // ------------------------------------------------------------------ stage timers
 enum Stage : int {
   ST_SETUP = 0, ST_CORR = 1, ST_ROWS32 = 2, ST_COLS32 = 3, ST_ROWS64 = 4, ST_COLS64 = 5,
-  ST_INTERP = 6, ST_GRID = 7, ST_KRYLOV = 8, ST_REFINE = 9, ST_TRANS = 10, ST_COUNT = 11
+  ST_INTERP = 6, ST_GRID = 7, ST_KRYLOV = 8, ST_REFINE = 9, ST_TRANS = 10, ST_SPARSE = 11,
+  ST_COUNT = 12   // ST_SPARSE: the sparse first x-transform of the plain FP32 2-D apply
 };
 
 struct Prof {
@@ -102,6 +103,7 @@ struct Ctx {
   // irregular nodes and their crossed arms (CSR)
   int nirr = 0, narms = 0;
   int* irr_node = nullptr;                    // work-grid index j*N + i
+  int* irr_rowptr = nullptr;                  // 2-D: row j's nodes [rowptr[j-1], rowptr[j])
   int* arm_ptr = nullptr;                     // nirr + 1
   int* arm_seg = nullptr;                     // narms: segment of the crossing
   double* arm_wD = nullptr;                   // narms x 6: density -> correction (double layer)
@@ -186,6 +188,10 @@ kfbi_status alloc_bytes(Ctx& c, void** p, size_t bytes);
 // right-hand side from `rhs` (may equal work).
 kfbi_status box_solve_f32(Ctx& c, const float* rhs, float* work);
 kfbi_status box_solve_f64(Ctx& c, const double* rhs, double* work);
+// the y-transform pair with the spectral division on the transposed FP32 grid X in place,
+// and the last half of the box solve: transpose X back into V and transform its rows
+kfbi_status ylines_f32(Ctx& c, float* X);
+kfbi_status x_pass_f32(Ctx& c, const float* X, float* V);
 kfbi_status init_box_tables(Ctx& c);
 kfbi_status autotune_f32(Ctx& c);   // column-pass variant per precision, on scratch grids
 kfbi_status autotune_f64(Ctx& c);

@@ -20,6 +20,7 @@
 #include <cstdarg>
 #include <cstring>
 
+#include <algorithm>
 #include <vector>
 
 #include "kfbi_internal.cuh"
@@ -725,6 +726,8 @@ kfbi_status setup_geometry(Ctx& c) {
     set_error("interface geometry rejected while building stencils (code %d)", h_err);
     return KFBI_ERR_GEOMETRY;
   }
+  c.irr_rowptr = node_off;       // row j (1 <= j < N) holds irregular nodes [j-1], [j]
+
   return KFBI_OK;
 }
 
