@@ -64,8 +64,13 @@ typedef enum {
                             (exact FP32-pair) arithmetic at regular nodes and in FP64 at
                             irregular nodes: FP64-accurate (about 1e-13 relative) at FP32
                             cost; the mixed BVP solver uses it for its accurate steps    */
-  KFBI_FP32_REFINED_ONCE = 3  /* one refinement step (about 1e-11 relative at N = 1024,
+  KFBI_FP32_REFINED_ONCE = 3, /* one refinement step (about 1e-11 relative at N = 1024,
                             3e-10 at N = 4096)                                           */
+  KFBI_TF32X3 = 4        /* box solve in the dense form of Alg. 4 (full diagonalisation by
+                            the sine matrix) as four GEMMs on the tcgen05 tensor cores, TF32
+                            with a three-term split and FP32 accumulation (FP32-class
+                            accuracy, about 1e-6 relative); 2-D, N a multiple of 128 up to
+                            4096; an apply / box-solve / interface-solve precision        */
 } kfbi_precision;
 
 typedef enum {
@@ -244,7 +249,8 @@ kfbi_status kfbi_set_solver(kfbi_ctx ctx, int precision, int gmres_m, int max_re
    z-transform pair), 4 DST rows FP64, 5 DST columns FP64, 6 interpolation, 7 dense grid
    build/copy, 8 Krylov vector kernels, 9 residual refinement of FP32 box solves,
    10 tile transposes of the work grid, 11 the sparse first x-transform of the plain FP32
-   2-D apply (evaluated from the irregular nodes straight into the transposed layout).  Launch counts are always
+   2-D apply (evaluated from the irregular nodes straight into the transposed layout),
+   12 the tensor-core GEMMs of the dense box solve (KFBI_TF32X3).  Launch counts are always
    kept; times only while profiling is on (enabling clears both). */
 #define KFBI_NSTAGES 16
 typedef struct {

@@ -23,6 +23,7 @@ KFBI_FP64 = 0
 KFBI_MIXED_FP32 = 1
 KFBI_FP32_REFINED = 2
 KFBI_FP32_REFINED_ONCE = 3
+KFBI_TF32X3 = 4
 KFBI_STATIC_MAX_N = 1024                  # limits of kfbi_box_solve_static (kfbi.h)
 KFBI_STATIC_SCRATCH_BYTES = 9 << 20
 KFBI_DOUBLE_LAYER = 0

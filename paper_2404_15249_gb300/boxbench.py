@@ -23,7 +23,7 @@ import numpy as np
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--N", type=int, default=4096)
-    ap.add_argument("--precision", type=int, default=1, help="0 FP64, 1 FP32, 2/3 refined FP32")
+    ap.add_argument("--precision", type=int, default=1, help="0 FP64, 1 FP32, 2/3 refined FP32, 4 tensor-core TF32x3")
     ap.add_argument("--kappa", type=float, default=1.0)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -70,12 +70,15 @@ def main(argv=None):
     ms = statistics.median(times)
     # plain solves only: a refined solve runs several transforms plus residual passes
     nbytes = 3 * 2.0 * N * N * (8 if a.precision == 0 else 4) if a.precision in (0, 1) else None
+    # tensor-core solve: four N x N x N GEMMs, three TF32 products each
+    flops = 4 * 3 * 2.0 * N**3 if a.precision == 4 else None
     if a.apply:
-        nbytes = None
+        nbytes = flops = None
     print(json.dumps({"N": N, "precision": a.precision, "apply": a.apply, "ms_per_solve": ms,
                       "times_ms": times, "dst_variant": list(info["dst_variant"]),
                       "transform_bytes": nbytes,
-                      "transform_GBps": nbytes / ms / 1e6 if nbytes else None}))
+                      "transform_GBps": nbytes / ms / 1e6 if nbytes else None,
+                      "tensor_TFLOPs": flops / ms / 1e9 if flops else None}))
     ctx.close()
 
 

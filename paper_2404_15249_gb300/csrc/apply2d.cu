@@ -354,6 +354,10 @@ kfbi_status apply_potential(Ctx& c, Layer layer, int precision, const double* de
   }
   const int steps = refine_steps_of(precision);
   KFBI_TRY(correct<float>(c, d, s, nullptr, c.B32, 0, steps ? c.B64 : nullptr));
+  if (precision == KFBI_TF32X3) {                   // dense sine transforms on tensor cores
+    KFBI_TRY(box_solve_tc(c, c.B32, c.V32));
+    return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out);
+  }
   if (steps == 0 && c.irr_rowptr && c.dim == 2) {
     // sparse first x-transform, then the dense y-transform pair and the last x-transform
     float* X = reinterpret_cast<float*>(c.XT);
@@ -422,7 +426,8 @@ kfbi_status interface_solve(Ctx& c, int precision, const double* dens, const dou
   KFBI_CUDA_TRY(cudaGetLastError());
   KFBI_TRY(correct<float>(c, dens, nullptr, f_ctrl, W, 1));
   if (rhs_grid) KFBI_TRY(to_grid<float>(c, W, nullptr, nullptr, nullptr, rhs_grid));
-  KFBI_TRY(box_solve_f32(c, W, W));
+  if (precision == KFBI_TF32X3) KFBI_TRY(box_solve_tc(c, W, W));
+  else KFBI_TRY(box_solve_f32(c, W, W));
   if (v_grid) KFBI_TRY(to_grid<float>(c, W, nullptr, nullptr, nullptr, v_grid));
   if (out) KFBI_TRY(interp<float>(c, W, nullptr, nullptr, dens, nullptr, f_ctrl, out));
   return KFBI_OK;
@@ -459,7 +464,8 @@ kfbi_status box_solve_grid(Ctx& c, int precision, const double* b_grid, double* 
   prof_count(c, ST_GRID);
   grid_to_work_kernel<float><<<rows_grid(c.N, c.N), 256, 0, c.stream>>>(c.N, b_grid, c.V32);
   KFBI_CUDA_TRY(cudaGetLastError());
-  KFBI_TRY(box_solve_f32(c, c.V32, c.V32));
+  if (precision == KFBI_TF32X3) KFBI_TRY(box_solve_tc(c, c.V32, c.V32));
+  else KFBI_TRY(box_solve_f32(c, c.V32, c.V32));
   return to_grid<float>(c, c.V32, nullptr, nullptr, nullptr, v_grid);
 }
 

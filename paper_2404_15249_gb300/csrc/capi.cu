@@ -110,7 +110,8 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
     return KFBI_ERR_ARG;
   }
   if (M < 8 || M > (1 << 22) || !(opt->hi > opt->lo) || !(opt->kappa >= 0.0) ||
-      opt->gmres_m < 1 || opt->gmres_m > 128 || opt->max_restarts < 0 || !(opt->tol > 0.0)) {
+      opt->gmres_m < 1 || opt->gmres_m > 128 || opt->max_restarts < 0 || !(opt->tol > 0.0) ||
+      !kfbi::valid_precision(opt->precision)) {
     kfbi::set_error("kfbi_setup: bad size or option");
     return KFBI_ERR_ARG;
   }
@@ -128,6 +129,11 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
   c.stream = (cudaStream_t)stream;
   c.plan = plan;
   c.dim = dim;
+  if (opt->precision == KFBI_TF32X3 && !kfbi::tc_supported(c)) {
+    kfbi::set_error("kfbi_setup: KFBI_TF32X3 needs a 2-D grid with N a multiple of 128 up to 4096");
+    free_handle(hd);
+    return KFBI_ERR_UNSUPPORTED;
+  }
   kfbi_status s = KFBI_OK;
   const size_t grid = (size_t)c.N * c.N * (dim == 3 ? (size_t)c.N : 1);
 #define SETUP_TRY(expr)       \
@@ -191,6 +197,7 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
       SETUP_TRY(kfbi::autotune_f64(c));
     }
     SETUP_TRY(kfbi::setup_geometry(c));
+    SETUP_TRY(kfbi::init_tc_tables(c));
   } else {
     SETUP_TRY(kfbi::setup_geometry3(c));
   }
@@ -211,6 +218,13 @@ static Ctx* ctx_of(kfbi_ctx h, cudaStream_t st) {
   return &h->c;
 }
 
+// the tensor-core precision exists for 2-D grids with N a multiple of 128 up to 4096 only
+static bool tc_refused(const Ctx& c, int precision, const char* who) {
+  if (precision != KFBI_TF32X3 || kfbi::tc_supported(c)) return false;
+  kfbi::set_error("%s: KFBI_TF32X3 needs a 2-D grid with N a multiple of 128 up to 4096", who);
+  return true;
+}
+
 kfbi_status kfbi_apply_layer_potential(kfbi_ctx ctx, int layer, int precision,
                                        const double* d_density, double* d_out, void* stream) {
   Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
@@ -219,6 +233,7 @@ kfbi_status kfbi_apply_layer_potential(kfbi_ctx ctx, int layer, int precision,
     kfbi::set_error("kfbi_apply_layer_potential: bad argument");
     return KFBI_ERR_ARG;
   }
+  if (tc_refused(*c, precision, "kfbi_apply_layer_potential")) return KFBI_ERR_UNSUPPORTED;
   return kfbi::apply_potential(*c, layer == KFBI_DOUBLE_LAYER ? kfbi::Layer::Double
                                                               : kfbi::Layer::Single,
                                precision, d_density, d_out);
@@ -232,6 +247,7 @@ kfbi_status kfbi_apply_volume(kfbi_ctx ctx, int precision, const double* d_f_gri
     kfbi::set_error("kfbi_apply_volume: bad argument");
     return KFBI_ERR_ARG;
   }
+  if (tc_refused(*c, precision, "kfbi_apply_volume")) return KFBI_ERR_UNSUPPORTED;
   return kfbi::interface_solve(*c, precision, nullptr, d_f_grid, d_f_ctrl, nullptr, nullptr,
                                d_out);
 }
@@ -245,6 +261,7 @@ kfbi_status kfbi_interface_solve(kfbi_ctx ctx, int precision, const double* d_de
     kfbi::set_error("kfbi_interface_solve: bad argument");
     return KFBI_ERR_ARG;
   }
+  if (tc_refused(*c, precision, "kfbi_interface_solve")) return KFBI_ERR_UNSUPPORTED;
   return kfbi::interface_solve(*c, precision, d_density, d_f_grid, d_f_ctrl, d_rhs_grid, d_v_grid,
                                d_out);
 }
@@ -256,6 +273,7 @@ kfbi_status kfbi_box_solve(kfbi_ctx ctx, int precision, const double* d_b_grid, 
     kfbi::set_error("kfbi_box_solve: bad argument");
     return KFBI_ERR_ARG;
   }
+  if (tc_refused(*c, precision, "kfbi_box_solve")) return KFBI_ERR_UNSUPPORTED;
   return kfbi::box_solve_grid(*c, precision, d_b_grid, d_v_grid);
 }
 
@@ -303,6 +321,7 @@ kfbi_status kfbi_set_solver(kfbi_ctx ctx, int precision, int gmres_m, int max_re
     return KFBI_ERR_ARG;
   }
   Ctx& c = ctx->c;
+  if (tc_refused(c, precision, "kfbi_set_solver")) return KFBI_ERR_UNSUPPORTED;
   c.opt.precision = precision;
   c.opt.gmres_m = gmres_m;
   c.opt.max_restarts = max_restarts;
@@ -436,7 +455,7 @@ kfbi_status kfbi_profile_read(kfbi_ctx ctx, kfbi_stage_times* out) {
 const char* kfbi_stage_name(int s) {
   static const char* names[] = {"setup", "correction", "dst_rows_f32", "dst_cols_f32",
                                 "dst_rows_f64", "dst_cols_f64", "interpolation", "grid",
-                                "krylov", "refine", "transpose", "sparse_x_f32"};
+                                "krylov", "refine", "transpose", "sparse_x_f32", "dst_tc_tf32x3"};
   return (s >= 0 && s < kfbi::ST_COUNT) ? names[s] : "unused";
 }
 

@@ -261,7 +261,8 @@ kfbi_status alloc_gmres(Ctx& c, int m) {
 }
 
 static kfbi_status apply_K(Ctx& c, int precision, const double* x, double* y, Counters& cnt) {
-  if (precision == KFBI_MIXED_FP32) ++cnt.applies32; else ++cnt.applies64;   // FP64-accurate
+  if (precision == KFBI_MIXED_FP32 || precision == KFBI_TF32X3) ++cnt.applies32;
+  else ++cnt.applies64;   // FP64-accurate
   return apply_potential(c, Layer::Double, precision, x, y);
 }
 
@@ -423,11 +424,12 @@ kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const 
   const double tol_abs = c.opt.tol * gnorm;
   double res = 0.0;
   int cycles = 0;
-  if (c.opt.precision == KFBI_MIXED_FP32) {
+  if (c.opt.precision == KFBI_MIXED_FP32 || c.opt.precision == KFBI_TF32X3) {
     // twice-refined applies (about 1e-13) while the residual is above tol / 1e-9,
     // once-refined (about 1e-10 at the largest grids) down to tol / inner_tol, plain FP32
-    // below (inner_tol: the assumed relative accuracy of an FP32 apply)
-    const Relax relax{{KFBI_FP32_REFINED, KFBI_FP32_REFINED_ONCE, KFBI_MIXED_FP32},
+    // (FFT or tensor-core transforms) below (inner_tol: the assumed relative accuracy of
+    // an FP32 apply)
+    const Relax relax{{KFBI_FP32_REFINED, KFBI_FP32_REFINED_ONCE, c.opt.precision},
                       {tol_abs / 1e-9, tol_abs / c.opt.inner_tol}};
     KFBI_TRY(gmres_run(c, relax, acc, ghat, phi, true, tol_abs, c.opt.max_restarts + 1, cnt,
                        &res, &cycles));

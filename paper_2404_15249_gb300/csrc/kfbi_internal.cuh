@@ -62,7 +62,7 @@ struct BoxTables {
 enum Stage : int {
   ST_SETUP = 0, ST_CORR = 1, ST_ROWS32 = 2, ST_COLS32 = 3, ST_ROWS64 = 4, ST_COLS64 = 5,
   ST_INTERP = 6, ST_GRID = 7, ST_KRYLOV = 8, ST_REFINE = 9, ST_TRANS = 10, ST_SPARSE = 11,
-  ST_COUNT = 12   // ST_SPARSE: the sparse first x-transform of the plain FP32 2-D apply
+  ST_TC = 12, ST_COUNT = 13   // ST_SPARSE: sparse first x-transform; ST_TC: tensor-core GEMMs
 };
 
 struct Prof {
@@ -145,6 +145,8 @@ struct Ctx {
   float* H32 = nullptr;                             // dense right-hand side, FP32 high part
   float* D32 = nullptr;                             // dense right-hand side, FP32 low part
   void* XT = nullptr;                               // transposed work grid (N x N, FP64 size)
+  float* tc_shi = nullptr;                          // sine matrix, TF32 high part (N x N)
+  float* tc_slo = nullptr;                          // sine matrix, TF32 low part
   BoxTables<float> t32{};
   BoxTables<double> t64{};
   int rows_variant[2] = {0, 0};                     // row-pass variant per precision (autotuned)
@@ -208,8 +210,13 @@ kfbi_status combined_u(Ctx& c, int precision, const double* dens, const double* 
                        const double* f_ctrl, double* u_grid);
 inline bool valid_precision(int p) {
   return p == KFBI_FP64 || p == KFBI_MIXED_FP32 || p == KFBI_FP32_REFINED ||
-         p == KFBI_FP32_REFINED_ONCE;
+         p == KFBI_FP32_REFINED_ONCE || p == KFBI_TF32X3;
 }
+
+// dense tensor-core box solve (dst_tc.cu)
+bool tc_supported(const Ctx& c);
+kfbi_status init_tc_tables(Ctx& c);
+kfbi_status box_solve_tc(Ctx& c, const float* rhs, float* work);
 
 // 3-D (kfbi3d.cu, dst3d.cu): setup and the same stages on the N^3 work grid
 kfbi_status setup_geometry3(Ctx& c);

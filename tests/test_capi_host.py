@@ -51,6 +51,10 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     assert lib.kfbi_setup(ctypes.byref(o), 64, dummy, dummy, dummy, None, ctypes.byref(h)) == 1
     assert b"512" in lib.kfbi_last_error()
     assert not h.value
+    # unknown solver precision
+    o.dim, o.N, o.precision = 2, 128, 99
+    assert lib.kfbi_setup(ctypes.byref(o), 64, dummy, dummy, dummy, None, ctypes.byref(h)) == 1
+    assert not h.value
     assert lib.kfbi_apply_layer_potential(None, 0, 0, dummy, dummy, None) == 1
     assert lib.kfbi_destroy(None) == 1
     assert lib.kfbi_batch_create(None, 0, ctypes.byref(h)) == 1
