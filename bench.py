@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--n3d", type=int, default=256,
                     help="grid size of the 3-D companion measurement (0: skip)")
+    ap.add_argument("--ntc", type=int, default=1024,
+                    help="grid size of the tensor-core box-solve measurement (0: skip)")
     ap.add_argument("--batch", type=int, default=256,
                     help="problems in the batched companion measurement (0: skip)")
     return ap.parse_args()
@@ -373,6 +375,9 @@ def run_kfbi(a):
     batch = None
     if rank == 0 and a.batch > 0:
         batch = run_batch_companion(a, dev)
+    tc = None
+    if rank == 0 and a.ntc > 0:
+        tc = run_tc_companion(a, dev, flush)
 
     launches = int(sum(v[1] for v in stages.values()))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -398,7 +403,8 @@ def run_kfbi(a):
             "stage_launches": {k: int(v[1]) for k, v in stages.items() if v[1]},
             **fp64,
             "companion_3d": companion,
-            "companion_batch": batch}
+            "companion_batch": batch,
+            "companion_tc": tc}
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -462,6 +468,75 @@ def run_3d_companion(a, dev, flush):
             "applies_per_solve": applies, "iterations": info["iterations"],
             "err_inf_mixed": err_mixed, "fp64_solve_ms": ms64, "err_inf_fp64": err64,
             "fp64_iterations": info64["iterations"], "speedup_vs_fp64": ms64 / ms_mixed}
+
+
+NOMINAL_TF32_PER_BF16 = 1.1 / 2.25     # dense tensor rates, TF32 : BF16
+
+
+def run_tc_companion(a, dev, flush):
+    """The tensor-core box solve (dense sine-matrix form, four tcgen05 TF32 GEMMs with a
+    three-term split) against the FFT FP32 box solve on one flower context: median of 10
+    solves each (L2 flushed before each), and one mixed-precision BVP solve with the
+    tensor-core apply as its lowest tier.  Tensor roofline: 24 N^3 flops per solve (4 GEMMs
+    x 3 products x 2 N^3) against the TF32 peak taken as the measured BF16 burst peak times
+    the nominal TF32/BF16 ratio."""
+    import numpy as np
+    import torch
+    import kfbi_workloads as W
+    import paper_2404_15249_gb300 as K
+
+    N = a.ntc
+    prob = W.config_helmholtz(N, a.kappa, "flower")
+    ctx = K.Kfbi2D(prob.iface.pts, prob.iface.normals, prob.iface.curv, N, a.kappa,
+                   precision=K.KFBI_TF32X3, tol=1e-10)
+    rng = np.random.default_rng(W.SEED)
+    b = torch.as_tensor(rng.standard_normal((N + 1, N + 1)), device=dev)
+    v = torch.empty_like(b)
+    st = torch.cuda.current_stream()
+
+    def med(prec, n=10):
+        for _ in range(3):
+            ctx.box_solve(b, prec, out=v)
+        out = []
+        for _ in range(n):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ctx.box_solve(b, prec, out=v)
+            e1.record(st)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return statistics.median(out)
+
+    ms_tc, ms_fft = med(K.KFBI_TF32X3), med(K.KFBI_MIXED_FP32)
+    fg = torch.as_tensor(prob.f_grid(), device=dev)
+    fc = torch.as_tensor(prob.f_ctrl(), device=dev)
+    gc = torch.as_tensor(prob.g_ctrl(), device=dev)
+    u = torch.empty_like(b)
+    ctx.solve_bvp(fg, fc, gc, u_out=u)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    _, _, info = ctx.solve_bvp(fg, fc, gc, u_out=u)
+    e1.record(st)
+    e1.synchronize()
+    inside = ctx.inside_mask().cpu().numpy().astype(bool)
+    err = float(np.max(np.abs(u.cpu().numpy() - prob.u_grid())[inside]))
+    ctx.close()
+    flops = 24.0 * N ** 3
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    bf16 = float(json.load(open(pk))["bf16_tflops"]) if os.path.exists(pk) else 1900.0
+    peak = bf16 * NOMINAL_TF32_PER_BF16
+    return {"workload": f"box solve (Alg. 4, dense form) of a random right-hand side on the "
+                        f"flower context, N={N}, kappa={a.kappa}; mixed BVP solve with "
+                        f"tensor-core applies as the lowest tier",
+            "N": N, "tc_box_solve_ms": ms_tc, "fft_fp32_box_solve_ms": ms_fft,
+            "roofline": {"bound": "tensor", "kernel": "dst_gemm_kernel (tcgen05 kind::tf32)",
+                         "achieved": flops / (ms_tc / 1e3) / 1e12, "peak": peak,
+                         "unit": "TFLOP/s", "frac": flops / (ms_tc / 1e3) / 1e12 / peak,
+                         "peak_source": "measured BF16 burst x nominal TF32/BF16 ratio",
+                         "flops_per_solve": flops},
+            "mixed_tc_solve_ms": e0.elapsed_time(e1), "mixed_tc_iterations": info["iterations"],
+            "mixed_tc_applies_low": info["applies_low"], "mixed_tc_err_inf": err}
 
 
 def run_batch_companion(a, dev):

@@ -188,10 +188,19 @@ class Kfbi2D:
     def _new(self, n):
         return self.torch.empty(n, dtype=self.torch.float64, device=self.dev)
 
+    def _out(self, out, numel):
+        """A caller-supplied output buffer: contiguous float64 on this context's device."""
+        t = self.torch
+        if not (isinstance(out, t.Tensor) and out.dtype == t.float64 and out.is_contiguous()
+                and out.device == t.device(self.dev) and out.numel() == numel):
+            raise ValueError(f"out must be a contiguous float64 tensor of {numel} elements "
+                             f"on {self.dev}")
+        return out
+
     # ------------------------------------------------------------------ API
     def apply_layer_potential(self, density, layer=KFBI_DOUBLE_LAYER, precision=KFBI_FP64, out=None):
         d = self._vec(density)
-        out = self._new(self.M) if out is None else out
+        out = self._new(self.M) if out is None else self._out(out, self.M)
         _check(lib().kfbi_apply_layer_potential(self.handle, int(layer), int(precision), _ptr(d),
                                                 _ptr(out), _stream_ptr(self.stream)),
                "kfbi_apply_layer_potential")
@@ -214,9 +223,9 @@ class Kfbi2D:
                "kfbi_interface_solve")
         return rhs, v, out
 
-    def box_solve(self, b_grid, precision=KFBI_FP64):
+    def box_solve(self, b_grid, precision=KFBI_FP64, out=None):
         b = self._vec(b_grid)
-        v = self._grid()
+        v = self._grid() if out is None else self._out(out, (self.N + 1) ** self.dim)
         _check(lib().kfbi_box_solve(self.handle, int(precision), _ptr(b), _ptr(v),
                                     _stream_ptr(self.stream)), "kfbi_box_solve")
         return v

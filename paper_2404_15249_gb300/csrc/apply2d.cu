@@ -150,20 +150,26 @@ __global__ void split_kernel(long n, const double* __restrict__ b, float* __rest
 // The double-layer right-hand side is nonzero only at irregular nodes, so the plain FP32
 // apply evaluates the first sine transform (along x) directly on them (the same DST-I sums,
 // in another order), written straight into the transposed layout of the column pass:
-// X[k][j] = sum over irregular (i, j) of b_ij sin(pi i k / N), in the transposed layout
-// of the column pass.  A thread takes one row j and 32 consecutive modes k; along k the
-// sine follows by rotation from the table value at the first mode (32 steps).
-constexpr int SPARSE_KB = 32;
+// X[k][j] = sum over irregular (i, j) of b_ij sin(pi i k / N).  With theta = pi i k / N the
+// modes k, N - k, N/2 + k and N/2 - k share one (cos theta, sin theta):
+//   sin(pi i (N - k) / N)   = (-1)^(i+1) sin theta,
+//   sin(pi i (N/2 +- k) / N) = sin(pi i / 2 +- theta) = +-sin theta or cos theta by i mod 4,
+// so a thread takes one row j and SPARSE_KB consecutive modes k in [0, N/4] and fills four
+// output rows; along k the pair (cos, sin) follows by rotation from the table value at the
+// block's first mode (SPARSE_KB steps).
+constexpr int SPARSE_KB = 16;
 
-__global__ void sparse_rows_t_kernel(int N, const int* __restrict__ irr_node,
-                                     const int* __restrict__ rowptr, const float* __restrict__ B,
-                                     const float2* __restrict__ tw, float* __restrict__ X) {
+__global__ void __launch_bounds__(128)
+    sparse_rows_t_kernel(int N, const int* __restrict__ irr_node, const int* __restrict__ rowptr,
+                         const float* __restrict__ B, const float2* __restrict__ tw,
+                         float* __restrict__ X) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int k0 = blockIdx.y * SPARSE_KB;
+  const int Q = N / 4, H = N / 2;
   if (j >= N) return;
-  float acc[SPARSE_KB];
+  float a1[SPARSE_KB], a2[SPARSE_KB], a3[SPARSE_KB], a4[SPARSE_KB];
 #pragma unroll
-  for (int kk = 0; kk < SPARSE_KB; ++kk) acc[kk] = 0.f;
+  for (int kk = 0; kk < SPARSE_KB; ++kk) a1[kk] = a2[kk] = a3[kk] = a4[kk] = 0.f;
   if (j > 0) {
     for (int n = rowptr[j - 1]; n < rowptr[j]; ++n) {
       const int node = irr_node[n];
@@ -172,19 +178,35 @@ __global__ void sparse_rows_t_kernel(int N, const int* __restrict__ irr_node,
       const float2 t0 = tw[(int)(((long)i * k0) % (2 * N))], ti = tw[i];
       float cs = t0.x, sn = -t0.y;
       const float C = ti.x, S = -ti.y;
+      const bool odd = i & 1;
+      const float p2 = odd ? b : -b;                          // mode N - k
+      const float p3 = ((i & 3) == 0 || (i & 3) == 1) ? b : -b; // mode N/2 + k
+      const float p4 = odd ? p3 : -p3;                        // mode N/2 - k
 #pragma unroll
       for (int kk = 0; kk < SPARSE_KB; ++kk) {
-        acc[kk] = fmaf(b, sn, acc[kk]);
+        const float t = odd ? cs : sn;
+        a1[kk] = fmaf(b, sn, a1[kk]);
+        a2[kk] = fmaf(p2, sn, a2[kk]);
+        a3[kk] = fmaf(p3, t, a3[kk]);
+        a4[kk] = fmaf(p4, t, a4[kk]);
         const float cn = cs * C - sn * S;
         sn = fmaf(sn, C, cs * S);
         cs = cn;
       }
     }
   }
+  // every mode written exactly once: k in [0, N/4], N - k and N/2 - k for 0 < k < N/4,
+  // N/2 + k for 0 <= k <= N/4 (X[0] = 0)
 #pragma unroll
   for (int kk = 0; kk < SPARSE_KB; ++kk) {
     const int k = k0 + kk;
-    if (k < N) X[(size_t)k * N + j] = (k == 0) ? 0.f : acc[kk];
+    if (k > Q) break;
+    X[(size_t)k * N + j] = (k == 0) ? 0.f : a1[kk];
+    X[(size_t)(H + k) * N + j] = a3[kk];
+    if (k > 0 && k < Q) {
+      X[(size_t)(N - k) * N + j] = a2[kk];
+      X[(size_t)(H - k) * N + j] = a4[kk];
+    }
   }
 }
 
@@ -363,7 +385,7 @@ kfbi_status apply_potential(Ctx& c, Layer layer, int precision, const double* de
     float* X = reinterpret_cast<float*>(c.XT);
     const float2* tw = reinterpret_cast<const float2*>(c.t32.tw);
     int pr = prof_begin(c, ST_SPARSE);
-    sparse_rows_t_kernel<<<dim3((c.N + 127) / 128, (c.N + SPARSE_KB - 1) / SPARSE_KB), 128, 0,
+    sparse_rows_t_kernel<<<dim3((c.N + 127) / 128, (c.N / 4 + SPARSE_KB) / SPARSE_KB), 128, 0,
                            c.stream>>>(c.N, c.irr_node, c.irr_rowptr, c.B32, tw, X);
     prof_end(c, pr);
     KFBI_CUDA_TRY(cudaGetLastError());

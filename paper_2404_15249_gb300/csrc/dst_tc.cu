@@ -3,13 +3,21 @@
 // it is), the full diagonalisation is four GEMMs
 //     T1 = (B S)^T,  X2 = (T1 S) / (lambda_l + lambda_m - kappa^2) (2/N)^2,
 //     T3 = (X2 S)^T, V = T3 S,
-// each C = A S^T (S symmetric) with A and S K-major.  The GEMMs run on tcgen05: operands
-// in shared memory in the canonical K-major layout without swizzle (core matrices of
-// 8 rows x 16 bytes), the FP32 accumulator in tensor memory, MMAs issued by one thread and
-// tracked by an mbarrier per shared-memory stage (two stages: the next K chunk is staged
-// while the MMAs of the current one run).  TF32 with a three-term split
-// (A_hi S_hi + A_hi S_lo + A_lo S_hi, hi = TF32 rounding, lo = TF32 of the remainder) keeps
-// FP32-class accuracy.  Every wait is bounded; tensor memory is released on every path.
+// each C = A S^T (S symmetric) with A and S K-major.  TF32 with a three-term split
+// (A_hi S_hi + A_hi S_lo + A_lo S_hi, hi = TF32 rounding, lo = TF32 of the exact FP32
+// remainder) keeps FP32-class accuracy.  Every operand is kept in global memory as its
+// (hi, lo) pair: S once at setup, the right-hand side by one split pass, and each GEMM's
+// epilogue writes the pair of its output for the next GEMM, so the main loop only copies.
+//
+// GEMM kernel: one 128 x BN output tile per CTA, warp-specialised.  Two producer warps
+// copy K chunks of 16 with 16-byte cp.async into a ring of ST shared-memory stages laid
+// out in the canonical K-major no-swizzle form (core matrices of 8 rows x 16 bytes; copy q
+// of a tile lands at byte 16 q, so the stores of a warp are contiguous) and signal each
+// stage on its "full" mbarrier when their copies land; one thread of warp 4 waits on it,
+// issues the tcgen05.mma (kind::tf32) of the chunk with the FP32 accumulators in tensor
+// memory and commits them to the stage's "empty" mbarrier, which the producers wait on
+// before they refill the stage; warps 0-3 then read the accumulators for the epilogue.
+// Every mbarrier wait is bounded; tensor memory is released on every path.
 #include <atomic>
 
 #include "kfbi_internal.cuh"
@@ -17,19 +25,27 @@
 namespace kfbi {
 namespace {
 
-constexpr int BM = 128, BN = 64, KC = 32;          // CTA tile and K chunk
-constexpr int A_BYTES = BM * KC * 4, B_BYTES = BN * KC * 4;
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // A hi, A lo, S hi, S lo
-constexpr int SMEM_BYTES = 2 * STAGE_BYTES;               // two stages: 96 KB
-constexpr int TC_THREADS = 128;
+constexpr int BM = 128, KC = 16;
+constexpr int A_BYTES = BM * KC * 4;                // one part (hi or lo) of an A chunk
+
+template <int BN>
+struct Tile {
+  static constexpr int B_BYTES = BN * KC * 4;
+  static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;     // A hi, A lo, S hi, S lo
+  static constexpr int ST = (192 * 1024) / STAGE;              // stages in 192 KB
+  static constexpr int SMEM = ST * STAGE;
+  // partial accumulators in tensor memory (all 512 columns): chunk c adds into c % NACC.
+  // The tensor core's FP32 accumulation is not round-to-nearest; splitting the K sum
+  // into NACC partial sums, added in the epilogue, divides its systematic drift by NACC.
+  static constexpr int NACC = 512 / BN;
+  // instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, M = 128, N = BN
+  static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) |
+                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static_assert(ST >= 3, "pipeline depth");
+};
 
 __device__ __forceinline__ uint32_t sm_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// byte offset of element (r, k) of an R x KC chunk, k a multiple of 4 (16-byte group)
-__device__ __forceinline__ int canon(int r, int k) {
-  return (((r >> 3) * (KC / 4) + (k >> 2)) << 7) + ((r & 7) << 4);
 }
 
 // shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte offsets,
@@ -39,10 +55,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(LBO >> 4) << 16) |
          ((uint64_t)(SBO >> 4) << 32) | ((uint64_t)1 << 46);
 }
-
-// instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, M = 128, N = 64
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
 
 __device__ __forceinline__ float tf32(float x) {
   uint32_t r;
@@ -78,165 +90,241 @@ __global__ void sine_split_kernel(int N, float* shi, float* slo) {
   }
 }
 
-// C[r][c] = sum_k A[r][k] S[c][k] on the tile rows [m0, m0+128), columns [n0, n0+64).
+// FP32 values -> TF32 (hi, lo) pair
+__global__ void split_tf32_kernel(long n, const float* __restrict__ x, float* __restrict__ hi,
+                                  float* __restrict__ lo) {
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    const float v = x[q], h = tf32(v);
+    hi[q] = h;
+    lo[q] = tf32(v - h);
+  }
+}
+
+constexpr int PRODUCERS = 64;                  // warps 5 and 6
+constexpr int GEMM_THREADS = 128 + 32 + PRODUCERS;   // epilogue warps 0-3, MMA warp 4
+
+// copy rows [r0, r0 + R) x columns [kc, kc + KC) of a row-major N x N matrix into the
+// canonical layout at dst: copy q (row r0 + 8 (q / (2 KC)) + q % 8, column group
+// (q / 8) % (KC / 4)) lands at byte 16 q; producer thread pt takes q = pt, pt + 64, ...
+template <int R>
+__device__ __forceinline__ void copy_tile(uint32_t dst, const float* __restrict__ src, int N,
+                                          int r0, int kc, int pt) {
+#pragma unroll
+  for (int it = 0; it < R * (KC / 4) / PRODUCERS; ++it) {
+    const int q = it * PRODUCERS + pt;
+    const int r = r0 + (q / (2 * KC)) * 8 + (q & 7), g = (q >> 3) & (KC / 4 - 1);
+    const float* p = src + (size_t)r * N + kc + 4 * g;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * q), "l"(p)
+                 : "memory");
+  }
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_addr(bar)), "r"(count) : "memory");
+}
+
+// C[r][c] = sum_k A[r][k] S[c][k] on the tile rows [m0, m0+128), columns [n0, n0+BN), A
+// and S given as TF32 (hi, lo) pairs.
 // mode 0: out[r][c] = C;  mode 1: out[c][r] = C;  mode 2: out[r][c] = C * scale /
-// (lam[r] + lam[c] - kappa2), zero where r or c is 0.
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    dst_gemm_kernel(const float* __restrict__ A, const float* __restrict__ shi,
-                    const float* __restrict__ slo, float* __restrict__ out, int N, int mode,
+// (lam[r] + lam[c] - kappa2), zero where r or c is 0.  With out_lo non-null the output is
+// written as its TF32 pair (out, out_lo), else as FP32 values.
+template <int BN>
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    dst_gemm_kernel(const float* __restrict__ ahi, const float* __restrict__ alo,
+                    const float* __restrict__ shi, const float* __restrict__ slo,
+                    float* __restrict__ out, float* __restrict__ out_lo, int N, int mode,
                     const float* __restrict__ lam, float kappa2, float scale, int* err) {
+  using TL = Tile<BN>;
+  constexpr int ST = TL::ST;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t full[ST];
+  __shared__ __align__(8) uint64_t empty[ST];
+  __shared__ __align__(8) uint64_t done;
   __shared__ uint32_t tbase;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      sm_addr(&tbase)),
-                 "r"(BN)
+                 "r"(BN * TL::NACC)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(&bar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(&bar[1])) : "memory");
+    for (int s = 0; s < ST; ++s) {
+      bar_init(&full[s], PRODUCERS);
+      bar_init(&empty[s], 1);
+    }
+    bar_init(&done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tbase;
+  const uint32_t sbase = sm_addr(smem);
   const int nchunks = N / KC;
-  int uses[2] = {0, 0}, waits[2] = {0, 0};
   bool ok = true;
 
-  auto stage = [&](int s, int kc) {
-    unsigned char* base = smem + s * STAGE_BYTES;
-    unsigned char* ahi = base;
-    unsigned char* alo = base + A_BYTES;
-    unsigned char* bhi = base + 2 * A_BYTES;
-    unsigned char* blo = base + 2 * A_BYTES + B_BYTES;
-    // A: thread t takes row t, eight groups of 4 values (one 128-byte row segment)
-    const float* arow = A + (size_t)(m0 + tid) * N + kc;
-#pragma unroll
-    for (int g = 0; g < KC / 4; ++g) {
-      const float4 v = *reinterpret_cast<const float4*>(arow + 4 * g);
-      const float4 h = make_float4(tf32(v.x), tf32(v.y), tf32(v.z), tf32(v.w));
-      const float4 l = make_float4(tf32(v.x - h.x), tf32(v.y - h.y), tf32(v.z - h.z), tf32(v.w - h.w));
-      const int o = canon(tid, 4 * g);
-      *reinterpret_cast<float4*>(ahi + o) = h;
-      *reinterpret_cast<float4*>(alo + o) = l;
+  if (tid >= 160) {
+    // producers: chunk c into stage c % ST once the MMAs of chunk c - ST have read it
+    const int pt = tid - 160;
+#pragma unroll 1
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c % ST;
+      if (c >= ST) ok = bar_wait(&empty[s], (uint32_t)((c / ST - 1) & 1)) && ok;
+      const uint32_t st = sbase + (uint32_t)(s * TL::STAGE);
+      const int kc = c * KC;
+      copy_tile<BM>(st, ahi, N, m0, kc, pt);
+      copy_tile<BM>(st + A_BYTES, alo, N, m0, kc, pt);
+      copy_tile<BN>(st + 2 * A_BYTES, shi, N, n0, kc, pt);
+      copy_tile<BN>(st + 2 * A_BYTES + TL::B_BYTES, slo, N, n0, kc, pt);
+      // arrives on full[s] once this thread's copies so far have landed
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(sm_addr(&full[s]))
+                   : "memory");
     }
-    // S: threads 0..63 take rows n0 + t of the hi table, 64..127 those of the lo table
-    const int r = tid & (BN - 1);
-    const float* srow = (tid < BN ? shi : slo) + (size_t)(n0 + r) * N + kc;
-    unsigned char* dst = tid < BN ? bhi : blo;
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (tid == 128) {
+    // MMA issuer (warp 4, one thread)
+#pragma unroll 1
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c % ST;
+      ok = bar_wait(&full[s], (uint32_t)((c / ST) & 1)) && ok;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = sbase + (uint32_t)(s * TL::STAGE);
+      const uint32_t a_hi = st, a_lo = st + A_BYTES;
+      const uint32_t b_hi = st + 2 * A_BYTES, b_lo = b_hi + TL::B_BYTES;
+      const uint32_t d = tmem + (uint32_t)((c % TL::NACC) * BN);
 #pragma unroll
-    for (int g = 0; g < KC / 4; ++g)
-      *reinterpret_cast<float4*>(dst + canon(r, 4 * g)) = *reinterpret_cast<const float4*>(srow + 4 * g);
-  };
-
-  auto issue = [&](int s, bool first) {
-    unsigned char* base = smem + s * STAGE_BYTES;
-    const uint32_t ahi = sm_addr(base), alo = ahi + A_BYTES;
-    const uint32_t bhi = sm_addr(base + 2 * A_BYTES), blo = bhi + B_BYTES;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int term = 0; term < 3; ++term) {
+        const uint32_t a = term == 2 ? a_lo : a_hi;
+        const uint32_t b = term == 1 ? b_lo : b_hi;
 #pragma unroll
-    for (int term = 0; term < 3; ++term) {
-      const uint32_t a = term == 2 ? alo : ahi;
-      const uint32_t b = term == 1 ? blo : bhi;
-#pragma unroll
-      for (int ks = 0; ks < KC / 8; ++ks) {
-        const uint64_t ad = smem_desc(a + ks * 256), bd = smem_desc(b + ks * 256);
-        const uint32_t acc = (first && term == 0 && ks == 0) ? 0u : 1u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
-            : "memory");
+        for (int ks = 0; ks < KC / 8; ++ks) {
+          const uint64_t ad = smem_desc(a + ks * 256), bd = smem_desc(b + ks * 256);
+          const uint32_t acc = (c < TL::NACC && term == 0 && ks == 0) ? 0u : 1u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+              "l"(ad), "l"(bd), "r"(TL::IDESC), "r"(acc)
+              : "memory");
+        }
       }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       sm_addr(&empty[s]))
+                   : "memory");
     }
+    // completes once every MMA above has
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     sm_addr(&bar[s]))
+                     sm_addr(&done))
                  : "memory");
-  };
-
-  for (int c = 0; c < nchunks; ++c) {
-    const int s = c & 1;
-    if (uses[s] > waits[s]) {                 // the MMAs that read this stage are done
-      ok = bar_wait(&bar[s], (uint32_t)(waits[s] & 1)) && ok;
-      ++waits[s];
-    }
-    stage(s, c * KC);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) issue(s, c == 0);
-    ++uses[s];
   }
-  for (int s = 0; s < 2; ++s)
-    while (uses[s] > waits[s]) {
-      ok = bar_wait(&bar[s], (uint32_t)(waits[s] & 1)) && ok;
-      ++waits[s];
-    }
-  if (!ok && lane == 0) atomicOr(err, 2);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (tid < 128) {
+    ok = bar_wait(&done, 0u) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  if (!ok) atomicOr(err, 2);
 
-  // epilogue: warp w holds rows m0 + 32 w + lane, 16 columns per load
-  const int row = m0 + warp * 32 + lane;
-  const float lr = (mode == 2) ? lam[row] - kappa2 : 0.f;
-#pragma unroll
-  for (int c0 = 0; c0 < BN; c0 += 16) {
-    uint32_t v[16];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-        "[%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-          "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    if (mode == 1) {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) out[(size_t)(n0 + c0 + j) * N + row] = __uint_as_float(v[j]);
-    } else {
+  if (tid < 128) {
+    // epilogue: warp w holds rows m0 + 32 w + lane, 16 columns per load; the partial sums
+    // are added pairwise
+    const int row = m0 + warp * 32 + lane;
+    const float lr = (mode == 2) ? lam[row] - kappa2 : 0.f;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
       float x[16];
+      float part[TL::NACC][16];
+#pragma unroll
+      for (int a = 0; a < TL::NACC; ++a) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+            "[%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+              "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) part[a][j] = __uint_as_float(v[j]);
+      }
+#pragma unroll
+      for (int w = 1; w < TL::NACC; w *= 2)
+#pragma unroll
+        for (int a = 0; a + w < TL::NACC; a += 2 * w)
+#pragma unroll
+          for (int j = 0; j < 16; ++j) part[a][j] += part[a + w][j];
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        x[j] = __uint_as_float(v[j]);
+        x[j] = part[0][j];
         if (mode == 2) {
           const int col = n0 + c0 + j;
           x[j] = (row == 0 || col == 0) ? 0.f : x[j] * scale / (lr + lam[col]);
         }
       }
-      float4* o = reinterpret_cast<float4*>(out + (size_t)row * N + n0 + c0);
+      if (mode == 1) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) o[j] = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+        for (int j = 0; j < 16; ++j) {
+          const size_t o = (size_t)(n0 + c0 + j) * N + row;
+          if (out_lo) {
+            const float h = tf32(x[j]);
+            out[o] = h;
+            out_lo[o] = tf32(x[j] - h);
+          } else {
+            out[o] = x[j];
+          }
+        }
+      } else {
+        const size_t o = (size_t)row * N + n0 + c0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float4 w = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+          if (out_lo) {
+            const float4 h = make_float4(tf32(w.x), tf32(w.y), tf32(w.z), tf32(w.w));
+            *reinterpret_cast<float4*>(out_lo + o + 4 * j) =
+                make_float4(tf32(w.x - h.x), tf32(w.y - h.y), tf32(w.z - h.z), tf32(w.w - h.w));
+            w = h;
+          }
+          *reinterpret_cast<float4*>(out + o + 4 * j) = w;
+        }
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(BN * TL::NACC)
                  : "memory");
 }
 
-kfbi_status gemm(Ctx& c, const float* A, float* out, int mode) {
+template <int BN>
+kfbi_status gemm_n(Ctx& c, const float* ahi, const float* alo, float* out, float* out_lo,
+                   int mode) {
   static std::atomic<bool> attr{false};
   if (!attr) {
-    KFBI_CUDA_TRY(cudaFuncSetAttribute(dst_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       SMEM_BYTES));
+    KFBI_CUDA_TRY(cudaFuncSetAttribute(dst_gemm_kernel<BN>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<BN>::SMEM));
     attr = true;
   }
   const int N = c.N;
   const float scale = (float)((2.0 / N) * (2.0 / N));
   const int pr = prof_begin(c, ST_TC);
-  dst_gemm_kernel<<<dim3(N / BN, N / BM), TC_THREADS, SMEM_BYTES, c.stream>>>(
-      A, c.tc_shi, c.tc_slo, out, N, mode, c.t32.lam, (float)c.kappa2, scale, c.err_flag + 2);
+  dst_gemm_kernel<BN><<<dim3(N / BN, N / BM), GEMM_THREADS, Tile<BN>::SMEM, c.stream>>>(
+      ahi, alo, c.tc_shi, c.tc_slo, out, out_lo, N, mode, c.t32.lam, (float)c.kappa2, scale,
+      c.err_flag + 2);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
+}
+
+// 128 x 256 tiles where they fill the GPU (N >= 2048), 128 x 64 below
+kfbi_status gemm(Ctx& c, const float* ahi, const float* alo, float* out, float* out_lo, int mode) {
+  return c.N >= 2048 ? gemm_n<256>(c, ahi, alo, out, out_lo, mode)
+                     : gemm_n<64>(c, ahi, alo, out, out_lo, mode);
 }
 
 }  // namespace
@@ -254,16 +342,26 @@ kfbi_status init_tc_tables(Ctx& c) {
   return KFBI_OK;
 }
 
+// rhs and work: N x N FP32 work grids (may be the same buffer).  Scratch: the TF32 pairs
+// live in H32 / D32 and in the two halves of XT.
 kfbi_status box_solve_tc(Ctx& c, const float* rhs, float* work) {
   if (!tc_supported(c) || !c.tc_shi) {
     set_error("tensor-core box solve: 2-D grids with N a multiple of %d up to 4096 only", BM);
     return KFBI_ERR_UNSUPPORTED;
   }
-  float* X = reinterpret_cast<float*>(c.XT);
-  KFBI_TRY(gemm(c, rhs, X, 1));     // T1 = (B S)^T
-  KFBI_TRY(gemm(c, X, work, 2));    // X2 = T1 S / (lambda_l + lambda_m - kappa^2) (2/N)^2
-  KFBI_TRY(gemm(c, work, X, 1));    // T3 = (X2 S)^T
-  return gemm(c, X, work, 0);       // V = T3 S
+  const long n = (long)c.N * c.N;
+  float* phi = c.H32;
+  float* plo = c.D32;
+  float* qhi = reinterpret_cast<float*>(c.XT);
+  float* qlo = qhi + n;
+  prof_count(c, ST_TC);
+  split_tf32_kernel<<<(int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192), 256, 0, c.stream>>>(
+      n, rhs, phi, plo);
+  KFBI_CUDA_TRY(cudaGetLastError());
+  KFBI_TRY(gemm(c, phi, plo, qhi, qlo, 1));       // T1 = (B S)^T
+  KFBI_TRY(gemm(c, qhi, qlo, phi, plo, 2));       // X2 = T1 S / (lambda_l + lambda_m - kappa^2) (2/N)^2
+  KFBI_TRY(gemm(c, phi, plo, qhi, qlo, 1));       // T3 = (X2 S)^T
+  return gemm(c, qhi, qlo, work, nullptr, 0);     // V = T3 S
 }
 
 }  // namespace kfbi
