@@ -421,7 +421,13 @@ template <> struct RawVec<4> { typedef unsigned int type; };
 template <> struct RawVec<8> { typedef uint2 type; };
 template <> struct RawVec<16> { typedef uint4 type; };
 
-__device__ __forceinline__ float recip(float d) { return __frcp_rn(d); }
+// FP32: the hardware approximate reciprocal (relative error within 2^-22, a few ulp of the
+// FP32 transform's own rounding), one instruction instead of a correctly rounded sequence
+__device__ __forceinline__ float recip(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return r;
+}
 __device__ __forceinline__ double recip(double d) {
   // Newton-Raphson from the FP32 reciprocal: two steps reach FP64 accuracy
   double r = (double)__frcp_rn((float)d);
