@@ -157,7 +157,7 @@ __global__ void split_kernel(long n, const double* __restrict__ b, float* __rest
 // so a thread takes one row j and SPARSE_KB consecutive modes k in [0, N/4] and fills four
 // output rows; along k the pair (cos, sin) follows by rotation from the table value at the
 // block's first mode (SPARSE_KB steps).
-constexpr int SPARSE_KB = 16;
+constexpr int SPARSE_KB = 8;
 
 __global__ void __launch_bounds__(128)
     sparse_rows_t_kernel(int N, const int* __restrict__ irr_node, const int* __restrict__ rowptr,

@@ -429,8 +429,8 @@ __device__ __forceinline__ float recip(float d) {
   return r;
 }
 __device__ __forceinline__ double recip(double d) {
-  // Newton-Raphson from the FP32 reciprocal: two steps reach FP64 accuracy
-  double r = (double)__frcp_rn((float)d);
+  // Newton-Raphson from the approximate FP32 reciprocal: two steps reach FP64 accuracy
+  double r = (double)recip((float)d);
   r = r * (2.0 - d * r);
   r = r * (2.0 - d * r);
   return r;
