@@ -67,10 +67,12 @@ typedef enum {
   KFBI_FP32_REFINED_ONCE = 3, /* one refinement step (about 1e-11 relative at N = 1024,
                             3e-10 at N = 4096)                                           */
   KFBI_TF32X3 = 4        /* box solve in the dense form of Alg. 4 (full diagonalisation by
-                            the sine matrix) as four GEMMs on the tcgen05 tensor cores, TF32
-                            with a three-term split and FP32 accumulation (FP32-class
-                            accuracy, about 1e-6 relative); 2-D, N a multiple of 128 up to
-                            4096; an apply / box-solve / interface-solve precision        */
+                            the sine matrix) as GEMMs on the tcgen05 tensor cores (four in
+                            2-D, six in 3-D), TF32 with a three-term split and FP32
+                            accumulation (FP32-class accuracy); N a multiple of 128, up to
+                            8192 in 2-D and 512 in 3-D (else KFBI_ERR_UNSUPPORTED); an
+                            apply / box-solve / interface-solve precision, and as solver
+                            precision the mixed solver with tensor-core plain applies      */
 } kfbi_precision;
 
 typedef enum {

@@ -130,7 +130,7 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
   c.plan = plan;
   c.dim = dim;
   if (opt->precision == KFBI_TF32X3 && !kfbi::tc_supported(c)) {
-    kfbi::set_error("kfbi_setup: KFBI_TF32X3 needs a 2-D grid with N a multiple of 128 up to 4096");
+    kfbi::set_error("kfbi_setup: KFBI_TF32X3 needs N a multiple of 128, up to 8192 in 2-D and 512 in 3-D");
     free_handle(hd);
     return KFBI_ERR_UNSUPPORTED;
   }
@@ -200,6 +200,7 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
     SETUP_TRY(kfbi::init_tc_tables(c));
   } else {
     SETUP_TRY(kfbi::setup_geometry3(c));
+    SETUP_TRY(kfbi::init_tc_tables(c));
   }
   SETUP_TRY(kfbi::alloc_gmres(c, c.opt.gmres_m));
   if (cudaStreamSynchronize(c.stream) != cudaSuccess) {
@@ -218,10 +219,10 @@ static Ctx* ctx_of(kfbi_ctx h, cudaStream_t st) {
   return &h->c;
 }
 
-// the tensor-core precision exists for 2-D grids with N a multiple of 128 up to 4096 only
+// the tensor-core precision exists for N a multiple of 128, up to 8192 in 2-D and 512 in 3-D
 static bool tc_refused(const Ctx& c, int precision, const char* who) {
   if (precision != KFBI_TF32X3 || kfbi::tc_supported(c)) return false;
-  kfbi::set_error("%s: KFBI_TF32X3 needs a 2-D grid with N a multiple of 128 up to 4096", who);
+  kfbi::set_error("%s: KFBI_TF32X3 needs N a multiple of 128, up to 8192 in 2-D and 512 in 3-D", who);
   return true;
 }
 

@@ -1,9 +1,13 @@
 // Box solve of Alg. 4 in its dense form on the tensor cores: with the sine matrix
-// S[l][i] = sin(pi l i / N) (zero in row and column 0, so the N x N work grid is used as
-// it is), the full diagonalisation is four GEMMs
-//     T1 = (B S)^T,  X2 = (T1 S) / (lambda_l + lambda_m - kappa^2) (2/N)^2,
-//     T3 = (X2 S)^T, V = T3 S,
-// each C = A S^T (S symmetric) with A and S K-major.  TF32 with a three-term split
+// S[l][i] = sin(pi l i / N) (zero in row and column 0, so the work grid is used as it is),
+// the full diagonalisation is a chain of GEMMs C = A S^T (S symmetric, A and S K-major).
+// 2-D (B[j][i]):  T1 = (B S)^T,  X2 = (T1 S) / (lambda_l + lambda_m - kappa^2) (2/N)^2,
+//                 T3 = (X2 S)^T, V = T3 S.
+// 3-D (B[k][j][i] as an N^2 x N matrix): each GEMM transforms the fastest axis and writes
+// its result transposed (N x N^2), which moves the next axis to the front:
+//   (k,j,i) -> (l,k,j) -> (m,l,k) -> (n,m,l) with the division by
+//   lambda_l + lambda_m + lambda_n - kappa^2 and (2/N)^3 in the third epilogue, then the
+//   three inverse transforms back to (k,j,i).  TF32 with a three-term split
 // (A_hi S_hi + A_hi S_lo + A_lo S_hi, hi = TF32 rounding, lo = TF32 of the exact FP32
 // remainder) keeps FP32-class accuracy.  Every operand is kept in global memory as its
 // (hi, lo) pair: S once at setup, the right-hand side by one split pass, and each GEMM's
@@ -123,16 +127,18 @@ __device__ __forceinline__ void bar_init(uint64_t* bar, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_addr(bar)), "r"(count) : "memory");
 }
 
-// C[r][c] = sum_k A[r][k] S[c][k] on the tile rows [m0, m0+128), columns [n0, n0+BN), A
-// and S given as TF32 (hi, lo) pairs.
-// mode 0: out[r][c] = C;  mode 1: out[c][r] = C;  mode 2: out[r][c] = C * scale /
-// (lam[r] + lam[c] - kappa2), zero where r or c is 0.  With out_lo non-null the output is
-// written as its TF32 pair (out, out_lo), else as FP32 values.
+// C[r][c] = sum_k A[r][k] S[c][k] on the tile rows [m0, m0+128), columns [n0, n0+BN) of
+// an M x N result (A: M x N, S: N x N), A and S given as TF32 (hi, lo) pairs.
+// mode 0: out[r][c] = C (M = N);  mode 1: out[c][r] = C;  mode 2 (M = N): out[r][c] =
+// C * scale / (lam[r] + lam[c] - kappa2), zero where r or c is 0;  mode 3 (M = N^2):
+// out[c][r] = C * scale / (lam[r % N] + lam[r / N] + lam[c] - kappa2), zero where any of
+// the three indices is 0.  With out_lo non-null the output is written as its TF32 pair
+// (out, out_lo), else as FP32 values.
 template <int BN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     dst_gemm_kernel(const float* __restrict__ ahi, const float* __restrict__ alo,
                     const float* __restrict__ shi, const float* __restrict__ slo,
-                    float* __restrict__ out, float* __restrict__ out_lo, int N, int mode,
+                    float* __restrict__ out, float* __restrict__ out_lo, int M, int N, int mode,
                     const float* __restrict__ lam, float kappa2, float scale, int* err) {
   using TL = Tile<BN>;
   constexpr int ST = TL::ST;
@@ -230,7 +236,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     // epilogue: warp w holds rows m0 + 32 w + lane, 16 columns per load; the partial sums
     // are added pairwise
     const int row = m0 + warp * 32 + lane;
-    const float lr = (mode == 2) ? lam[row] - kappa2 : 0.f;
+    // row part of the divisor; zero_row: a boundary mode in the row index
+    float lr = 0.f;
+    bool zero_row = false;
+    if (mode == 2) {
+      lr = lam[row] - kappa2;
+      zero_row = row == 0;
+    } else if (mode == 3) {
+      const int ri = row % N, rj = row / N;
+      lr = lam[ri] + lam[rj] - kappa2;
+      zero_row = ri == 0 || rj == 0;
+    }
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
       float x[16];
@@ -260,15 +276,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         x[j] = part[0][j];
-        if (mode == 2) {
+        if (mode >= 2) {
           const int col = n0 + c0 + j;
-          x[j] = (row == 0 || col == 0) ? 0.f : x[j] * scale / (lr + lam[col]);
+          float r;
+          asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(lr + lam[col]));
+          x[j] = (zero_row || col == 0) ? 0.f : x[j] * scale * r;
         }
       }
-      if (mode == 1) {
+      if (mode == 1 || mode == 3) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const size_t o = (size_t)(n0 + c0 + j) * N + row;
+          const size_t o = (size_t)(n0 + c0 + j) * M + row;
           if (out_lo) {
             const float h = tf32(x[j]);
             out[o] = h;
@@ -304,32 +322,39 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 template <int BN>
 kfbi_status gemm_n(Ctx& c, const float* ahi, const float* alo, float* out, float* out_lo,
                    int mode) {
+  static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
   static std::atomic<bool> attr{false};
   if (!attr) {
     KFBI_CUDA_TRY(cudaFuncSetAttribute(dst_gemm_kernel<BN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<BN>::SMEM));
     attr = true;
   }
-  const int N = c.N;
-  const float scale = (float)((2.0 / N) * (2.0 / N));
+  const int N = c.N, M = c.dim == 3 ? N * N : N;
+  const double s1 = 2.0 / N;
+  const float scale = (float)(c.dim == 3 ? s1 * s1 * s1 : s1 * s1);
   const int pr = prof_begin(c, ST_TC);
-  dst_gemm_kernel<BN><<<dim3(N / BN, N / BM), GEMM_THREADS, Tile<BN>::SMEM, c.stream>>>(
-      ahi, alo, c.tc_shi, c.tc_slo, out, out_lo, N, mode, c.t32.lam, (float)c.kappa2, scale,
+  dst_gemm_kernel<BN><<<dim3(N / BN, M / BM), GEMM_THREADS, Tile<BN>::SMEM, c.stream>>>(
+      ahi, alo, c.tc_shi, c.tc_slo, out, out_lo, M, N, mode, c.t32.lam, (float)c.kappa2, scale,
       c.err_flag + 2);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
 }
 
-// 128 x 256 tiles where they fill the GPU (N >= 2048), 128 x 64 below
+// 128 x 256 tiles where they fill the GPU (2-D N >= 2048, 3-D N^2 rows), else 128 x 64
 kfbi_status gemm(Ctx& c, const float* ahi, const float* alo, float* out, float* out_lo, int mode) {
-  return c.N >= 2048 ? gemm_n<256>(c, ahi, alo, out, out_lo, mode)
-                     : gemm_n<64>(c, ahi, alo, out, out_lo, mode);
+  const bool wide = c.N >= 2048 || c.dim == 3;
+  if (wide && c.N % 256 == 0) return gemm_n<256>(c, ahi, alo, out, out_lo, mode);
+  if (wide) return gemm_n<128>(c, ahi, alo, out, out_lo, mode);
+  return gemm_n<64>(c, ahi, alo, out, out_lo, mode);
 }
 
 }  // namespace
 
-bool tc_supported(const Ctx& c) { return c.dim == 2 && c.N % BM == 0 && c.N <= 4096; }
+// 2-D: N a multiple of 128 up to 8192; 3-D: N a multiple of 128 up to 512
+bool tc_supported(const Ctx& c) {
+  return c.N % BM == 0 && ((c.dim == 2 && c.N <= 8192) || (c.dim == 3 && c.N <= 512));
+}
 
 kfbi_status init_tc_tables(Ctx& c) {
   if (!tc_supported(c)) return KFBI_OK;
@@ -342,14 +367,14 @@ kfbi_status init_tc_tables(Ctx& c) {
   return KFBI_OK;
 }
 
-// rhs and work: N x N FP32 work grids (may be the same buffer).  Scratch: the TF32 pairs
-// live in H32 / D32 and in the two halves of XT.
+// rhs and work: FP32 work grids (N^2 or N^3, may be the same buffer).  Scratch: the TF32
+// pairs live in H32 / D32 and in the two halves of XT.
 kfbi_status box_solve_tc(Ctx& c, const float* rhs, float* work) {
   if (!tc_supported(c) || !c.tc_shi) {
-    set_error("tensor-core box solve: 2-D grids with N a multiple of %d up to 4096 only", BM);
+    set_error("tensor-core box solve: N a multiple of %d, up to 8192 in 2-D and 512 in 3-D", BM);
     return KFBI_ERR_UNSUPPORTED;
   }
-  const long n = (long)c.N * c.N;
+  const long n = (long)c.N * c.N * (c.dim == 3 ? c.N : 1);
   float* phi = c.H32;
   float* plo = c.D32;
   float* qhi = reinterpret_cast<float*>(c.XT);
@@ -358,10 +383,18 @@ kfbi_status box_solve_tc(Ctx& c, const float* rhs, float* work) {
   split_tf32_kernel<<<(int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192), 256, 0, c.stream>>>(
       n, rhs, phi, plo);
   KFBI_CUDA_TRY(cudaGetLastError());
-  KFBI_TRY(gemm(c, phi, plo, qhi, qlo, 1));       // T1 = (B S)^T
-  KFBI_TRY(gemm(c, qhi, qlo, phi, plo, 2));       // X2 = T1 S / (lambda_l + lambda_m - kappa^2) (2/N)^2
-  KFBI_TRY(gemm(c, phi, plo, qhi, qlo, 1));       // T3 = (X2 S)^T
-  return gemm(c, qhi, qlo, work, nullptr, 0);     // V = T3 S
+  if (c.dim == 2) {
+    KFBI_TRY(gemm(c, phi, plo, qhi, qlo, 1));     // T1 = (B S)^T
+    KFBI_TRY(gemm(c, qhi, qlo, phi, plo, 2));     // X2 = T1 S / (lambda_l + lambda_m - kappa^2) (2/N)^2
+    KFBI_TRY(gemm(c, phi, plo, qhi, qlo, 1));     // T3 = (X2 S)^T
+    return gemm(c, qhi, qlo, work, nullptr, 0);   // V = T3 S
+  }
+  KFBI_TRY(gemm(c, phi, plo, qhi, qlo, 1));       // (k,j,i) -> (l,k,j)
+  KFBI_TRY(gemm(c, qhi, qlo, phi, plo, 1));       // -> (m,l,k)
+  KFBI_TRY(gemm(c, phi, plo, qhi, qlo, 3));       // -> (n,m,l), divided
+  KFBI_TRY(gemm(c, qhi, qlo, phi, plo, 1));       // inverse: -> (i,n,m)
+  KFBI_TRY(gemm(c, phi, plo, qhi, qlo, 1));       // -> (j,i,n)
+  return gemm(c, qhi, qlo, work, nullptr, 1);     // -> (k,j,i)
 }
 
 }  // namespace kfbi

@@ -825,6 +825,11 @@ static kfbi_status refined_solve3(Ctx& c, const float* b32, const float* bhi, co
 // FP64 transforms for FP64, FP32 transforms (refined or not) otherwise
 static bool use_fp32(int precision) { return precision != KFBI_FP64; }
 
+// plain FP32 box solve: FFT form, or the dense form on the tensor cores for KFBI_TF32X3
+static kfbi_status plain_solve3(Ctx& c, int precision, const float* b, float* v) {
+  return precision == KFBI_TF32X3 ? box_solve_tc(c, b, v) : box_solve3_f32(c, b, v);
+}
+
 kfbi_status apply_potential3(Ctx& c, Layer layer, int precision, const double* dens, double* out) {
   if (layer != Layer::Double) {
     set_error("single-layer potential: 2-D only");
@@ -835,7 +840,7 @@ kfbi_status apply_potential3(Ctx& c, Layer layer, int precision, const double* d
   if (use_fp32(precision)) {
     KFBI_TRY(correct3<float>(c, c.B32, 0, steps ? c.B64 : nullptr));
     if (steps == 0) {
-      KFBI_TRY(box_solve3_f32(c, c.B32, c.V32));
+      KFBI_TRY(plain_solve3(c, precision, c.B32, c.V32));
       return interp3<float>(c, c.V32, dens, out);
     }
     KFBI_TRY(refined_solve3(c, c.B32, nullptr, nullptr, steps));
@@ -870,7 +875,7 @@ kfbi_status interface_solve3(Ctx& c, int precision, const double* dens, const do
     prof_count(c, ST_GRID);
     convert_kernel3<<<grid_blocks(nw), 256, 0, c.stream>>>(nw, B, c.V32);
     KFBI_CUDA_TRY(cudaGetLastError());
-    KFBI_TRY(box_solve3_f32(c, c.V32, c.V32));
+    KFBI_TRY(plain_solve3(c, precision, c.V32, c.V32));
     if (v_grid) {
       prof_count(c, ST_GRID);
       work_to_grid3_kernel<float><<<grid_blocks(ng), 256, 0, c.stream>>>(N, c.V32, nullptr, v_grid);
@@ -932,7 +937,7 @@ kfbi_status box_solve_grid3(Ctx& c, int precision, const double* b_grid, double*
   if (precision != KFBI_FP64) {
     grid_to_work3_kernel<float><<<grid_blocks(nw), 256, 0, c.stream>>>(N, b_grid, c.V32);
     KFBI_CUDA_TRY(cudaGetLastError());
-    KFBI_TRY(box_solve3_f32(c, c.V32, c.V32));
+    KFBI_TRY(plain_solve3(c, precision, c.V32, c.V32));
     work_to_grid3_kernel<float><<<grid_blocks(ng), 256, 0, c.stream>>>(N, c.V32, nullptr, v_grid);
   } else {
     grid_to_work3_kernel<double><<<grid_blocks(nw), 256, 0, c.stream>>>(N, b_grid, c.V64);

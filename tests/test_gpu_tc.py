@@ -122,3 +122,73 @@ def test_tc_unsupported_sizes_are_refused():
     with pytest.raises(K.KfbiError) as e:
         make(prob, precision=K.KFBI_TF32X3)
     assert e.value.status == 8
+
+
+# ------------------------------------------------------------------ 3-D (six GEMMs)
+def make3(prob, **kw):
+    import kfbi_workloads.surfaces3d as S3  # noqa: F401
+    from oracle import kfbi3d as O3
+    I = prob.iface
+    ctx = K.Kfbi3D(I.pts, I.normals, I.shape, I.N, prob.kappa, **kw)
+    geom = O3.Geometry3D(I.pts, I.normals, I.shape, I.N, prob.kappa)
+    return ctx, geom
+
+
+@pytest.mark.parametrize("kappa", [0.0, 2.0])
+def test_tc_box_solve_parity_3d(kappa):
+    """N = 128: the N^2 x N GEMMs span 128 row tiles; every unknown against the oracle."""
+    import kfbi_workloads.surfaces3d as S3
+    from oracle import kfbi3d as O3
+    N = 128
+    prob = S3.Problem3D(S3.intersect(S3.sphere(), N), kappa, S3.manufactured_sin3(kappa))
+    ctx, geom = make3(prob)
+    rng = np.random.default_rng(5)
+    b = np.zeros((N + 1,) * 3)
+    b[1:N, 1:N, 1:N] = rng.standard_normal((N - 1,) * 3)
+    ref = O3.box_solve_dst(b, N, geom.h, kappa * kappa)
+    v = ctx.box_solve(b, K.KFBI_TF32X3).cpu().numpy()
+    assert rel(v, ref) < 2e-5
+    assert np.all(v[0] == 0) and np.all(v[-1] == 0) and np.all(v[:, :, 0] == 0)
+    ctx.close()
+
+
+def test_tc_apply_parity_and_mixed_solve_3d():
+    import kfbi_workloads.surfaces3d as S3
+    from oracle import kfbi3d as O3
+    prob = S3.Problem3D(S3.intersect(S3.ellipsoid(), 128), 1.0, S3.manufactured_sin3(1.0))
+    ctx, geom = make3(prob, tol=1e-10)
+    phi = S3.random_density3(geom.P, prob.iface.pts, seed=8)
+    ref = O3.apply_double_layer(geom, phi)
+    assert rel(ctx.apply_layer_potential(phi, 0, K.KFBI_TF32X3).cpu().numpy(), ref) < 1e-4
+    u64, phi64, _ = ctx.solve_bvp(prob.f_grid(), prob.f_ctrl(), prob.g_ctrl())
+    ctx.set_solver(K.KFBI_TF32X3, 50, 20, 1e-10, 1e-5)
+    u, phi_tc, info = ctx.solve_bvp(prob.f_grid(), prob.f_ctrl(), prob.g_ctrl())
+    assert info["converged"] and info["applies_low"] > 0, info
+    assert rel(phi_tc.cpu().numpy(), phi64.cpu().numpy()) < 1e-6
+    exact = prob.u_grid()
+    e64 = np.abs(u64.cpu().numpy() - exact)[geom.inside].max()
+    assert np.abs(u.cpu().numpy() - exact)[geom.inside].max() < 1.1 * e64
+    ctx.close()
+
+
+def test_tc_largest_2d_grid_box_solve_manufactured():
+    """N = 8192 (S tables of 2 x 268 MB): a discrete solution v, b = (Lap_h - kappa^2) v in
+    FP64, the tensor-core solve must give v back.  A random v is the hardest case: b is
+    dominated by the highest modes (|lambda| ~ 8/h^2) and every error in the sums of the low
+    modes is amplified by up to lambda_max / lambda_min ~ N^2.  The dense sums run over
+    K = 8192 terms with the tensor core's FP32 accumulation (two partial accumulators per
+    tile at this width), against log2 N rounding stages of the FFT: measured 2.8e-3 here
+    against < 1e-3 for the FFT FP32 path."""
+    N, kappa = 8192, 2.0
+    iface = W.circle(2 * N, 0.45)
+    ctx = K.Kfbi2D(iface.pts, iface.normals, iface.curv, N, kappa)
+    h = 2.0 / N
+    g = torch.Generator(device="cuda").manual_seed(N)
+    v = torch.zeros((N + 1, N + 1), dtype=torch.float64, device="cuda")
+    v[1:N, 1:N] = torch.rand((N - 1, N - 1), generator=g, device="cuda", dtype=torch.float64) - 0.5
+    b = torch.zeros_like(v)
+    b[1:N, 1:N] = ((v[2:, 1:N] + v[:-2, 1:N] + v[1:N, 2:] + v[1:N, :-2] - 4.0 * v[1:N, 1:N]) / (h * h)
+                   - kappa * kappa * v[1:N, 1:N])
+    out = ctx.box_solve(b, K.KFBI_TF32X3)
+    assert float((out - v).abs().max()) / float(v.abs().max()) < 5e-3
+    ctx.close()
