@@ -12,6 +12,7 @@
 #include <string>
 #include <thread>
 #include <vector>
+#include <cstdlib>
 
 #include "kfbi_internal.cuh"
 
@@ -482,7 +483,13 @@ kfbi_status batch_solve(kfbi_ctx* ctxs, int count, int nrhs, const double* const
     return (c.dim == 3 ? n * n * n : n * n) * std::log2((double)c.N);
   };
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
-  const int workers = std::max(1, std::min(count, kBatchWorkers));
+  // KFBI_BATCH_WORKERS (1..64) overrides the number of concurrent problems
+  int nw = kBatchWorkers;
+  if (const char* e = std::getenv("KFBI_BATCH_WORKERS")) {
+    const int v = std::atoi(e);
+    if (v >= 1 && v <= 64) nw = v;
+  }
+  const int workers = std::max(1, std::min(count, nw));
   cudaEvent_t start;
   KFBI_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
   KFBI_CUDA_TRY(cudaEventRecord(start, stream));
