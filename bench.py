@@ -35,6 +35,7 @@ METRIC = "KFBI full-solve ms & grid-pts/s per potential apply: mixed vs FP64, sa
 UNIT = "grid-pts/s"
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_FP64_GFLOPS = 1250.0
+NOMINAL_TF32_PER_BF16 = 1.1 / 2.25     # dense tensor rates, TF32 : BF16
 
 
 def parse():
@@ -459,6 +460,37 @@ def run_3d_companion(a, dev, flush):
     ctx.set_solver(K.KFBI_FP64, 50, 20, 1e-10, 1e-5)
     ctx.solve_bvp(fg, fc, gc, u_out=u, dens_out=phi)
     ms64, info64, err64 = timed(2)
+    # box solve alone: FFT FP32 form against the tensor-core dense form (36 N^4 flops)
+    tc = None
+    if N % 128 == 0:
+        b = torch.randn((N + 1,) * 3, dtype=torch.float64, device=dev)
+        vb = torch.empty_like(b)
+
+        def box_ms(prec, n=5):
+            for _ in range(2):
+                ctx.box_solve(b, prec, out=vb)
+            out = []
+            for _ in range(n):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                ctx.box_solve(b, prec, out=vb)
+                e1.record(st)
+                e1.synchronize()
+                out.append(e0.elapsed_time(e1))
+            return statistics.median(out)
+
+        ms_fft, ms_tc = box_ms(K.KFBI_MIXED_FP32), box_ms(K.KFBI_TF32X3)
+        flops = 36.0 * N ** 4
+        pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        bf16 = float(json.load(open(pk))["bf16_tflops"]) if os.path.exists(pk) else 1900.0
+        peak = bf16 * NOMINAL_TF32_PER_BF16
+        tc = {"fft_fp32_box_solve_ms": ms_fft, "tc_box_solve_ms": ms_tc,
+              "note": "box solves of a random right-hand side, including the conversions "
+                      "between the user grid and the work grid",
+              "tensor_tflops": flops / (ms_tc / 1e3) / 1e12,
+              "tensor_frac": flops / (ms_tc / 1e3) / 1e12 / peak,
+              "peak_source": "measured BF16 burst x nominal TF32/BF16 ratio"}
     ctx.close()
     return {"workload": f"3-D Dirichlet Poisson, ellipsoid (0.7, 0.5, 0.4), N={N} "
                         f"({N + 1}^3 nodes), {I.P} grid-line intersection points, "
@@ -467,10 +499,8 @@ def run_3d_companion(a, dev, flush):
             "mixed_solve_ms": ms_mixed, "grid_pts_per_s_per_apply": (N + 1) ** 3 * applies / (ms_mixed / 1e3),
             "applies_per_solve": applies, "iterations": info["iterations"],
             "err_inf_mixed": err_mixed, "fp64_solve_ms": ms64, "err_inf_fp64": err64,
-            "fp64_iterations": info64["iterations"], "speedup_vs_fp64": ms64 / ms_mixed}
-
-
-NOMINAL_TF32_PER_BF16 = 1.1 / 2.25     # dense tensor rates, TF32 : BF16
+            "fp64_iterations": info64["iterations"], "speedup_vs_fp64": ms64 / ms_mixed,
+            "box_solve_fft_vs_tc": tc}
 
 
 def run_tc_companion(a, dev, flush):

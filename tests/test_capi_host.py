@@ -68,3 +68,16 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(root, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_binding_constants_match_the_header():
+    """Every enum value the binding defines is the one include/kfbi.h declares."""
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "include", "kfbi.h")).read()
+    declared = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(KFBI_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    bound = {k: v for k, v in vars(K).items() if k.startswith("KFBI_") and isinstance(v, int)
+             and k in declared}
+    assert {"KFBI_FP64", "KFBI_MIXED_FP32", "KFBI_TF32X3", "KFBI_DOUBLE_LAYER"} <= set(bound)
+    for k, v in bound.items():
+        assert declared[k] == v, k
