@@ -1,5 +1,6 @@
 """GPU parity of the 3-D path (through the C ABI) against the 3-D FP64 CPU oracle on the
-same seeded inputs (grid-line intersections of an ellipsoid and a sphere).
+same seeded inputs (grid-line intersections of an ellipsoid, a sphere and the star surface
+rho = 0.5 + 0.1 sin 3 theta cos 4 phi).
 
 Tolerances as in 2-D: FP64 GPU path within 1e-11 relative of the oracle; FP32 box
 solves within 2e-5 relative for one transform and 1e-4 for an apply; node labels and
@@ -27,6 +28,7 @@ CASES = {
     "ellipsoid32_k0": lambda: S3.Problem3D(S3.intersect(S3.ellipsoid(), 32), 0.0, S3.manufactured_sin3(0.0)),
     "sphere48_k2": lambda: S3.Problem3D(S3.intersect(S3.sphere(), 48), 2.0, S3.manufactured_sin3(2.0)),
     "ellipsoid64_k1": lambda: S3.Problem3D(S3.intersect(S3.ellipsoid(), 64), 1.0, S3.manufactured_sin3(1.0)),
+    "star64_k0": lambda: S3.Problem3D(S3.intersect(S3.star(), 64), 0.0, S3.manufactured_sin3(0.0)),
 }
 
 
@@ -148,7 +150,7 @@ def test_solve_bvp_fp64_matches_oracle(case):
     ctx.close()
 
 
-@pytest.mark.parametrize("case", ["ellipsoid64_k1"])
+@pytest.mark.parametrize("case", ["ellipsoid64_k1", "star64_k0"])
 def test_solve_bvp_mixed_precision(case):
     prob = CASES[case]()
     ctx64, geom = make(prob, tol=1e-10)
