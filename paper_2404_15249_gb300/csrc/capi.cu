@@ -52,6 +52,7 @@ static void free_handle(kfbi_ctx_s* hd) {
     cudaFree(c.hcol); cudaFree(c.yvec); cudaFree(c.gm_part); cudaFree(c.gm_counter);
   }
   if (c.h_pinned) cudaFreeHost(c.h_pinned);
+  kfbi::free_tc(c);
   for (int i = 0; i < 2; ++i)
     if (c.gm_ev[i]) cudaEventDestroy(c.gm_ev[i]);
   delete hd;

@@ -13,16 +13,20 @@
 // (hi, lo) pair: S once at setup, the right-hand side by one split pass, and each GEMM's
 // epilogue writes the pair of its output for the next GEMM, so the main loop only copies.
 //
-// GEMM kernel: one 128 x BN output tile per CTA, warp-specialised.  Two producer warps
-// copy K chunks of 16 with 16-byte cp.async into a ring of ST shared-memory stages laid
-// out in the canonical K-major no-swizzle form (core matrices of 8 rows x 16 bytes; copy q
-// of a tile lands at byte 16 q, so the stores of a warp are contiguous) and signal each
-// stage on its "full" mbarrier when their copies land; one thread of warp 4 waits on it,
+// GEMM kernel: one 128 x BN output tile per CTA, warp-specialised.  The producer fills a
+// ring of ST shared-memory stages with K chunks of 16 and signals each stage on its "full"
+// mbarrier: either one thread issuing four TMA tensor loads per chunk (64-byte swizzled
+// K-major tiles, completion counted in bytes on the mbarrier), or two producer warps with
+// 16-byte cp.async into the canonical K-major no-swizzle form (core matrices of 8 rows x
+// 16 bytes; copy q of a tile lands at byte 16 q).  One thread of warp 4 waits on it,
 // issues the tcgen05.mma (kind::tf32) of the chunk with the FP32 accumulators in tensor
 // memory and commits them to the stage's "empty" mbarrier, which the producers wait on
 // before they refill the stage; warps 0-3 then read the accumulators for the epilogue.
 // Every mbarrier wait is bounded; tensor memory is released on every path.
+#include <cuda.h>
+
 #include <atomic>
+#include <cstdlib>
 
 #include "kfbi_internal.cuh"
 
@@ -123,6 +127,23 @@ __device__ __forceinline__ void copy_tile(uint32_t dst, const float* __restrict_
   }
 }
 
+// shared-memory descriptor of a K-major tile written by TMA with the 64-byte swizzle: rows
+// of 64 bytes (KC = 16 values), 8-row atoms of 512 bytes, descriptor version 1
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+// TMA: rows [y, y + box) x columns [x, x + KC) of the tensor map's matrix into dst
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(sm_addr(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void bar_init(uint64_t* bar, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_addr(bar)), "r"(count) : "memory");
 }
@@ -134,10 +155,14 @@ __device__ __forceinline__ void bar_init(uint64_t* bar, int count) {
 // out[c][r] = C * scale / (lam[r % N] + lam[r / N] + lam[c] - kappa2), zero where any of
 // the three indices is 0.  With out_lo non-null the output is written as its TF32 pair
 // (out, out_lo), else as FP32 values.
-template <int BN>
+template <int BN, bool TMA>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     dst_gemm_kernel(const float* __restrict__ ahi, const float* __restrict__ alo,
                     const float* __restrict__ shi, const float* __restrict__ slo,
+                    const __grid_constant__ CUtensorMap map_ahi,
+                    const __grid_constant__ CUtensorMap map_alo,
+                    const __grid_constant__ CUtensorMap map_shi,
+                    const __grid_constant__ CUtensorMap map_slo,
                     float* __restrict__ out, float* __restrict__ out_lo, int M, int N, int mode,
                     const float* __restrict__ lam, float kappa2, float scale, int* err) {
   using TL = Tile<BN>;
@@ -158,7 +183,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   }
   if (tid == 0) {
     for (int s = 0; s < ST; ++s) {
-      bar_init(&full[s], PRODUCERS);
+      bar_init(&full[s], TMA ? 1 : PRODUCERS);
       bar_init(&empty[s], 1);
     }
     bar_init(&done, 1);
@@ -171,8 +196,26 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   const uint32_t sbase = sm_addr(smem);
   const int nchunks = N / KC;
   bool ok = true;
+  // the swizzled TMA tiles need stage bases on 512-byte boundaries
+  const bool aligned = !TMA || (sbase & 511u) == 0;
 
-  if (tid >= 160) {
+  if (TMA && tid == 160) {
+    if (!aligned) atomicOr(err, 4);
+#pragma unroll 1
+    for (int c = 0; aligned && c < nchunks; ++c) {
+      const int s = c % ST;
+      if (c >= ST) ok = bar_wait(&empty[s], (uint32_t)((c / ST - 1) & 1)) && ok;
+      const uint32_t st = sbase + (uint32_t)(s * TL::STAGE);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_addr(&full[s])),
+                   "r"((uint32_t)TL::STAGE)
+                   : "memory");
+      const int kc = c * KC;
+      tma_load(st, &map_ahi, kc, m0, &full[s]);
+      tma_load(st + A_BYTES, &map_alo, kc, m0, &full[s]);
+      tma_load(st + 2 * A_BYTES, &map_shi, kc, n0, &full[s]);
+      tma_load(st + 2 * A_BYTES + TL::B_BYTES, &map_slo, kc, n0, &full[s]);
+    }
+  } else if (!TMA && tid >= 160) {
     // producers: chunk c into stage c % ST once the MMAs of chunk c - ST have read it
     const int pt = tid - 160;
 #pragma unroll 1
@@ -193,7 +236,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   } else if (tid == 128) {
     // MMA issuer (warp 4, one thread)
 #pragma unroll 1
-    for (int c = 0; c < nchunks; ++c) {
+    for (int c = 0; aligned && c < nchunks; ++c) {
       const int s = c % ST;
       ok = bar_wait(&full[s], (uint32_t)((c / ST) & 1)) && ok;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -208,7 +251,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         const uint32_t b = term == 1 ? b_lo : b_hi;
 #pragma unroll
         for (int ks = 0; ks < KC / 8; ++ks) {
-          const uint64_t ad = smem_desc(a + ks * 256), bd = smem_desc(b + ks * 256);
+          // K step of 8 values: 32 bytes along a swizzled row, or two core matrices
+          const uint64_t ad = TMA ? smem_desc_sw64(a + ks * 32) : smem_desc(a + ks * 256);
+          const uint64_t bd = TMA ? smem_desc_sw64(b + ks * 32) : smem_desc(b + ks * 256);
           const uint32_t acc = (c < TL::NACC && term == 0 && ks == 0) ? 0u : 1u;
           asm volatile(
               "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -319,34 +364,83 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                  : "memory");
 }
 
+// Tensor maps of the GEMM operands (2-D views, rows x N values, 64-byte swizzle, boxes of
+// KC columns): the TF32 pairs in (H32, D32) and in the two halves of XT with 128-row boxes,
+// the sine tables with BN-row boxes.  Encoded once at setup through the driver entry point.
+struct TcMaps {
+  CUtensorMap a_hi[2], a_lo[2], s_hi, s_lo;
+  const float* a_base[2];          // H32 and the first half of XT: which pair a GEMM reads
+  int bn;
+};
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool encode_map(EncodeTiled enc, CUtensorMap* m, const float* base, long rows, int cols,
+                int box_rows) {
+  const cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)cols * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)box_rows};
+  const cuuint32_t estride[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dim, stride, box,
+             estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// tile width of the context: 128 x 256 where it fills the GPU (2-D N >= 2048, 3-D N^2 rows),
+// else 128 x 64
+int tile_bn(const Ctx& c) {
+  const bool wide = c.N >= 2048 || c.dim == 3;
+  return wide ? (c.N % 256 == 0 ? 256 : 128) : 64;
+}
+
 template <int BN>
 kfbi_status gemm_n(Ctx& c, const float* ahi, const float* alo, float* out, float* out_lo,
                    int mode) {
   static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
   static std::atomic<bool> attr{false};
   if (!attr) {
-    KFBI_CUDA_TRY(cudaFuncSetAttribute(dst_gemm_kernel<BN>,
+    KFBI_CUDA_TRY(cudaFuncSetAttribute(dst_gemm_kernel<BN, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<BN>::SMEM));
+    KFBI_CUDA_TRY(cudaFuncSetAttribute(dst_gemm_kernel<BN, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<BN>::SMEM));
     attr = true;
   }
   const int N = c.N, M = c.dim == 3 ? N * N : N;
   const double s1 = 2.0 / N;
   const float scale = (float)(c.dim == 3 ? s1 * s1 * s1 : s1 * s1);
+  // TMA loads when the operand pair has tensor maps (KFBI_TC_CPASYNC=1 forces the cp.async
+  // producers, for comparison)
+  static const bool force_cpasync = [] {
+    const char* e = std::getenv("KFBI_TC_CPASYNC");
+    return e && e[0] == '1';
+  }();
+  const TcMaps* tm = reinterpret_cast<const TcMaps*>(c.tc_maps);
+  const int pair = (tm && ahi == tm->a_base[0]) ? 0 : ((tm && ahi == tm->a_base[1]) ? 1 : -1);
+  const bool tma = tm && pair >= 0 && tm->bn == BN && !force_cpasync;
+  static const CUtensorMap zero_map{};
   const int pr = prof_begin(c, ST_TC);
-  dst_gemm_kernel<BN><<<dim3(N / BN, M / BM), GEMM_THREADS, Tile<BN>::SMEM, c.stream>>>(
-      ahi, alo, c.tc_shi, c.tc_slo, out, out_lo, M, N, mode, c.t32.lam, (float)c.kappa2, scale,
-      c.err_flag + 2);
+  if (tma)
+    dst_gemm_kernel<BN, true><<<dim3(N / BN, M / BM), GEMM_THREADS, Tile<BN>::SMEM, c.stream>>>(
+        ahi, alo, c.tc_shi, c.tc_slo, tm->a_hi[pair], tm->a_lo[pair], tm->s_hi, tm->s_lo, out,
+        out_lo, M, N, mode, c.t32.lam, (float)c.kappa2, scale, c.err_flag + 2);
+  else
+    dst_gemm_kernel<BN, false><<<dim3(N / BN, M / BM), GEMM_THREADS, Tile<BN>::SMEM, c.stream>>>(
+        ahi, alo, c.tc_shi, c.tc_slo, zero_map, zero_map, zero_map, zero_map, out, out_lo, M, N,
+        mode, c.t32.lam, (float)c.kappa2, scale, c.err_flag + 2);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
 }
 
-// 128 x 256 tiles where they fill the GPU (2-D N >= 2048, 3-D N^2 rows), else 128 x 64
 kfbi_status gemm(Ctx& c, const float* ahi, const float* alo, float* out, float* out_lo, int mode) {
-  const bool wide = c.N >= 2048 || c.dim == 3;
-  if (wide && c.N % 256 == 0) return gemm_n<256>(c, ahi, alo, out, out_lo, mode);
-  if (wide) return gemm_n<128>(c, ahi, alo, out, out_lo, mode);
-  return gemm_n<64>(c, ahi, alo, out, out_lo, mode);
+  switch (tile_bn(c)) {
+    case 256: return gemm_n<256>(c, ahi, alo, out, out_lo, mode);
+    case 128: return gemm_n<128>(c, ahi, alo, out, out_lo, mode);
+    default: return gemm_n<64>(c, ahi, alo, out, out_lo, mode);
+  }
 }
 
 }  // namespace
@@ -364,7 +458,42 @@ kfbi_status init_tc_tables(Ctx& c) {
   prof_count(c, ST_SETUP);
   sine_split_kernel<<<4096, 256, 0, c.stream>>>(c.N, c.tc_shi, c.tc_slo);
   KFBI_CUDA_TRY(cudaGetLastError());
+  // tensor maps for the TMA producer; without the driver entry point the GEMMs fall back to
+  // the cp.async producers
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return KFBI_OK;
+  }
+  const EncodeTiled enc = reinterpret_cast<EncodeTiled>(fn);
+  TcMaps* tm = new (std::nothrow) TcMaps();
+  if (!tm) return KFBI_OK;
+  const long rows = c.dim == 3 ? (long)c.N * c.N : c.N;
+  const long total = rows * c.N;
+  const float* xt = reinterpret_cast<const float*>(c.XT);
+  tm->bn = tile_bn(c);
+  tm->a_base[0] = c.H32;
+  tm->a_base[1] = xt;
+  const bool ok = encode_map(enc, &tm->a_hi[0], c.H32, rows, c.N, BM) &&
+                  encode_map(enc, &tm->a_lo[0], c.D32, rows, c.N, BM) &&
+                  encode_map(enc, &tm->a_hi[1], xt, rows, c.N, BM) &&
+                  encode_map(enc, &tm->a_lo[1], xt + total, rows, c.N, BM) &&
+                  encode_map(enc, &tm->s_hi, c.tc_shi, c.N, c.N, tm->bn) &&
+                  encode_map(enc, &tm->s_lo, c.tc_slo, c.N, c.N, tm->bn);
+  if (!ok) {
+    delete tm;
+    return KFBI_OK;
+  }
+  c.tc_maps = tm;
   return KFBI_OK;
+}
+
+void free_tc(Ctx& c) {
+  delete reinterpret_cast<TcMaps*>(c.tc_maps);
+  c.tc_maps = nullptr;
 }
 
 // rhs and work: FP32 work grids (N^2 or N^3, may be the same buffer).  Scratch: the TF32

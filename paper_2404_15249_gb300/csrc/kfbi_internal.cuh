@@ -147,6 +147,7 @@ struct Ctx {
   void* XT = nullptr;                               // transposed work grid (N x N, FP64 size)
   float* tc_shi = nullptr;                          // sine matrix, TF32 high part (N x N)
   float* tc_slo = nullptr;                          // sine matrix, TF32 low part
+  void* tc_maps = nullptr;                          // TMA tensor maps of the GEMM operands
   BoxTables<float> t32{};
   BoxTables<double> t64{};
   int rows_variant[2] = {0, 0};                     // row-pass variant per precision (autotuned)
@@ -217,6 +218,7 @@ inline bool valid_precision(int p) {
 bool tc_supported(const Ctx& c);
 kfbi_status init_tc_tables(Ctx& c);
 kfbi_status box_solve_tc(Ctx& c, const float* rhs, float* work);
+void free_tc(Ctx& c);
 
 // 3-D (kfbi3d.cu, dst3d.cu): setup and the same stages on the N^3 work grid
 kfbi_status setup_geometry3(Ctx& c);
