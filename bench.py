@@ -378,7 +378,7 @@ def run_kfbi(a):
         batch = run_batch_companion(a, dev)
     tc = None
     if rank == 0 and a.ntc > 0:
-        tc = run_tc_companion(a, dev, flush)
+        tc = run_tc_companion(a, dev, flush, ctx, N) if N % 128 == 0 and N <= 8192 else None
 
     launches = int(sum(v[1] for v in stages.values()))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -503,28 +503,25 @@ def run_3d_companion(a, dev, flush):
             "box_solve_fft_vs_tc": tc}
 
 
-def run_tc_companion(a, dev, flush):
+def run_tc_companion(a, dev, flush, main_ctx, main_N):
     """The tensor-core box solve (dense sine-matrix form, four tcgen05 TF32 GEMMs with a
-    three-term split) against the FFT FP32 box solve on one flower context: median of 10
-    solves each (L2 flushed before each), and one mixed-precision BVP solve with the
-    tensor-core apply as its lowest tier.  Tensor roofline: 24 N^3 flops per solve (4 GEMMs
-    x 3 products x 2 N^3) against the TF32 peak taken as the measured BF16 burst peak times
-    the nominal TF32/BF16 ratio."""
+    three-term split, operands loaded by TMA) against the FFT FP32 box solve: median of 10
+    solves each (L2 flushed before each) on the headline context (N = main_N) and on a
+    flower context at N = --ntc, plus one mixed-precision BVP solve there with the
+    tensor-core apply as its lowest tier.  Tensor roofline (at main_N): 24 N^3 flops per
+    solve (4 GEMMs x 3 products x 2 N^3) against the TF32 peak taken as the measured BF16
+    burst peak times the nominal TF32/BF16 ratio."""
     import numpy as np
     import torch
     import kfbi_workloads as W
     import paper_2404_15249_gb300 as K
 
-    N = a.ntc
-    prob = W.config_helmholtz(N, a.kappa, "flower")
-    ctx = K.Kfbi2D(prob.iface.pts, prob.iface.normals, prob.iface.curv, N, a.kappa,
-                   precision=K.KFBI_TF32X3, tol=1e-10)
-    rng = np.random.default_rng(W.SEED)
-    b = torch.as_tensor(rng.standard_normal((N + 1, N + 1)), device=dev)
-    v = torch.empty_like(b)
     st = torch.cuda.current_stream()
+    rng = np.random.default_rng(W.SEED)
 
-    def med(prec, n=10):
+    def med(ctx, n_grid, prec, n=10):
+        b = torch.as_tensor(rng.standard_normal((n_grid + 1, n_grid + 1)), device=dev)
+        v = torch.empty_like(b)
         for _ in range(3):
             ctx.box_solve(b, prec, out=v)
         out = []
@@ -538,11 +535,17 @@ def run_tc_companion(a, dev, flush):
             out.append(e0.elapsed_time(e1))
         return statistics.median(out)
 
-    ms_tc, ms_fft = med(K.KFBI_TF32X3), med(K.KFBI_MIXED_FP32)
+    big_tc = med(main_ctx, main_N, K.KFBI_TF32X3)
+    big_fft = med(main_ctx, main_N, K.KFBI_MIXED_FP32)
+    N = a.ntc
+    prob = W.config_helmholtz(N, a.kappa, "flower")
+    ctx = K.Kfbi2D(prob.iface.pts, prob.iface.normals, prob.iface.curv, N, a.kappa,
+                   precision=K.KFBI_TF32X3, tol=1e-10)
+    ms_tc, ms_fft = med(ctx, N, K.KFBI_TF32X3), med(ctx, N, K.KFBI_MIXED_FP32)
     fg = torch.as_tensor(prob.f_grid(), device=dev)
     fc = torch.as_tensor(prob.f_ctrl(), device=dev)
     gc = torch.as_tensor(prob.g_ctrl(), device=dev)
-    u = torch.empty_like(b)
+    u = torch.empty((N + 1, N + 1), dtype=torch.float64, device=dev)
     ctx.solve_bvp(fg, fc, gc, u_out=u)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
@@ -552,19 +555,22 @@ def run_tc_companion(a, dev, flush):
     inside = ctx.inside_mask().cpu().numpy().astype(bool)
     err = float(np.max(np.abs(u.cpu().numpy() - prob.u_grid())[inside]))
     ctx.close()
-    flops = 24.0 * N ** 3
+    flops = 24.0 * main_N ** 3
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     bf16 = float(json.load(open(pk))["bf16_tflops"]) if os.path.exists(pk) else 1900.0
     peak = bf16 * NOMINAL_TF32_PER_BF16
-    return {"workload": f"box solve (Alg. 4, dense form) of a random right-hand side on the "
-                        f"flower context, N={N}, kappa={a.kappa}; mixed BVP solve with "
-                        f"tensor-core applies as the lowest tier",
-            "N": N, "tc_box_solve_ms": ms_tc, "fft_fp32_box_solve_ms": ms_fft,
-            "roofline": {"bound": "tensor", "kernel": "dst_gemm_kernel (tcgen05 kind::tf32)",
-                         "achieved": flops / (ms_tc / 1e3) / 1e12, "peak": peak,
-                         "unit": "TFLOP/s", "frac": flops / (ms_tc / 1e3) / 1e12 / peak,
+    return {"workload": f"box solves (Alg. 4, dense form on the tensor cores vs FFT FP32) of a "
+                        f"random right-hand side at N={main_N} (headline context) and N={N} "
+                        f"(flower, kappa={a.kappa}); mixed BVP solve at N={N} with tensor-core "
+                        f"applies as the lowest tier",
+            "N": main_N, "tc_box_solve_ms": big_tc, "fft_fp32_box_solve_ms": big_fft,
+            "roofline": {"bound": "tensor", "kernel": "dst_gemm_kernel (tcgen05 kind::tf32, TMA)",
+                         "achieved": flops / (big_tc / 1e3) / 1e12, "peak": peak,
+                         "unit": "TFLOP/s", "frac": flops / (big_tc / 1e3) / 1e12 / peak,
                          "peak_source": "measured BF16 burst x nominal TF32/BF16 ratio",
                          "flops_per_solve": flops},
+            "small": {"N": N, "tc_box_solve_ms": ms_tc, "fft_fp32_box_solve_ms": ms_fft,
+                      "tensor_tflops": 24.0 * N ** 3 / (ms_tc / 1e3) / 1e12},
             "mixed_tc_solve_ms": e0.elapsed_time(e1), "mixed_tc_iterations": info["iterations"],
             "mixed_tc_applies_low": info["applies_low"], "mixed_tc_err_inf": err}
 
