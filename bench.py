@@ -146,16 +146,22 @@ def traffic_for(kernel, N):
 
 STAGE_KERNEL = {"dst_rows_f32": ("rows_kernel<float>", 4), "dst_cols_f32": ("cols_kernel<float>", 4),
                 "dst_rows_f64": ("rows_kernel<double>", 8), "dst_cols_f64": ("cols_kernel<double>", 8),
-                "transpose": ("transpose_vec_kernel<float>", 4)}
+                "transpose": ("transpose_vec_kernel<float>", 4),
+                "dst_tri_f32": ("ytri_kernel<float>", 4)}
 
 
-def roofline(stage_ms, N, variants):
+def roofline(stage_ms, N, variants, tri_k0):
     """Dominant stage of the timed region -> roofline entry for its kernel.  The column
     stage is yline_kernel when the autotuner chose the transposed column pass (variant bit
-    2; the transposes are then their own stage), else cols_kernel."""
+    2; the transposes are then their own stage), else cols_kernel.  In FP32 the y-line
+    transform pair runs on the x-modes below tri_k0 and the tridiagonal y-solve on the
+    rest, so their algorithmic bytes cover tri_k0 and N - tri_k0 lines."""
     kernels = dict(STAGE_KERNEL)
+    lines = {k: N for k in kernels}
     if variants[1] & 4:
         kernels["dst_cols_f32"] = ("yline_kernel<float>", 4)
+        lines["dst_cols_f32"] = tri_k0
+    lines["dst_tri_f32"] = N - tri_k0
     if variants[3] & 4:
         kernels["dst_cols_f64"] = ("yline_kernel<double>", 8)
     cand = {k: v for k, v in stage_ms.items() if k in kernels and v[1] > 0 and v[0] > 0}
@@ -176,7 +182,7 @@ def roofline(stage_ms, N, variants):
                 "peak_source": "nominal FP64", "traffic": None, "launches": launches,
                 "avg_launch_us": avg_s * 1e6}
     peak, src = peaks()
-    nbytes = 2.0 * N * N * esize          # every unknown read once and written once
+    nbytes = 2.0 * N * lines[name] * esize   # every unknown of its lines read and written once
     ach = nbytes / avg_s / 1e9
     return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak, "peak_source": src, "traffic": traffic_for(kernel, N),
@@ -388,7 +394,7 @@ def run_kfbi(a):
                        "precision": "FP32 box solves, FP64 geometry/Krylov/refinement",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "replicas": world},
-            "roofline": roofline(stages, N, ctx.info()["dst_variant"]),
+            "roofline": roofline(stages, N, ctx.info()["dst_variant"], ctx.info()["tri_first_mode"]),
             "dst_variant": ctx.info()["dst_variant"],
             "cpu_baseline": cpu,
             "clocks": clk,

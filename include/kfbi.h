@@ -123,6 +123,9 @@ typedef struct {
                             transpose back) */
   int dim;               /* 2 or 3                                                        */
   int n_crossings_z;     /* 3-D: points on z-lines; 0 in 2-D                              */
+  int tri_first_mode;    /* 2-D FP32 box solves: x-modes k >= this are solved along y by
+                            tridiagonal elimination (the lower ones by the sine-transform
+                            pair); N when every mode takes the transform pair           */
 } kfbi_ctx_info;
 
 /* Fills *opt with dim 2, N 128, box [-1,1], kappa 0, FP64, m 50, 20 restarts,
@@ -252,7 +255,8 @@ kfbi_status kfbi_set_solver(kfbi_ctx ctx, int precision, int gmres_m, int max_re
    build/copy, 8 Krylov vector kernels, 9 residual refinement of FP32 box solves,
    10 tile transposes of the work grid, 11 the sparse first x-transform of the plain FP32
    2-D apply (evaluated from the irregular nodes straight into the transposed layout),
-   12 the tensor-core GEMMs of the dense box solve (KFBI_TF32X3).  Launch counts are always
+   12 the tensor-core GEMMs of the dense box solve (KFBI_TF32X3), 13 the tridiagonal
+   y-solves of the well-conditioned x-modes in the FP32 2-D box solve.  Launch counts are always
    kept; times only while profiling is on (enabling clears both). */
 #define KFBI_NSTAGES 16
 typedef struct {

@@ -59,7 +59,7 @@ class CtxInfo(ctypes.Structure):
                 ("n_crossings_y", ctypes.c_int), ("n_irregular", ctypes.c_int),
                 ("n_inside", ctypes.c_int), ("device_bytes", ctypes.c_int64),
                 ("dst_variant", ctypes.c_int * 4), ("dim", ctypes.c_int),
-                ("n_crossings_z", ctypes.c_int)]
+                ("n_crossings_z", ctypes.c_int), ("tri_first_mode", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -184,6 +184,7 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
   if (dim == 2) {
     // KFBI_DST_VARIANTS="r32,c32,r64,c64" fixes the transform variants (profiling runs,
     // where the autotuner's timings would be distorted by the profiler)
+    c.tri_k0 = kfbi::tri_first_mode(c);
     const char* fixed = std::getenv("KFBI_DST_VARIANTS");
     int v[4];
     if (fixed && std::sscanf(fixed, "%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3]) == 4 &&
@@ -305,6 +306,7 @@ kfbi_status kfbi_get_info(kfbi_ctx ctx, kfbi_ctx_info* info) {
   info->n_crossings_x = c.dim == 2 ? c.ncross[0] : c.npts_axis[0];
   info->n_crossings_y = c.dim == 2 ? c.ncross[1] : c.npts_axis[1];
   info->n_crossings_z = c.dim == 2 ? 0 : c.npts_axis[2];
+  info->tri_first_mode = c.dim == 2 ? c.tri_k0 : c.N;
   info->n_irregular = c.nirr;
   info->n_inside = c.n_inside;
   info->device_bytes = c.bytes + (int64_t)sizeof(double) * ((int64_t)(c.gm_m + 1) * c.M);
@@ -457,7 +459,7 @@ kfbi_status kfbi_profile_read(kfbi_ctx ctx, kfbi_stage_times* out) {
 const char* kfbi_stage_name(int s) {
   static const char* names[] = {"setup", "correction", "dst_rows_f32", "dst_cols_f32",
                                 "dst_rows_f64", "dst_cols_f64", "interpolation", "grid",
-                                "krylov", "refine", "transpose", "sparse_x_f32", "dst_tc_tf32x3"};
+                                "krylov", "refine", "transpose", "sparse_x_f32", "dst_tc_tf32x3", "dst_tri_f32"};
   return (s >= 0 && s < kfbi::ST_COUNT) ? names[s] : "unused";
 }
 

@@ -27,6 +27,7 @@
 #pragma once
 
 #include <atomic>
+#include <type_traits>
 
 #include "kfbi_internal.cuh"
 
@@ -870,11 +871,16 @@ kfbi_status launch_ylines(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
   const T scale = T((2.0 / N) * (2.0 / N));
   KFBI_TRY(launch_transpose<T>(c, V, X, N, N, 1));
+  // FP32: the well-conditioned x-modes k >= tri_k0 are solved along y by elimination
+  const int nfft = (std::is_same<T, float>::value && c.tri_k0 > 0 && c.tri_k0 < N) ? c.tri_k0 : N;
+  const int fblocks = blocks < (nfft + lpc - 1) / lpc ? blocks : (nfft + lpc - 1) / lpc;
   const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
-  yline_kernel<T, N, EPT, 2><<<blocks, threads, smem, c.stream>>>(X, stw, tw, lam, T(c.kappa2),
-                                                                  scale, N, c.err_flag + 2);
+  yline_kernel<T, N, EPT, 2><<<fblocks, threads, smem, c.stream>>>(X, stw, tw, lam, T(c.kappa2),
+                                                                   scale, nfft, c.err_flag + 2);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
+  if constexpr (std::is_same<T, float>::value)
+    if (nfft < N) KFBI_TRY(ytri_f32(c, X, nfft));
   KFBI_TRY(launch_transpose<T>(c, X, V, N, N, 1));
   return KFBI_OK;
 }
@@ -901,11 +907,15 @@ kfbi_status launch_ylines_only(Ctx& c, T* X, const cx<T>* tw, const T* lam) {
   int blocks = (N + lpc - 1) / lpc;
   blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
   const T scale = T((2.0 / N) * (2.0 / N));
+  const int nfft = (std::is_same<T, float>::value && c.tri_k0 > 0 && c.tri_k0 < N) ? c.tri_k0 : N;
+  const int fblocks = blocks < (nfft + lpc - 1) / lpc ? blocks : (nfft + lpc - 1) / lpc;
   const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
-  yline_kernel<T, N, EPT, 2><<<blocks, threads, smem, c.stream>>>(X, stw, tw, lam, T(c.kappa2),
-                                                                  scale, N, c.err_flag + 2);
+  yline_kernel<T, N, EPT, 2><<<fblocks, threads, smem, c.stream>>>(X, stw, tw, lam, T(c.kappa2),
+                                                                   scale, nfft, c.err_flag + 2);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
+  if constexpr (std::is_same<T, float>::value)
+    if (nfft < N) KFBI_TRY(ytri_f32(c, X, nfft));
   return KFBI_OK;
 }
 

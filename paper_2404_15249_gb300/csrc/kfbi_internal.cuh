@@ -62,7 +62,8 @@ struct BoxTables {
 enum Stage : int {
   ST_SETUP = 0, ST_CORR = 1, ST_ROWS32 = 2, ST_COLS32 = 3, ST_ROWS64 = 4, ST_COLS64 = 5,
   ST_INTERP = 6, ST_GRID = 7, ST_KRYLOV = 8, ST_REFINE = 9, ST_TRANS = 10, ST_SPARSE = 11,
-  ST_TC = 12, ST_COUNT = 13   // ST_SPARSE: sparse first x-transform; ST_TC: tensor-core GEMMs
+  ST_TC = 12, ST_TRI = 13, ST_COUNT = 14   // ST_SPARSE: sparse first x-transform; ST_TC:
+                                           // tensor-core GEMMs; ST_TRI: tridiagonal y-solves
 };
 
 struct Prof {
@@ -148,6 +149,7 @@ struct Ctx {
   float* tc_shi = nullptr;                          // sine matrix, TF32 high part (N x N)
   float* tc_slo = nullptr;                          // sine matrix, TF32 low part
   void* tc_maps = nullptr;                          // TMA tensor maps of the GEMM operands
+  int tri_k0 = 0;        // 2-D FP32: x-modes >= tri_k0 solved along y by elimination (N: none)
   BoxTables<float> t32{};
   BoxTables<double> t64{};
   int rows_variant[2] = {0, 0};                     // row-pass variant per precision (autotuned)
@@ -219,6 +221,10 @@ bool tc_supported(const Ctx& c);
 kfbi_status init_tc_tables(Ctx& c);
 kfbi_status box_solve_tc(Ctx& c, const float* rhs, float* work);
 void free_tc(Ctx& c);
+
+// tridiagonal y-solves of the well-conditioned x-modes (dst_tri.cu)
+int tri_first_mode(const Ctx& c);
+kfbi_status ytri_f32(Ctx& c, float* X, int k0);
 
 // 3-D (kfbi3d.cu, dst3d.cu): setup and the same stages on the N^3 work grid
 kfbi_status setup_geometry3(Ctx& c);
