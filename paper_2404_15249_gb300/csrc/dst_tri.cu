@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(TRI_THREADS)
 // 64 chunks per line from N = 2048 (shorter recursions per thread), 32 below
 template <int N>
 kfbi_status launch_tri(Ctx& c, float* X, int k0) {
-  constexpr int CH = N >= 2048 ? 64 : 32;
+  constexpr int CH = N >= 4096 ? 128 : (N >= 2048 ? 64 : 32);
   constexpr int LPB = TRI_THREADS / CH;
   constexpr size_t smem = (size_t)LPB * (N + CH + 2 * TRI_EXACT) * sizeof(float);
   static_assert(smem <= 227 * 1024, "tridiagonal pass exceeds shared memory");
