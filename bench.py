@@ -124,9 +124,16 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+KERNEL_SOURCE = {"rows_kernel": "dst_impl.cuh", "yline_kernel": "dst_impl.cuh",
+                 "cols_kernel": "dst_impl.cuh", "transpose_vec_kernel": "dst_impl.cuh",
+                 "ytri_kernel": "dst_tri.cu", "sparse_rows_t_kernel": "apply2d.cu"}
+
+
+def kernel_source_hash(kernel):
+    """First 12 hex digits of the SHA-256 of the CUDA source that defines `kernel`."""
     h = hashlib.sha256()
-    h.update(open(os.path.join(ROOT, "paper_2404_15249_gb300", "csrc", "dst_impl.cuh"), "rb").read())
+    src = KERNEL_SOURCE.get(kernel.split("<")[0], "dst_impl.cuh")
+    h.update(open(os.path.join(ROOT, "paper_2404_15249_gb300", "csrc", src), "rb").read())
     return h.hexdigest()[:12]
 
 
@@ -135,7 +142,7 @@ def traffic_for(kernel, N):
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    src = kernel_source_hash()
+    src = kernel_source_hash(kernel)
     for line in open(p):
         f = line.split()
         if len(f) >= 5 and not line.startswith("#") and f[0] == kernel and f[1] == src:
