@@ -170,6 +170,8 @@ struct Ctx {
   cudaEvent_t gm_ev[2] = {nullptr, nullptr};   // Arnoldi-step flag copies done
   double* gm_part = nullptr;       // per-block partial dot products
   unsigned* gm_counter = nullptr;  // blocks done in the current multi-dot
+  double* arn_part = nullptr;      // fused Arnoldi step: 3 x arn_grid x (m + 1) partial sums
+  int arn_grid = 0;                // its cooperative grid (0: the fused step is not used)
   int* err_flag = nullptr;     // device error flag
 
   int64_t bytes = 0;
