@@ -12,6 +12,9 @@
 //           (2/N)^2 / (lambda_k + lambda_l - kappa^2), DST-I along y again
 //   pass 3  DST-I along x of every row
 // with lambda_k = -(4/h^2) sin^2(pi k / 2N) the eigenvalues of the 1-D second difference.
+// In FP32 (2-D) pass 2 keeps the transform pair only for the low x-modes; the others are
+// solved along y by tridiagonal elimination (dst_tri.cu), the same system without the
+// transforms.
 //
 // DST-I of a line through one complex FFT of length N: z_m = u_{2m} + i u_{2m+1} packs the
 // odd extension u of the line (u_{2N-j} = -x_j); with Z = FFT_N(z), Z_k = a + ib and

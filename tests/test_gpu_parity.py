@@ -259,3 +259,28 @@ def test_fused_arnoldi_step_matches_the_five_kernel_step():
     assert out["0"][2]["iterations"] == out["1"][2]["iterations"]
     assert rel(out["1"][1], out["0"][1]) < 1e-12
     assert rel(out["1"][0], out["0"][0]) < 1e-12
+
+
+@pytest.mark.parametrize("kappa", [0.0, 10.0])
+def test_fp32_box_solve_with_and_without_the_tridiagonal_pass(kappa):
+    """FP32 box solves with the well-conditioned x-modes solved along y by tridiagonal
+    elimination (the default) and with every mode on the sine-transform pair
+    (KFBI_TRI=0 at setup): both within 2e-5 of the oracle."""
+    import os
+    N = 256
+    prob = W.Problem(W.circle(64, 0.4, (0.01, 0.02)), N, kappa, W.manufactured_sinpi(kappa))
+    rng = np.random.default_rng(N + 1)
+    b = np.zeros((N + 1, N + 1))
+    b[1:N, 1:N] = rng.standard_normal((N - 1, N - 1))
+    for flag in (None, "0"):
+        if flag is not None:
+            os.environ["KFBI_TRI"] = flag
+        try:
+            ctx, geom = make(prob)
+        finally:
+            os.environ.pop("KFBI_TRI", None)
+        k0 = ctx.info()["tri_first_mode"]
+        assert (k0 == N) if flag == "0" else (0 < k0 < N / 8)
+        ref = O.box_solve_dst(b, N, geom.h, kappa * kappa)
+        assert rel(ctx.box_solve(b, K.KFBI_MIXED_FP32).cpu().numpy(), ref) < 2e-5
+        ctx.close()
