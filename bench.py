@@ -197,6 +197,23 @@ def roofline(stage_ms, N, variants, tri_k0):
 
 
 # ------------------------------------------------------------------------ arms
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (x itself on one rank): the job's step time is that of
+    its slowest replica."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, grid_points, applies, ms):
+    """Grid points per second per apply summed over the world's replicas, each of which
+    runs the same solve in ms milliseconds (the slowest rank's time)."""
+    return world * grid_points * applies / (ms / 1e3)
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -312,14 +329,10 @@ def run_kfbi(a):
     ctx.profile(False)
     barrier()
     clk = clocks.stop()
-    ms = statistics.mean(step_ms)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(step_ms), dist, dev)
     applies = infos[-1]["applies_fp64"] + infos[-1]["applies_low"]
     err_mixed = err_inf(u)
-    value = world * (N + 1) ** 2 * applies / (ms / 1e3)
+    value = whole_job_rate(world, (N + 1) ** 2, applies, ms)
 
     # ---------------- FP64 path on the same inputs (same error check, speedup)
     fp64 = {}
@@ -364,12 +377,8 @@ def run_kfbi(a):
             e1.record(st)
             e1.synchronize()
             e2e_ms.append(e0.elapsed_time(e1))
-        em = statistics.mean(e2e_ms)
-        if dist is not None:
-            t = torch.tensor([em], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            em = float(t.item())
-        e2e = {"value": world * (N + 1) ** 2 * applies / (em / 1e3), "unit": UNIT,
+        em = max_over_ranks(statistics.mean(e2e_ms), dist, dev)
+        e2e = {"value": whole_job_rate(world, (N + 1) ** 2, applies, em), "unit": UNIT,
                "ms_per_step": em,
                "h2d_bytes_per_step": (h_fg.numel() + h_fc.numel() + h_gc.numel()) * 8,
                "d2h_bytes_per_step": (h_u.numel() + h_phi.numel()) * 8}
