@@ -81,30 +81,48 @@ __global__ void __launch_bounds__(TRI_THREADS)
     __syncthreads();
     const int s = lane * M, e = s + M;
     const int s1 = s < 1 ? 1 : s;                  // point 0 is the boundary
-    // forward elimination y_j = (x_j - A y_{j-1}) / den_j: warm-up, then in place
+    // the thread's chunk in registers: the recursions' dependency chains then run on
+    // register operands, shared memory is only read by the warm-ups and the final store
+    float r[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) r[i] = buf[tpad<N, CH>(s + i)];
+    // forward elimination y_j = (x_j - A y_{j-1}) / den_j: warm-up on the previous
+    // chunk's values, then the own chunk
     float y = 0.f;
 #pragma unroll 4
     for (int j = (s1 - w > 1 ? s1 - w : 1); j < s1; ++j)
       y = (buf[tpad<N, CH>(j)] - A * y) * (j < TRI_EXACT ? idx[j] : gs);
-    __syncthreads();
-#pragma unroll 4
-    for (int j = s1; j < e; ++j) {
-      y = (buf[tpad<N, CH>(j)] - A * y) * (j < TRI_EXACT ? idx[j] : gs);
-      buf[tpad<N, CH>(j)] = y;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const int j = s + i;
+      if (j >= 1) {
+        y = (r[i] - A * y) * (j < TRI_EXACT ? idx[j] : gs);
+        r[i] = y;
+      }
     }
+    __syncthreads();                               // every warm-up read the input values
+#pragma unroll
+    for (int i = 0; i < M; ++i) buf[tpad<N, CH>(s + i)] = r[i];
     __syncthreads();
-    // back substitution v_j = y_j - c'_j v_{j+1} (v_N = 0): warm-up, then in place, scaled
+    // back substitution v_j = y_j - c'_j v_{j+1} (v_N = 0): warm-up on the next chunk's
+    // y, then the own chunk, scaled
     float v = 0.f;
 #pragma unroll 4
     for (int j = (e - 1 + w < N - 1 ? e - 1 + w : N - 1); j >= e; --j)
       v = buf[tpad<N, CH>(j)] - (j < TRI_EXACT ? cpx[j] : cs) * v;
-    __syncthreads();
-#pragma unroll 4
-    for (int j = e - 1; j >= s1; --j) {
-      v = buf[tpad<N, CH>(j)] - (j < TRI_EXACT ? cpx[j] : cs) * v;
-      buf[tpad<N, CH>(j)] = v * scale;
+#pragma unroll
+    for (int i = M - 1; i >= 0; --i) {
+      const int j = s + i;
+      if (j >= 1) {
+        v = r[i] - (j < TRI_EXACT ? cpx[j] : cs) * v;
+        r[i] = v * scale;
+      } else {
+        r[i] = 0.f;
+      }
     }
-    if (lane == 0) buf[0] = 0.f;
+    __syncthreads();                               // every warm-up read the y values
+#pragma unroll
+    for (int i = 0; i < M; ++i) buf[tpad<N, CH>(s + i)] = r[i];
     __syncthreads();
     if (act)
       for (int q = lane; q < N / 4; q += CH) {
