@@ -56,9 +56,12 @@ typedef enum {
 
 typedef enum {
   KFBI_FP64 = 0,         /* every stage in FP64                                          */
-  KFBI_MIXED_FP32 = 1,   /* box solve in FP32 (apply); as a solver mode: FP64 Arnoldi and
-                            Givens with relaxed-precision matvecs and FP64-accurate
-                            residuals (see kfbi_solve_bvp)                               */
+  KFBI_MIXED_FP32 = 1,   /* box solve in FP32 (apply; in 2-D the well-conditioned x-modes
+                            are solved along y by tridiagonal elimination, the others by
+                            the sine-transform pair, see kfbi_ctx_info.tri_first_mode);
+                            as a solver mode: FP64 Arnoldi and Givens with relaxed-
+                            precision matvecs and FP64-accurate residuals (see
+                            kfbi_solve_bvp)                                              */
   KFBI_FP32_REFINED = 2, /* box solve from FP32 sine transforms corrected twice against
                             the residual of the 5-point system, formed in double-single
                             (exact FP32-pair) arithmetic at regular nodes and in FP64 at
