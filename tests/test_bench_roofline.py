@@ -1,0 +1,48 @@
+"""The bench's roofline bookkeeping on synthetic stage timings (no GPU): the dominant stage
+is picked by total time, its algorithmic bytes cover the lines its kernel owns, and the
+committed DRAM traffic is used only while the kernel's source hash matches."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+N = 4096
+
+
+def test_dominant_stage_and_bytes():
+    stages = {"dst_rows_f32": (5.6, 98), "dst_cols_f32": (1.0, 70), "dst_tri_f32": (2.3, 70),
+              "transpose": (2.1, 98), "krylov": (9.9, 1000)}
+    r = bench.roofline(stages, N, [0, 4, 1, 6], 252)
+    assert r["kernel"] == "rows_kernel<float>"          # krylov is not a transform stage
+    assert r["algorithmic_bytes"] == 2 * N * N * 4
+    assert r["achieved"] == pytest.approx(2 * N * N * 4 / (5.6 / 98 / 1e3) / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+
+
+def test_split_y_pass_bytes():
+    stages = {"dst_cols_f32": (9.0, 70), "dst_tri_f32": (2.3, 70)}
+    r = bench.roofline(stages, N, [0, 4, 1, 6], 252)
+    assert r["kernel"] == "yline_kernel<float>"
+    assert r["algorithmic_bytes"] == 2 * N * 252 * 4      # only the low x-modes
+    stages = {"dst_cols_f32": (1.0, 70), "dst_tri_f32": (2.3, 70)}
+    r = bench.roofline(stages, N, [0, 4, 1, 6], 252)
+    assert r["kernel"] == "ytri_kernel<float>"
+    assert r["algorithmic_bytes"] == 2 * N * (N - 252) * 4
+
+
+def test_traffic_only_for_the_current_source():
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    lines = [l.split() for l in open(p) if l.strip() and not l.startswith("#")]
+    rows = [f for f in lines if f[0] == "rows_kernel<float>"]
+    assert rows, "the dominant kernel has a committed traffic line"
+    current = bench.kernel_source_hash("rows_kernel<float>")
+    got = bench.traffic_for("rows_kernel<float>", N)
+    if rows[0][1] == current:
+        assert got == pytest.approx(float(rows[0][3]))
+    else:
+        assert got is None
+    assert bench.traffic_for("no_such_kernel", N) is None
