@@ -1,7 +1,7 @@
 """Box-solve micro-benchmark: kfbi_box_solve (Alg. 4) alone (or, with --apply, one
 double-layer apply), on a flower context.
 
-    python -m paper_2404_15249_gb300.boxbench --N 8192 --precision 1 --reps 5
+    python boxbench.py --N 8192 --precision 1 --reps 5
 
 Sets up one context (flower r = 0.5 + 0.15 cos 5t, M = 2N), then times `--reps` box
 solves of a seeded random right-hand side with CUDA events on the default stream, after
@@ -15,9 +15,13 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import statistics
+import sys
 
 import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 def main(argv=None):
@@ -33,7 +37,7 @@ def main(argv=None):
 
     import torch
     import kfbi_workloads as W
-    from . import Kfbi2D, lib, _ptr
+    from paper_2404_15249_gb300 import Kfbi2D, lib, _ptr
 
     N = a.N
     iface = W.flower(2 * N)

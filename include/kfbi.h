@@ -89,9 +89,11 @@ typedef struct {
                            <= 512 (3-D)                                                */
   double lo, hi;        /* box [lo, hi]^dim                                             */
   double kappa;         /* >= 0; PDE Lap u - kappa^2 u = f                               */
-  int precision;        /* kfbi_precision used by kfbi_solve_bvp: FP64 (plain FP64 GMRES),
-                           MIXED_FP32 (GMRES-IR: FP32 inner GMRES, refined-FP32 outer
-                           residuals) or FP32_REFINED (GMRES on refined applies)        */
+  int precision;        /* kfbi_precision used by kfbi_solve_bvp: FP64 (plain FP64 GMRES)
+                           or MIXED_FP32 / TF32X3 (one FP64 Arnoldi process whose matvecs
+                           are twice-refined, once-refined, then plain FP32 or tensor-core
+                           box solves as the residual drops; every restart cycle ends
+                           with an FP64-accurate residual, see kfbi_solve_bvp)        */
   int gmres_m;          /* GMRES restart length (Alg. 5), 1..128                         */
   int max_restarts;     /* GMRES restarts (cycles - 1)                                  */
   double tol;           /* stop when ||g_hat - K_D phi||_2 <= tol ||g_hat||_2            */
@@ -105,7 +107,9 @@ typedef struct {
   int outer_iterations;  /* GMRES restart cycles (each ends with an FP64-accurate residual) */
   int applies_fp64;      /* applies with an FP64-accurate box solve (FP64, or FP32
                             transforms refined against the FP64 residual)               */
-  int applies_low;       /* K_D applies with a plain FP32 box solve (inner GMRES)         */
+  int applies_low;       /* K_D applies with a plain FP32 or tensor-core box solve (the
+                            Arnoldi steps taken once the residual is below
+                            tol / inner_tol)                                             */
   double rel_residual;   /* final ||g_hat - K_D phi|| / ||g_hat|| (FP64 apply)           */
   int converged;         /* 1 if rel_residual <= tol                                     */
 } kfbi_solve_info;
@@ -194,8 +198,8 @@ kfbi_status kfbi_box_solve(kfbi_ctx ctx, int precision, const double* d_b_grid,
                            double* d_v_grid, void* stream);
 
 /* ---------------------------------------------------------- allocation-free box solve
-   The paper has no counterpart to this entry point.  It is the box solve above (Alg. 4,
-   same transform kernels, default variants) for callers that cannot allocate device
+   The paper has no counterpart to this entry point.  It is the box solve above (the same
+   transform kernels in their default variants) for callers that cannot allocate device
    memory when they need it: code running inside a pool that has already reserved the
    device's memory, or where the implicit device synchronisation of cudaMalloc/cudaFree
    cannot be tolerated.  kfbi_setup allocates a workspace sized by N and M, so those
@@ -218,11 +222,21 @@ kfbi_status kfbi_box_solve(kfbi_ctx ctx, int precision, const double* d_b_grid,
    each other's results; order them (one stream, or events).
    Errors: N above KFBI_STATIC_MAX_N or unsupported, null grids, hi <= lo, kappa < 0 or
    another precision -> KFBI_ERR_ARG (message names the limit), before any device work;
-   a failed CUDA call -> KFBI_ERR_CUDA.  Asynchronous on `stream`. */
+   a failed CUDA call -> KFBI_ERR_CUDA.  Asynchronous on `stream`: a bounded device-side
+   wait of the transform kernels that gives up (a staged copy that never completed) is
+   recorded in an error word at the end of the static array, not in this call's status;
+   kfbi_box_solve_static_check reports it. */
 #define KFBI_STATIC_MAX_N 1024
 #define KFBI_STATIC_SCRATCH_BYTES (9u << 20)
 kfbi_status kfbi_box_solve_static(int N, double lo, double hi, double kappa, int precision,
                                   const double* d_b_grid, double* d_v_grid, void* stream);
+
+/* Asynchronous error report of kfbi_box_solve_static (no counterpart in the paper either):
+   synchronises `stream`, then reads the static array's error word of the current device.
+   Returns KFBI_ERR_TIMEOUT, and clears the word, if a bounded wait of any static box solve
+   since the last check gave up (that solve's output is wrong); KFBI_OK otherwise.
+   Allocates nothing. */
+kfbi_status kfbi_box_solve_static_check(void* stream);
 
 /* Dirichlet BVP (Procedures 2-3 of Sec. 4.4): g_hat = g - (Y f)^+, K_D phi = g_hat by
    GMRES(m) (Alg. 5; FP64 Arnoldi with CGS2 and Givens rotations on the device), then

@@ -87,6 +87,7 @@ _SIGS = {
     "kfbi_interface_solve": (I, [P, I, P, P, P, P, P, P, P]),
     "kfbi_box_solve": (I, [P, I, P, P, P]),
     "kfbi_box_solve_static": (I, [I, D, D, D, I, P, P, P]),
+    "kfbi_box_solve_static_check": (I, [P]),
     "kfbi_solve_bvp": (I, [P, P, P, P, P, P, ctypes.POINTER(SolveInfo), P]),
     "kfbi_get_inside_mask": (I, [P, P, P]),
     "kfbi_get_info": (I, [P, ctypes.POINTER(CtxInfo)]),
@@ -305,6 +306,12 @@ def box_solve_static(N, b_grid, kappa=0.0, lo=-1.0, hi=1.0, precision=KFBI_FP64,
                                        _ptr(b_grid), _ptr(out), _stream_ptr(stream)),
            "kfbi_box_solve_static")
     return out
+
+
+def box_solve_static_check(stream=None):
+    """kfbi_box_solve_static_check: synchronises the stream and raises KfbiError
+    (ERR_TIMEOUT) if a bounded wait of an earlier static box solve gave up."""
+    _check(lib().kfbi_box_solve_static_check(_stream_ptr(stream)), "kfbi_box_solve_static_check")
 
 
 def batch_solve(ctxs, f_grids, f_ctrls, g_ctrls, u_grids, nrhs, stream=None):

@@ -17,9 +17,14 @@ constexpr int kMaxN = KFBI_STATIC_MAX_N;
 constexpr size_t kScratchBytes = KFBI_STATIC_SCRATCH_BYTES;
 constexpr int kMaxDevices = 64;
 
-// The scratch array.  Nothing in it has to start at zero: every call writes the tables and
-// the whole work grid before any kernel reads them.
+// The scratch array.  Nothing in the work area has to start at zero: every call writes the
+// tables and the whole work grid before any kernel reads them.  The last kCtlBytes hold the
+// error word (an int set when a bounded wait of a transform kernel gave up); it starts at
+// zero (device statics are zero-initialised at load) and only kfbi_box_solve_static_check
+// clears it again.
 static __device__ __align__(256) unsigned char g_box_scratch[kScratchBytes];
+constexpr size_t kCtlBytes = 256;
+constexpr size_t kWorkBytes = kScratchBytes - kCtlBytes;
 
 std::mutex g_lock;
 unsigned char* g_base[kMaxDevices];   // device address of g_box_scratch, per device
@@ -34,8 +39,8 @@ constexpr size_t bytes_needed() {
          round256(sizeof(T) * (size_t)N) +
          round256(sizeof(cx<T>) * (size_t)(P.twtotal > 0 ? P.twtotal : 1));
 }
-static_assert(bytes_needed<double, kMaxN>() <= kScratchBytes, "scratch too small for max N");
-static_assert(bytes_needed<double, 768>() <= kScratchBytes, "scratch too small for N = 768");
+static_assert(bytes_needed<double, kMaxN>() <= kWorkBytes, "scratch too small for max N");
+static_assert(bytes_needed<double, 768>() <= kWorkBytes, "scratch too small for N = 768");
 
 // twiddles tw[s] = e^{-i pi s/N} (s < 2N) and eigenvalues lam[k] = -(4/h^2) sin^2(pi k/2N)
 // of the 1-D second difference, computed in FP64 and rounded to T
@@ -105,12 +110,13 @@ struct Launch {
     load_kernel<T><<<dim3(gg.x, N), 256, 0, s>>>(N, b, work);
     KFBI_CUDA_TRY(cudaGetLastError());
     const int row_blocks = (N + LPC - 1) / LPC;
-    dst::rows_kernel<T, N, E><<<row_blocks, LPC * P.tpl, rows_smem, s>>>(work, work, stw, tw, T(1), N, nullptr);
+    int* err = reinterpret_cast<int*>(base + kWorkBytes);
+    dst::rows_kernel<T, N, E><<<row_blocks, LPC * P.tpl, rows_smem, s>>>(work, work, stw, tw, T(1), N, err);
     KFBI_CUDA_TRY(cudaGetLastError());
     dst::cols_kernel<T, N, E, 512><<<N / L, L * P.tpl, cols_smem, s>>>(
         work, stw, tw, lam, T(kappa2), T((2.0 / N) * (2.0 / N)));
     KFBI_CUDA_TRY(cudaGetLastError());
-    dst::rows_kernel<T, N, E><<<row_blocks, LPC * P.tpl, rows_smem, s>>>(work, work, stw, tw, T(1), N, nullptr);
+    dst::rows_kernel<T, N, E><<<row_blocks, LPC * P.tpl, rows_smem, s>>>(work, work, stw, tw, T(1), N, err);
     KFBI_CUDA_TRY(cudaGetLastError());
     store_kernel<T><<<gg, 256, 0, s>>>(N, work, v);
     KFBI_CUDA_TRY(cudaGetLastError());
@@ -196,4 +202,21 @@ extern "C" kfbi_status kfbi_box_solve_static(int N, double lo, double hi, double
   if (precision == KFBI_FP64)
     return solve_any<double>(N, base, h, kappa * kappa, d_b_grid, d_v_grid, s);
   return solve_any<float>(N, base, h, kappa * kappa, d_b_grid, d_v_grid, s);
+}
+
+extern "C" kfbi_status kfbi_box_solve_static_check(void* stream) {
+  using namespace kfbi::boxstatic;
+  unsigned char* base = nullptr;
+  KFBI_TRY(device_setup(&base));
+  const cudaStream_t s = (cudaStream_t)stream;
+  KFBI_CUDA_TRY(cudaStreamSynchronize(s));
+  int err = 0;                          // host stack word: a synchronous 4-byte copy
+  KFBI_CUDA_TRY(cudaMemcpy(&err, base + kWorkBytes, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    KFBI_CUDA_TRY(cudaMemset(base + kWorkBytes, 0, sizeof(int)));
+    kfbi::set_error("kfbi_box_solve_static: a staged line copy of an earlier call did not "
+                    "complete (bounded wait expired); its output is wrong");
+    return KFBI_ERR_TIMEOUT;
+  }
+  return KFBI_OK;
 }

@@ -50,7 +50,6 @@ static void free_handle(kfbi_ctx_s* hd) {
   if (c.basis) {
     cudaFree(c.basis); cudaFree(c.hess); cudaFree(c.givens); cudaFree(c.gvec);
     cudaFree(c.hcol); cudaFree(c.yvec); cudaFree(c.gm_part); cudaFree(c.gm_counter);
-    if (c.arn_part) cudaFree(c.arn_part);
   }
   if (c.h_pinned) cudaFreeHost(c.h_pinned);
   kfbi::free_tc(c);

@@ -800,12 +800,8 @@ kfbi_status launch_rows(Ctx& c, const T* in, T* out, const cx<T>* tw, T scale, i
   static_assert(rows_smem<T, N, EPT>(lpc) <= 227 * 1024, "row pass exceeds shared memory");
   const int threads = lpc * P.tpl;
   const size_t smem = rows_smem<T, N, EPT>(lpc);
-  static std::atomic<bool> attr{false};   // set once per process (any host thread)
-  if (!attr) {
-    KFBI_CUDA_TRY(cudaFuncSetAttribute(rows_kernel<T, N, EPT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  static PerDeviceOnce attr;   // the limit is set once per device
+  KFBI_TRY(set_smem_limit_once(attr, (const void*)rows_kernel<T, N, EPT>, smem));
   int per_sm = 0;
   KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_kernel<T, N, EPT>,
                                                               threads, smem));
@@ -829,12 +825,8 @@ kfbi_status launch_cols(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   static_assert(cols_smem<T, N, EPT, MAXT>() <= 227 * 1024, "column pass exceeds shared memory");
   const int threads = L * P.tpl;
   const size_t smem = cols_smem<T, N, EPT, MAXT>();
-  static std::atomic<bool> attr{false};   // set once per process (any host thread)
-  if (!attr) {
-    KFBI_CUDA_TRY(cudaFuncSetAttribute(cols_kernel<T, N, EPT, MAXT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  static PerDeviceOnce attr;   // the limit is set once per device
+  KFBI_TRY(set_smem_limit_once(attr, (const void*)cols_kernel<T, N, EPT, MAXT>, smem));
   int per_sm = 0;
   KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &per_sm, cols_kernel<T, N, EPT, MAXT>, threads, smem));
@@ -860,12 +852,8 @@ kfbi_status launch_ylines(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   T* X = reinterpret_cast<T*>(c.XT);
   const int threads = lpc * P.tpl;
   const size_t smem = yline_smem<T, N, EPT>();
-  static std::atomic<bool> attr{false};   // set once per process (any host thread)
-  if (!attr) {
-    KFBI_CUDA_TRY(cudaFuncSetAttribute(yline_kernel<T, N, EPT, 2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  static PerDeviceOnce attr;   // the limit is set once per device
+  KFBI_TRY(set_smem_limit_once(attr, (const void*)yline_kernel<T, N, EPT, 2>, smem));
   int per_sm = 0;
   KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yline_kernel<T, N, EPT, 2>,
                                                               threads, smem));
@@ -897,12 +885,8 @@ kfbi_status launch_ylines_only(Ctx& c, T* X, const cx<T>* tw, const T* lam) {
   KFBI_TRY((stage_table<T, N, EPT>(c, tw, &stw)));
   const int threads = lpc * P.tpl;
   const size_t smem = yline_smem<T, N, EPT>();
-  static std::atomic<bool> attr{false};
-  if (!attr) {
-    KFBI_CUDA_TRY(cudaFuncSetAttribute(yline_kernel<T, N, EPT, 2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  static PerDeviceOnce attr;   // the limit is set once per device
+  KFBI_TRY(set_smem_limit_once(attr, (const void*)yline_kernel<T, N, EPT, 2>, smem));
   int per_sm = 0;
   KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yline_kernel<T, N, EPT, 2>,
                                                               threads, smem));

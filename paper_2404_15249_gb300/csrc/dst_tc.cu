@@ -400,14 +400,9 @@ template <int BN>
 kfbi_status gemm_n(Ctx& c, const float* ahi, const float* alo, float* out, float* out_lo,
                    int mode) {
   static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
-  static std::atomic<bool> attr{false};
-  if (!attr) {
-    KFBI_CUDA_TRY(cudaFuncSetAttribute(dst_gemm_kernel<BN, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<BN>::SMEM));
-    KFBI_CUDA_TRY(cudaFuncSetAttribute(dst_gemm_kernel<BN, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<BN>::SMEM));
-    attr = true;
-  }
+  static PerDeviceOnce attr_tma, attr_cp;   // the limits are set once per device
+  KFBI_TRY(set_smem_limit_once(attr_tma, (const void*)dst_gemm_kernel<BN, true>, Tile<BN>::SMEM));
+  KFBI_TRY(set_smem_limit_once(attr_cp, (const void*)dst_gemm_kernel<BN, false>, Tile<BN>::SMEM));
   const int N = c.N, M = c.dim == 3 ? N * N : N;
   const double s1 = 2.0 / N;
   const float scale = (float)(c.dim == 3 ? s1 * s1 * s1 : s1 * s1);

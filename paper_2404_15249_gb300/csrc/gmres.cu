@@ -14,8 +14,6 @@
 #include <vector>
 #include <cstdlib>
 
-#include <cooperative_groups.h>
-
 #include "kfbi_internal.cuh"
 
 namespace kfbi {
@@ -204,138 +202,6 @@ __global__ void finish_kernel(int j, int m, int M, const double* __restrict__ w,
   for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hc[i] = col[i];
 }
 
-// One whole Arnoldi step (CGS2 orthogonalisation of w against V_0..V_j, normalisation into
-// V_{j+1}, and the Givens update of finish_kernel) in one cooperative launch with three
-// grid-wide barriers instead of five launches.  Block g owns the element tiles
-// [t ARN_T, (t + 1) ARN_T) for t = g, g + G, ...; a dot product <V_b, w> is formed per block
-// by the warp owning b (warp-shuffle sums), the per-block partials are added in block order
-// by every block after the barrier (deterministic), and each phase writes its own partial
-// buffer so that no block overwrites partials another is still reading.
-constexpr int ARN_T = 128;
-
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;   // valid in lane 0
-}
-
-__global__ void __launch_bounds__(ARN_T)
-    arnoldi_kernel(int j, int m, int M, double* __restrict__ w, double* __restrict__ V, int ld,
-                   double* __restrict__ part, double* hess, double* giv, double* gvec,
-                   double* scal) {
-  namespace cgr = cooperative_groups;
-  cgr::grid_group grid = cgr::this_grid();
-  extern __shared__ double dyn[];
-  double* h1 = dyn;                  // m + 1
-  double* h2 = dyn + (m + 1);        // m + 1
-  double* gsh = dyn + 2 * (m + 1);   // 2m: rotations
-  __shared__ double red[ARN_T / 32];
-  const int nb = j + 1, G = gridDim.x, pld = m + 1;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int NW = ARN_T / 32;
-  double* p1 = part;
-  double* p2 = part + (size_t)G * pld;
-  double* p3 = part + 2 * (size_t)G * pld;
-  auto dots = [&](double* out) {    // out[g * pld + b] = this block's part of <V_b, w>
-    for (int b = warp; b < nb; b += NW) {
-      const double* v = V + (size_t)b * ld;
-      double acc = 0.0;
-      for (int t = blockIdx.x; t * ARN_T < M; t += G)
-#pragma unroll
-        for (int e = 0; e < ARN_T / 32; ++e) {
-          const int x = t * ARN_T + lane + 32 * e;
-          if (x < M) acc += v[x] * w[x];
-        }
-      acc = warp_sum(acc);
-      if (lane == 0) out[(size_t)blockIdx.x * pld + b] = acc;
-    }
-  };
-  auto reduce = [&](const double* in, double* h) {   // h[b] = sum over blocks, block order
-    for (int b = threadIdx.x; b < nb; b += ARN_T) {
-      double u = 0.0;
-      for (int g = 0; g < G; ++g) u += __ldcg(in + (size_t)g * pld + b);
-      h[b] = u;
-    }
-    __syncthreads();
-  };
-  auto update = [&](const double* h, bool norm) {    // w -= V h on own elements
-    double ss = 0.0;
-    for (int t = blockIdx.x; t * ARN_T < M; t += G) {
-      const int x = t * ARN_T + threadIdx.x;
-      if (x < M) {
-        double s[4] = {0.0, 0.0, 0.0, 0.0};
-        int b = 0;
-        for (; b + 3 < nb; b += 4) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) s[u] += h[b + u] * V[(size_t)(b + u) * ld + x];
-        }
-        for (; b < nb; ++b) s[0] += h[b] * V[(size_t)b * ld + x];
-        const double wn = w[x] - ((s[0] + s[1]) + (s[2] + s[3]));
-        w[x] = wn;
-        ss += wn * wn;
-      }
-    }
-    __syncthreads();   // the block's updated elements, before its warps read them
-    return ss;
-  };
-
-  dots(p1);
-  grid.sync();
-  reduce(p1, h1);
-  update(h1, false);
-  dots(p2);
-  grid.sync();
-  reduce(p2, h2);
-  double ss = warp_sum(update(h2, true));
-  if (lane == 0) red[warp] = ss;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int q = 0; q < NW; ++q) t += red[q];
-    p3[blockIdx.x] = t;
-  }
-  grid.sync();
-  double nsq = 0.0;
-  for (int g = 0; g < G; ++g) nsq += __ldcg(p3 + g);
-  const double nrm = sqrt(nsq);
-  const double beta = scal[2];
-  const bool breakdown = !(nrm > 1e-14 * beta);
-  if (!breakdown)
-    for (int t = blockIdx.x; t * ARN_T < M; t += G) {
-      const int x = t * ARN_T + threadIdx.x;
-      if (x < M) V[(size_t)(j + 1) * ld + x] = w[x] / nrm;
-    }
-  if (blockIdx.x != 0) return;
-  // Givens update of the new Hessenberg column (as finish_kernel)
-  double* col = h1;                  // h1 + h2 in place
-  for (int i = threadIdx.x; i <= j; i += ARN_T) col[i] = h1[i] + h2[i];
-  for (int i = threadIdx.x; i < 2 * j; i += ARN_T) gsh[i] = giv[i];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    col[j + 1] = nrm;
-    for (int i = 0; i < j; ++i) {
-      const double cs = gsh[2 * i], sn = gsh[2 * i + 1];
-      const double t = cs * col[i] + sn * col[i + 1];
-      col[i + 1] = -sn * col[i] + cs * col[i + 1];
-      col[i] = t;
-    }
-    const double den = hypot(col[j], col[j + 1]);
-    const double cs = col[j] / den, sn = col[j + 1] / den;
-    giv[2 * j] = cs;
-    giv[2 * j + 1] = sn;
-    col[j] = den;
-    col[j + 1] = 0.0;
-    const double gj = gvec[j];
-    gvec[j + 1] = -sn * gj;
-    gvec[j] = cs * gj;
-    scal[0] = fabs(sn * gj);
-    scal[1] = breakdown ? 1.0 : 0.0;
-    scal[3] = (isfinite(nrm) && isfinite(den)) ? 0.0 : 1.0;
-  }
-  __syncthreads();
-  double* hc = hess + (size_t)j * (m + 1);
-  for (int i = threadIdx.x; i <= j + 1; i += ARN_T) hc[i] = col[i];
-}
-
 // back substitution R y = g (k x k, R upper triangular in hess), R and g staged in
 // shared memory when they fit (dynamic: k (k + 1) doubles), else read from global memory
 __global__ void lsq_kernel(int k, int m, const double* hess, const double* gvec, double* y,
@@ -377,8 +243,6 @@ kfbi_status alloc_gmres(Ctx& c, int m) {
   if (c.basis) {
     cudaFree(c.basis); cudaFree(c.hess); cudaFree(c.givens); cudaFree(c.gvec);
     cudaFree(c.hcol); cudaFree(c.yvec); cudaFree(c.gm_part); cudaFree(c.gm_counter);
-    if (c.arn_part) cudaFree(c.arn_part);
-    c.arn_part = nullptr;
   }
   const int M = c.M;
   KFBI_CUDA_TRY(cudaMalloc((void**)&c.basis, sizeof(double) * (size_t)(m + 1) * M));
@@ -391,27 +255,6 @@ kfbi_status alloc_gmres(Ctx& c, int m) {
   KFBI_CUDA_TRY(cudaMalloc((void**)&c.gm_part, sizeof(double) * nparts));
   KFBI_CUDA_TRY(cudaMalloc((void**)&c.gm_counter, sizeof(unsigned)));
   KFBI_CUDA_TRY(cudaMemset(c.gm_counter, 0, sizeof(unsigned)));
-  // fused Arnoldi step (opt-in, KFBI_FUSED_ARNOLDI=1): one block per element tile up to one
-  // per SM, if the device runs cooperative launches of that size.  Measured on GB300 it is
-  // not faster: at M = 8192 its three grid barriers cost more than the four launches they
-  // replace (3.6 vs 2.3 ms of Krylov work per solve), and a batch of 256 small problems on
-  // 8 streams ran 5% slower with it.
-  c.arn_grid = 0;
-  const char* fe = std::getenv("KFBI_FUSED_ARNOLDI");
-  const bool want = fe && fe[0] == '1';
-  int dev = 0, coop = 0, sms = 0, per_sm = 0;
-  const size_t arn_smem = sizeof(double) * (4 * (size_t)m + 2);
-  if (want && cudaGetDevice(&dev) == cudaSuccess &&
-      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arnoldi_kernel, ARN_T, arn_smem) ==
-          cudaSuccess && per_sm >= 1) {
-    const int tiles = (M + ARN_T - 1) / ARN_T;
-    const int g = std::min(tiles, sms);
-    KFBI_CUDA_TRY(cudaMalloc((void**)&c.arn_part, sizeof(double) * 3 * (size_t)g * (m + 1)));
-    c.arn_grid = g;
-  }
-  cudaGetLastError();
   for (int i = 0; i < 2; ++i)
     if (!c.gm_ev[i]) KFBI_CUDA_TRY(cudaEventCreateWithFlags(&c.gm_ev[i], cudaEventDisableTiming));
   c.gm_m = m;
@@ -502,17 +345,7 @@ static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const do
       KFBI_TRY(apply_K(c, prec, c.basis + (size_t)j * M, w, cnt));
       ++cnt.iters;
       const int pk = prof_begin(c, ST_KRYLOV);
-      if (c.arn_grid > 0) {
-        // the whole step in one cooperative launch
-        int jj = j, mm = m, MM = M, ld = M;
-        double* basis = c.basis;
-        double* part = c.arn_part;
-        void* args[] = {&jj, &mm, &MM, &w, &basis, &ld, &part, &c.hess, &c.givens, &c.gvec,
-                        &c.scal};
-        KFBI_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)arnoldi_kernel, dim3(c.arn_grid),
-                                                  dim3(ARN_T), args,
-                                                  sizeof(double) * (4 * (size_t)m + 2), st));
-      } else {
+      {
         prof_count(c, ST_KRYLOV, 4);
         const size_t hsm = sizeof(double) * (j + 1);
         const dim3 dg(dot_blocks(M), j + 1);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <vector>
@@ -28,6 +29,27 @@ const char* last_error_message();          // this thread's last set_error text
     kfbi_status s_ = (expr);           \
     if (s_ != KFBI_OK) return s_;      \
   } while (0)
+
+// A kernel's dynamic shared-memory limit is an attribute of the kernel in one device's
+// context: it is set once per device ordinal (from whichever host thread launches first;
+// two threads racing both set the same value, which is harmless).
+constexpr int kMaxDeviceOrdinals = 64;
+struct PerDeviceOnce {
+  std::atomic<bool> done[kMaxDeviceOrdinals] = {};
+};
+inline kfbi_status set_smem_limit_once(PerDeviceOnce& once, const void* func, size_t bytes) {
+  int dev = 0;
+  KFBI_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDeviceOrdinals) {
+    set_error("device ordinal %d above %d", dev, kMaxDeviceOrdinals - 1);
+    return KFBI_ERR_ARG;
+  }
+  if (!once.done[dev].load(std::memory_order_acquire)) {
+    KFBI_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    once.done[dev].store(true, std::memory_order_release);
+  }
+  return KFBI_OK;
+}
 
 // ------------------------------------------------------------------ FFT plan
 // Complex FFT of length N = 2^a or 3*2^a in shared memory.  Every thread of a line
@@ -170,8 +192,6 @@ struct Ctx {
   cudaEvent_t gm_ev[2] = {nullptr, nullptr};   // Arnoldi-step flag copies done
   double* gm_part = nullptr;       // per-block partial dot products
   unsigned* gm_counter = nullptr;  // blocks done in the current multi-dot
-  double* arn_part = nullptr;      // fused Arnoldi step: 3 x arn_grid x (m + 1) partial sums
-  int arn_grid = 0;                // its cooperative grid (0: the fused step is not used)
   int* err_flag = nullptr;     // device error flag
 
   int64_t bytes = 0;

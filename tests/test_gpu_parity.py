@@ -240,27 +240,6 @@ def test_largest_grid_box_solve_manufactured(N):
     ctx.close()
 
 
-def test_fused_arnoldi_step_matches_the_five_kernel_step():
-    """The opt-in cooperative Arnoldi step (one launch with grid barriers) gives the same
-    solve as the five-kernel step to rounding."""
-    import os
-    prob = CASES["flower128_poisson"]()
-    fg, fc, gc = prob.f_grid(), prob.f_ctrl(), prob.g_ctrl()
-    out = {}
-    for flag in ("0", "1"):
-        os.environ["KFBI_FUSED_ARNOLDI"] = flag
-        try:
-            ctx, geom = make(prob, tol=1e-12)
-            u, phi, info = ctx.solve_bvp(fg, fc, gc)
-            out[flag] = (u.cpu().numpy(), phi.cpu().numpy(), info)
-            ctx.close()
-        finally:
-            del os.environ["KFBI_FUSED_ARNOLDI"]
-    assert out["0"][2]["iterations"] == out["1"][2]["iterations"]
-    assert rel(out["1"][1], out["0"][1]) < 1e-12
-    assert rel(out["1"][0], out["0"][0]) < 1e-12
-
-
 @pytest.mark.parametrize("kappa", [0.0, 10.0])
 def test_fp32_box_solve_with_and_without_the_tridiagonal_pass(kappa):
     """FP32 box solves with the well-conditioned x-modes solved along y by tridiagonal
