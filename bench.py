@@ -50,8 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--n3d", type=int, default=256,
-                    help="grid size of the 3-D companion measurement (0: skip)")
+    ap.add_argument("--n3d", default="128,256,512",
+                    help="grid sizes of the 3-D companion measurement, comma separated (0: skip)")
     ap.add_argument("--ntc", type=int, default=1024,
                     help="grid size of the tensor-core box-solve measurement (0: skip)")
     ap.add_argument("--batch", type=int, default=256,
@@ -196,6 +196,56 @@ def roofline(stage_ms, N, variants, tri_k0):
             "algorithmic_bytes": nbytes, "launches": launches, "avg_launch_us": avg_s * 1e6}
 
 
+def fp64_roofline(stage_ms, N, alu):
+    """Dominant FP64 transform stage of the plain FP64 solve against the measured FP64 FMA
+    throughput: 5 N log2 N flops per complex FFT of length N (the conventional count), one
+    FFT per line for the row pass and two for the y-transform pair, N lines per launch."""
+    cand = {k: v for k, v in stage_ms.items()
+            if k in ("dst_rows_f64", "dst_cols_f64") and v[1] > 0 and v[0] > 0}
+    if not cand or not alu:
+        return None
+    name = max(cand, key=lambda k: cand[k][0])
+    ms, launches = cand[name]
+    avg_s = ms / launches / 1e3
+    ffts = 1 if "rows" in name else 2
+    flops = ffts * N * 5.0 * N * math.log2(N)
+    ach = flops / avg_s / 1e12
+    return {"bound": "alu", "kernel": "rows_kernel<double>" if "rows" in name else "yline_kernel<double>",
+            "achieved": ach, "peak": alu["fp64_tflops"], "unit": "TFLOP/s",
+            "frac": ach / alu["fp64_tflops"], "peak_source": "measured (kfbi_measure_fma_peak, FP64)",
+            "launches": launches, "avg_launch_us": avg_s * 1e6,
+            "stage_share": ms / sum(v[0] for v in stage_ms.values() if v[1])}
+
+
+# stages whose kernels carry the box solve's sine transforms and y-solves (Alg. 4)
+DST_STAGES = ("dst_rows_f32", "dst_cols_f32", "dst_tri_f32", "sparse_x_f32", "transpose")
+
+
+def dst_stage_roofline(stage_ms, N, solves):
+    """The box-solve (DST) stage of the mixed solve as a whole against the HBM roofline:
+    algorithmic bytes 24 B per interior unknown for a box solve of a dense right-hand side
+    (three passes, each reading and writing the FP32 grid once) and 16 B for the sparse
+    right-hand side of a plain double-layer apply (its first x-transform reads only the
+    irregular nodes), over the summed device time of the stage's kernels.  A plain apply
+    runs one sparse x-transform and one row pass, a dense box solve two row passes, so
+    the counts follow from the launches of the two kernels."""
+    ms = sum(stage_ms[k][0] for k in DST_STAGES if k in stage_ms)
+    if ms <= 0 or solves <= 0:
+        return None
+    sparse = stage_ms.get("sparse_x_f32", (0.0, 0))[1] / solves
+    rows = stage_ms.get("dst_rows_f32", (0.0, 0))[1] / solves
+    dense = (rows - sparse) / 2.0
+    unknowns = float(N - 1) ** 2
+    nbytes = (24.0 * dense + 16.0 * sparse) * unknowns
+    peak, src = peaks()
+    ach = nbytes / (ms / solves / 1e3) / 1e9
+    return {"bound": "hbm", "stage": "box solves of one mixed BVP solve (" + ", ".join(
+                k for k in DST_STAGES if k in stage_ms and stage_ms[k][1]) + ")",
+            "dense_box_solves": dense, "sparse_box_solves": sparse,
+            "algorithmic_bytes": nbytes, "ms": ms / solves, "achieved": ach, "peak": peak,
+            "unit": "GB/s", "frac": ach / peak, "peak_source": src}
+
+
 # ------------------------------------------------------------------------ arms
 def max_over_ranks(x, dist, device):
     """The largest x over all ranks (x itself on one rank): the job's step time is that of
@@ -310,11 +360,12 @@ def run_kfbi(a):
     # ---------------- mixed-precision solve (the timed path)
     for _ in range(a.warmup):
         ctx.solve_bvp(fg, fc, gc, u_out=u, dens_out=phi)
+    st = torch.cuda.current_stream()
+    ctx.profile(True)                 # clears the launch counters ...
+    ctx.profile(False)                # ... which keep counting without per-launch events
     clocks = Clocks(local)
     clocks.start()
     barrier()
-    ctx.profile(True)
-    st = torch.cuda.current_stream()
     step_ms, infos = [], []
     for _ in range(a.steps):
         flush.fill_(1.0)
@@ -325,14 +376,29 @@ def run_kfbi(a):
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         infos.append(info)
-    stages = ctx.profile_read()
-    ctx.profile(False)
+    counted = ctx.profile_read()      # launches of the timed steps (no device times)
     barrier()
     clk = clocks.stop()
     ms = max_over_ranks(statistics.mean(step_ms), dist, dev)
     applies = infos[-1]["applies_fp64"] + infos[-1]["applies_low"]
     err_mixed = err_inf(u)
     value = whole_job_rate(world, (N + 1) ** 2, applies, ms)
+
+    # ---------------- the same solves again with CUDA events around every launch (on the
+    # library's stream): per-stage device time and the dominant kernel's launch duration
+    nprof = min(a.steps, 5)
+    ctx.profile(True)
+    for _ in range(nprof):
+        flush.fill_(1.0)
+        ctx.solve_bvp(fg, fc, gc, u_out=u, dens_out=phi)
+    stages = ctx.profile_read()
+    ctx.profile(False)
+
+    # measured FMA throughput of this GPU (FP64 and FP32), the denominators of the ALU
+    # rooflines of the FP64 transforms and of the FP32 transforms' arithmetic
+    alu_peaks = {"fp64_tflops": K.measure_fma_peak(True), "fp32_tflops": K.measure_fma_peak(False),
+                 "how": "kfbi_measure_fma_peak: 8 independent FMA chains per thread, every SM "
+                        "full, best of 3 launches (2 flops per FMA)"}
 
     # ---------------- FP64 path on the same inputs (same error check, speedup)
     fp64 = {}
@@ -348,9 +414,16 @@ def run_kfbi(a):
             e1.record(st)
             e1.synchronize()
             t64.append(e0.elapsed_time(e1))
+        ctx.profile(True)
+        flush.fill_(1.0)
+        ctx.solve_bvp(fg, fc, gc, u_out=u, dens_out=phi)
+        st64 = ctx.profile_read()
+        ctx.profile(False)
         fp64 = {"fp64_solve_ms": statistics.mean(t64), "err_inf_fp64": err_inf(u),
                 "fp64_iterations": i64["iterations"],
-                "speedup_vs_fp64": statistics.mean(t64) / ms}
+                "speedup_vs_fp64": statistics.mean(t64) / ms,
+                "fp64_stage_ms": {k: round(v[0], 4) for k, v in st64.items() if v[1]},
+                "fp64_roofline": fp64_roofline(st64, N, alu_peaks)}
         ctx.set_solver(K.KFBI_MIXED_FP32, 50, 20, 1e-10, 1e-5)
 
     # ---------------- end to end through the API with host buffers
@@ -393,8 +466,9 @@ def run_kfbi(a):
                          f"({dt:.1f} s, numpy on the host cores); unit as value"}
 
     companion = None
-    if rank == 0 and a.n3d > 0:
-        companion = run_3d_companion(a, dev, flush)
+    n3d = [int(x) for x in str(a.n3d).split(",") if int(x) > 0]
+    if rank == 0 and n3d:
+        companion = [run_3d_companion(n, dev, flush) for n in n3d]
     batch = None
     if rank == 0 and a.batch > 0:
         batch = run_batch_companion(a, dev)
@@ -402,7 +476,7 @@ def run_kfbi(a):
     if rank == 0 and a.ntc > 0:
         tc = run_tc_companion(a, dev, flush, ctx, N) if N % 128 == 0 and N <= 8192 else None
 
-    launches = int(sum(v[1] for v in stages.values()))
+    launches = int(sum(v[1] for v in counted.values()))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -411,6 +485,8 @@ def run_kfbi(a):
                        "l2": "flushed between timed steps (256 MiB write)",
                        "replicas": world},
             "roofline": roofline(stages, N, ctx.info()["dst_variant"], ctx.info()["tri_first_mode"]),
+            "dst_stage_roofline": dst_stage_roofline(stages, N, nprof),
+            "alu_peaks": alu_peaks,
             "dst_variant": ctx.info()["dst_variant"],
             "cpu_baseline": cpu,
             "clocks": clk,
@@ -422,8 +498,11 @@ def run_kfbi(a):
             "outer_iterations": infos[-1]["outer_iterations"],
             "rel_residual": infos[-1]["rel_residual"],
             "err_inf_mixed": err_mixed,
-            "stage_ms": {k: round(v[0] / a.steps, 4) for k, v in stages.items() if v[1]},
-            "stage_launches": {k: int(v[1]) for k, v in stages.items() if v[1]},
+            "stage_ms": {k: round(v[0] / nprof, 4) for k, v in stages.items() if v[1]},
+            "stage_launches": {k: int(v[1]) for k, v in counted.items() if v[1]},
+            "stage_note": (f"stage_ms: per solve, from {nprof} further solves with CUDA events "
+                           "around every launch (the headline steps run without them); "
+                           "stage_launches: over the timed steps"),
             **fp64,
             "companion_3d": companion,
             "companion_batch": batch,
@@ -436,7 +515,7 @@ def run_kfbi(a):
     return 0
 
 
-def run_3d_companion(a, dev, flush):
+def run_3d_companion(N, dev, flush):
     """The 3-D configuration (ellipsoid 0.7 x 0.5 x 0.4, u = sin x sin y sin z, kappa = 0)
     at one grid size: setup, mixed and FP64 Dirichlet solves timed with CUDA events
     (L2 flushed before each), errors against the exact solution.  Reported beside the
@@ -446,7 +525,6 @@ def run_3d_companion(a, dev, flush):
     import kfbi_workloads.surfaces3d as S3
     import paper_2404_15249_gb300 as K
 
-    N = a.n3d
     prob = S3.config_poisson3d(N, "ellipsoid")
     I = prob.iface
     fg = torch.as_tensor(prob.f_grid(), device=dev)
@@ -599,19 +677,23 @@ def run_tc_companion(a, dev, flush, main_ctx, main_N):
 
 def run_batch_companion(a, dev):
     """The batched configuration (random star curves, N from {64, ..., 1024}, kappa ~ U(0,5),
-    4 right-hand sides per problem, mixed precision) through kfbi_batch_solve: setup of all
-    contexts, then the whole batch timed with CUDA events; errors against the exact
-    solutions.  Reported beside the 2-D line."""
+    4 right-hand sides per problem, M = 2N, GMRES(50) to 1e-10) through kfbi_batch_solve:
+    setup of all contexts; the whole batch in mixed precision and then in plain FP64,
+    each timed with CUDA events after a warm-up batch; errors against the exact solutions;
+    and one more mixed batch with CUDA events around every launch of every context, whose
+    summed device time against the batch's wall time tells how busy the GPU was.
+    Reported beside the 2-D line."""
     import numpy as np
     import torch
     import kfbi_workloads as W
     import paper_2404_15249_gb300 as K
 
-    nrhs = 4
+    nrhs, m, restarts = 4, 50, 20
     cfg = W.config_batch(a.batch, nrhs)
     t0 = time.perf_counter()
     ctxs = [K.Kfbi2D(p.iface.pts, p.iface.normals, p.iface.curv, p.N, p.kappa,
-                     precision=K.KFBI_MIXED_FP32, gmres_m=100) for p, _ in cfg]
+                     precision=K.KFBI_MIXED_FP32, gmres_m=m, max_restarts=restarts, tol=1e-10)
+            for p, _ in cfg]
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     fg, fc, gc, ub, exact = [], [], [], [], []
@@ -623,35 +705,71 @@ def run_batch_companion(a, dev):
             gc.append(torch.as_tensor(q.g_ctrl(), device=dev))
             ub.append(torch.empty((p.N + 1, p.N + 1), dtype=torch.float64, device=dev))
             exact.append(q.u_grid())
-    K.batch_solve(ctxs, fg, fc, gc, ub, nrhs)          # warm-up
     st = torch.cuda.current_stream()
+    insides = [c.inside_mask().cpu().numpy().astype(bool) for c in ctxs]
+
+    def timed_batch():
+        K.batch_solve(ctxs, fg, fc, gc, ub, nrhs)          # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        infos = K.batch_solve(ctxs, fg, fc, gc, ub, nrhs)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        pts_applies, err = 0.0, 0.0
+        for k, (p, _) in enumerate(cfg):
+            for r in range(nrhs):
+                q = k * nrhs + r
+                i = infos[q]
+                pts_applies += (p.N + 1) ** 2 * (i["applies_fp64"] + i["applies_low"])
+                err = max(err, float(np.abs(ub[q].cpu().numpy() - exact[q])[insides[k]].max()))
+        bad = [(q // nrhs, q % nrhs, i["rel_residual"]) for q, i in enumerate(infos)
+               if not i["converged"]]
+        return ms, infos, pts_applies, err, bad
+
+    ms, infos, pts_applies, err, bad = timed_batch()
+    # device busy time: every launch of every context timed with events (one more batch)
+    for c in ctxs:
+        c.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
-    infos = K.batch_solve(ctxs, fg, fc, gc, ub, nrhs)
+    K.batch_solve(ctxs, fg, fc, gc, ub, nrhs)
     e1.record(st)
     e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    pts_applies = 0.0
-    err = 0.0
-    for k, (p, _) in enumerate(cfg):
-        inside = ctxs[k].inside_mask().cpu().numpy().astype(bool)
-        for r in range(nrhs):
-            q = k * nrhs + r
-            i = infos[q]
-            pts_applies += (p.N + 1) ** 2 * (i["applies_fp64"] + i["applies_low"])
-            err = max(err, float(np.abs(ub[q].cpu().numpy() - exact[q])[inside].max()))
+    wall_prof = e0.elapsed_time(e1)
+    busy = 0.0
+    launches = 0
+    for c in ctxs:
+        t = c.profile_read()
+        busy += sum(v[0] for v in t.values())
+        launches += sum(v[1] for v in t.values())
+        c.profile(False)
+    # the same batch in plain FP64
+    for c in ctxs:
+        c.set_solver(K.KFBI_FP64, m, restarts, 1e-10, 1e-5)
+    ms64, infos64, _, err64, bad64 = timed_batch()
     for c in ctxs:
         c.close()
     return {"workload": f"batched 2-D Poisson/Helmholtz: {a.batch} random star curves, "
                         f"N from {{64..1024}}, M = 2N, kappa ~ U(0,5), {nrhs} right-hand sides "
-                        f"each, mixed precision, GMRES(100) to 1e-10 (with a restart of 50 a "
-                        f"few of these geometries stagnate near 1e-9)",
+                        f"each, GMRES({m}) with {restarts} restarts to 1e-10; mixed precision "
+                        f"(timed) and plain FP64 (timed) on the same inputs",
             "problems": a.batch, "rhs": nrhs, "setup_s": setup_s, "batch_ms": ms,
             "solves_per_s": a.batch * nrhs / (ms / 1e3),
             "grid_pts_per_s_per_apply": pts_applies / (ms / 1e3),
-            "converged": sum(1 for i in infos if i["converged"]),
+            "converged": sum(1 for i in infos if i["converged"]), "not_converged": bad[:16],
             "max_rel_residual": max(i["rel_residual"] for i in infos),
-            "total_iterations": sum(i["iterations"] for i in infos), "max_err_inf": err}
+            "total_iterations": sum(i["iterations"] for i in infos), "max_err_inf": err,
+            "fp64_batch_ms": ms64, "speedup_vs_fp64": ms64 / ms,
+            "fp64_converged": sum(1 for i in infos64 if i["converged"]),
+            "fp64_not_converged": bad64[:16],
+            "fp64_total_iterations": sum(i["iterations"] for i in infos64),
+            "fp64_max_err_inf": err64,
+            "device_busy": {"kernel_ms_sum": busy, "wall_ms": wall_prof, "launches": launches,
+                            "note": "summed device time of every launch of every context "
+                                    "(events around each launch) over the wall time of the "
+                                    "same mixed batch; concurrent streams can make the sum "
+                                    "exceed the wall time"}}
 
 
 def main():

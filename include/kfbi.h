@@ -293,6 +293,14 @@ kfbi_status kfbi_destroy(kfbi_ctx ctx);
 const char* kfbi_status_string(kfbi_status s);
 const char* kfbi_last_error(void);
 
+/* ---------------------------------------------------------------- measurement helper
+   No counterpart in the paper: the measured arithmetic peak used as the denominator of
+   the ALU rooflines of the transform kernels.  Runs a kernel of independent fused
+   multiply-add chains on every SM (FP64 if fp64 != 0, else FP32), three timed launches
+   after a warm-up, and writes the best rate in TFLOP/s (2 flops per FMA) to *h_tflops.
+   Synchronising on `stream`; allocates nothing. */
+kfbi_status kfbi_measure_fma_peak(int fp64, double* h_tflops, void* stream);
+
 /* ---------------------------------------------------------------- batched problems
    Many independent problems (uneven N and M, 2-D or 3-D) solved together: a pool of up
    to 8 host workers, each driving its own CUDA stream, takes problems from a shared queue
@@ -307,14 +315,17 @@ typedef struct kfbi_batch_s* kfbi_batch;
 kfbi_status kfbi_batch_create(const kfbi_ctx* ctxs, int count, kfbi_batch* out);
 
 /* Solves count x nrhs BVPs: problem p, right-hand side r uses d_f_grid[p*nrhs + r],
-   d_f_ctrl[...], d_g_ctrl[...] and writes d_u_grid[p*nrhs + r] (device pointers, layout
-   as in kfbi_solve_bvp).  h_info: count*nrhs structs or NULL.  The work starts after
+   d_f_ctrl[...], d_g_ctrl[...] and writes d_u_grid[p*nrhs + r] and, when d_density_out
+   is not NULL, the boundary density into d_density_out[p*nrhs + r] (M_p values; device
+   pointers, layout as in kfbi_solve_bvp; the pointer table itself is a host array).
+   h_info: count*nrhs structs or NULL.  The work starts after
    everything already queued on `stream` and is finished when the call returns
    (synchronising).  The first failing solve stops the batch and its status is returned;
    KFBI_ERR_NOT_CONVERGED if some solve hit its iteration limit. */
 kfbi_status kfbi_batch_solve(kfbi_batch b, int nrhs, const double* const* d_f_grid,
                              const double* const* d_f_ctrl, const double* const* d_g_ctrl,
-                             double* const* d_u_grid, kfbi_solve_info* h_info, void* stream);
+                             double* const* d_u_grid, double* const* d_density_out,
+                             kfbi_solve_info* h_info, void* stream);
 
 kfbi_status kfbi_batch_destroy(kfbi_batch b);
 

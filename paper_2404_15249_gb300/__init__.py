@@ -97,8 +97,9 @@ _SIGS = {
     "kfbi_last_error": (ctypes.c_char_p, []),
     "kfbi_batch_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P)]),
     "kfbi_batch_solve": (I, [P, I, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
-                             ctypes.POINTER(P), ctypes.POINTER(SolveInfo), P]),
+                             ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(SolveInfo), P]),
     "kfbi_batch_destroy": (I, [P]),
+    "kfbi_measure_fma_peak": (I, [I, ctypes.POINTER(D), P]),
     "kfbi_profile": (I, [P, I]),
     "kfbi_profile_read": (I, [P, ctypes.POINTER(StageTimes)]),
     "kfbi_stage_name": (ctypes.c_char_p, [I]),
@@ -308,15 +309,24 @@ def box_solve_static(N, b_grid, kappa=0.0, lo=-1.0, hi=1.0, precision=KFBI_FP64,
     return out
 
 
+def measure_fma_peak(fp64: bool, stream=None) -> float:
+    """kfbi_measure_fma_peak: measured FMA throughput of the current device in TFLOP/s."""
+    out = ctypes.c_double()
+    _check(lib().kfbi_measure_fma_peak(1 if fp64 else 0, ctypes.byref(out), _stream_ptr(stream)),
+           "kfbi_measure_fma_peak")
+    return out.value
+
+
 def box_solve_static_check(stream=None):
     """kfbi_box_solve_static_check: synchronises the stream and raises KfbiError
     (ERR_TIMEOUT) if a bounded wait of an earlier static box solve gave up."""
     _check(lib().kfbi_box_solve_static_check(_stream_ptr(stream)), "kfbi_box_solve_static_check")
 
 
-def batch_solve(ctxs, f_grids, f_ctrls, g_ctrls, u_grids, nrhs, stream=None):
+def batch_solve(ctxs, f_grids, f_ctrls, g_ctrls, u_grids, nrhs, stream=None, dens_out=None):
     """kfbi_batch_create / kfbi_batch_solve / kfbi_batch_destroy over Kfbi2D contexts.
-    The per-(problem, rhs) lists hold device tensors, problem-major."""
+    The per-(problem, rhs) lists hold device tensors, problem-major; dens_out (optional)
+    is a list of the same length of float64 tensors of M_p values for the densities."""
     n = len(ctxs)
     arr = (ctypes.c_void_p * n)(*[c.handle.value for c in ctxs])
     b = ctypes.c_void_p()
@@ -325,7 +335,8 @@ def batch_solve(ctxs, f_grids, f_ctrls, g_ctrls, u_grids, nrhs, stream=None):
         mk = lambda ts: (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
         infos = (SolveInfo * (n * nrhs))()
         st = lib().kfbi_batch_solve(b, int(nrhs), mk(f_grids), mk(f_ctrls), mk(g_ctrls),
-                                    mk(u_grids), infos, _stream_ptr(stream))
+                                    mk(u_grids), None if dens_out is None else mk(dens_out),
+                                    infos, _stream_ptr(stream))
         if st not in (KFBI_OK, KFBI_ERR_NOT_CONVERGED):
             _check(st, "kfbi_batch_solve")
         return [i.as_dict() for i in infos]

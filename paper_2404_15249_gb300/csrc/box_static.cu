@@ -111,12 +111,14 @@ struct Launch {
     KFBI_CUDA_TRY(cudaGetLastError());
     const int row_blocks = (N + LPC - 1) / LPC;
     int* err = reinterpret_cast<int*>(base + kWorkBytes);
-    dst::rows_kernel<T, N, E><<<row_blocks, LPC * P.tpl, rows_smem, s>>>(work, work, stw, tw, T(1), N, err);
+    dst::rows_kernel<T, N, E><<<row_blocks, LPC * P.tpl, rows_smem, s>>>(work, work, stw, tw, T(1), N, err,
+                                                                      dst::kPollLimit);
     KFBI_CUDA_TRY(cudaGetLastError());
     dst::cols_kernel<T, N, E, 512><<<N / L, L * P.tpl, cols_smem, s>>>(
         work, stw, tw, lam, T(kappa2), T((2.0 / N) * (2.0 / N)));
     KFBI_CUDA_TRY(cudaGetLastError());
-    dst::rows_kernel<T, N, E><<<row_blocks, LPC * P.tpl, rows_smem, s>>>(work, work, stw, tw, T(1), N, err);
+    dst::rows_kernel<T, N, E><<<row_blocks, LPC * P.tpl, rows_smem, s>>>(work, work, stw, tw, T(1), N, err,
+                                                                      dst::kPollLimit);
     KFBI_CUDA_TRY(cudaGetLastError());
     store_kernel<T><<<gg, 256, 0, s>>>(N, work, v);
     KFBI_CUDA_TRY(cudaGetLastError());

@@ -130,6 +130,12 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
   c.stream = (cudaStream_t)stream;
   c.plan = plan;
   c.dim = dim;
+  // KFBI_TEST_POLL_LIMIT (tests of the failure path only): polls of a staged-copy wait
+  // before it records a timeout; 0 makes every such wait give up at once
+  if (const char* e = std::getenv("KFBI_TEST_POLL_LIMIT")) {
+    const long v = std::strtol(e, nullptr, 10);
+    if (v >= 0 && v < (1 << 20)) c.poll_limit = (int)v;
+  }
   if (opt->precision == KFBI_TF32X3 && !kfbi::tc_supported(c)) {
     kfbi::set_error("kfbi_setup: KFBI_TF32X3 needs N a multiple of 128, up to 8192 in 2-D and 512 in 3-D");
     free_handle(hd);
@@ -367,13 +373,14 @@ kfbi_status kfbi_batch_create(const kfbi_ctx* ctxs, int count, kfbi_batch* out) 
 
 kfbi_status kfbi_batch_solve(kfbi_batch b, int nrhs, const double* const* d_f_grid,
                              const double* const* d_f_ctrl, const double* const* d_g_ctrl,
-                             double* const* d_u_grid, kfbi_solve_info* h_info, void* stream) {
+                             double* const* d_u_grid, double* const* d_density_out,
+                             kfbi_solve_info* h_info, void* stream) {
   if (!b || nrhs < 1 || !d_f_grid || !d_f_ctrl || !d_g_ctrl || !d_u_grid) {
     kfbi::set_error("kfbi_batch_solve: bad argument");
     return KFBI_ERR_ARG;
   }
   return kfbi::batch_solve(b->ctxs.data(), (int)b->ctxs.size(), nrhs, d_f_grid, d_f_ctrl,
-                           d_g_ctrl, d_u_grid, h_info, (cudaStream_t)stream);
+                           d_g_ctrl, d_u_grid, d_density_out, h_info, (cudaStream_t)stream);
 }
 
 kfbi_status kfbi_batch_destroy(kfbi_batch b) {

@@ -38,7 +38,8 @@ kfbi_status box_solve3_n(Ctx& c, const T* rhs, T* A, const cx<T>* tw, const T* l
     const T scale = T((2.0 / N) * (2.0 / N) * (2.0 / N));
     const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
     yline_kernel<T, N, E, 3><<<blocks, threads, smem, c.stream>>>(A, stw, tw, lam, T(c.kappa2),
-                                                                  scale, n2, c.err_flag + 2);
+                                                                  scale, n2, c.err_flag + 2,
+                                                                  c.poll_limit);
     prof_end(c, pr);
     KFBI_CUDA_TRY(cudaGetLastError());
   }

@@ -303,8 +303,10 @@ __device__ __forceinline__ void dst_line(Raw&& load_pair, cx<T>* z0, cx<T>* z1, 
 // ---------------------------------------------------------------------------- line staging
 // The next block of contiguous lines is brought into shared memory by one bulk
 // asynchronous copy (completion counted on an mbarrier) while the current block is
-// transformed.  Waits are bounded: after 2^20 polls the kernel records a timeout in *err
-// (when given) and goes on, so a lost copy cannot hang the GPU.
+// transformed.  Waits are bounded: after `polls` polls (kPollLimit unless a test lowers it)
+// the kernel records a timeout in *err (when given), then waits up to kPollLimit more
+// polls for its own copy in flight (so no copy into shared memory outlives the wait) and
+// goes on, so a lost copy cannot hang the GPU.
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -327,9 +329,10 @@ __device__ __forceinline__ void stage_issue(void* dst, const void* src, uint32_t
       : "memory");
 }
 
-__device__ __forceinline__ void stage_wait(uint64_t* bar, uint32_t parity, int* err) {
-  const uint32_t a = smem_addr(bar);
-  for (int i = 0; i < (1 << 20); ++i) {
+constexpr int kPollLimit = 1 << 20;
+
+__device__ __forceinline__ bool stage_poll(uint32_t a, uint32_t parity, int polls) {
+  for (int i = 0; i < polls; ++i) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -337,9 +340,16 @@ __device__ __forceinline__ void stage_wait(uint64_t* bar, uint32_t parity, int* 
         : "=r"(done)
         : "r"(a), "r"(parity)
         : "memory");
-    if (done) return;
+    if (done) return true;
   }
+  return false;
+}
+
+__device__ __forceinline__ void stage_wait(uint64_t* bar, uint32_t parity, int* err, int polls) {
+  const uint32_t a = smem_addr(bar);
+  if (stage_poll(a, parity, polls)) return;
   if (err) atomicOr(err, 1);
+  stage_poll(a, parity, kPollLimit);           // drain the copy still in flight
 }
 
 // shared-memory bytes: FFT buffers of the row pass, and whether a staging line fits
@@ -367,7 +377,7 @@ template <typename T, int N, int EPT>
 __global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl : 256),
                                   ((cplan(N, EPT).tpl > 256 && EPT >= 16) ? 1 : 2))
     rows_kernel(const T* in, T* out, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
-                T scale, int nlines, int* err) {
+                T scale, int nlines, int* err, int polls) {
   constexpr CPlan P = cplan(N, EPT);
   constexpr bool STG = rows_staged<T, N, EPT>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -394,7 +404,7 @@ __global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl :
     const bool active = row < nlines;
     T* dst = out + (size_t)row * N;
     if constexpr (STG) {
-      stage_wait(&bar, (uint32_t)(it & 1), err);
+      stage_wait(&bar, (uint32_t)(it & 1), err, polls);
       const T* src = stage + (size_t)line * N;
       dst_line<T, N, EPT>(
           [&](int m, bool upper) {
@@ -667,7 +677,7 @@ template <typename T, int N, int EPT, int DIM>
 __global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl : 256),
                                   ((cplan(N, EPT).tpl > 256 && EPT >= 16) ? 1 : 2))
     yline_kernel(T* U, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
-                 const T* __restrict__ lam, T kappa2, T scale, int nlines, int* err) {
+                 const T* __restrict__ lam, T kappa2, T scale, int nlines, int* err, int polls) {
   constexpr CPlan P = cplan(N, EPT);
   constexpr size_t LB = col_line_bytes<T, N>();
   constexpr bool STG = yline_staged<T, N, EPT>();
@@ -711,7 +721,7 @@ __global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl :
       raw[l] = (zero_line || l == 0) ? T(0) : x * scale * recip(lk + lam[l]);
     };
     if constexpr (STG) {
-      stage_wait(&bar, (uint32_t)(it & 1), err);
+      stage_wait(&bar, (uint32_t)(it & 1), err, polls);
       const T* src = stage + (size_t)line * N;
       dst_line<T, N, EPT>(
           [&](int m, bool upper) {
@@ -810,7 +820,7 @@ kfbi_status launch_rows(Ctx& c, const T* in, T* out, const cx<T>* tw, T scale, i
   blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
   const int pr = prof_begin(c, sizeof(T) == 4 ? ST_ROWS32 : ST_ROWS64);
   rows_kernel<T, N, EPT><<<blocks, threads, smem, c.stream>>>(in, out, stw, tw, scale, nlines,
-                                                              c.err_flag + 2);
+                                                              c.err_flag + 2, c.poll_limit);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
@@ -867,7 +877,8 @@ kfbi_status launch_ylines(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   const int fblocks = blocks < (nfft + lpc - 1) / lpc ? blocks : (nfft + lpc - 1) / lpc;
   const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
   yline_kernel<T, N, EPT, 2><<<fblocks, threads, smem, c.stream>>>(X, stw, tw, lam, T(c.kappa2),
-                                                                   scale, nfft, c.err_flag + 2);
+                                                                   scale, nfft, c.err_flag + 2,
+                                                                   c.poll_limit);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   if constexpr (std::is_same<T, float>::value)
@@ -898,7 +909,8 @@ kfbi_status launch_ylines_only(Ctx& c, T* X, const cx<T>* tw, const T* lam) {
   const int fblocks = blocks < (nfft + lpc - 1) / lpc ? blocks : (nfft + lpc - 1) / lpc;
   const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
   yline_kernel<T, N, EPT, 2><<<fblocks, threads, smem, c.stream>>>(X, stw, tw, lam, T(c.kappa2),
-                                                                   scale, nfft, c.err_flag + 2);
+                                                                   scale, nfft, c.err_flag + 2,
+                                                                   c.poll_limit);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   if constexpr (std::is_same<T, float>::value)

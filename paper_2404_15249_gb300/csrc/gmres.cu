@@ -324,7 +324,10 @@ static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const do
   norm_kernel<<<1, 1024, 0, st>>>(r, M, c.scal, 2);
   KFBI_TRY(read_scal(c, 4));
   double beta = c.h_pinned[2];
-  if (!std::isfinite(beta)) return KFBI_ERR_NUMERIC;
+  if (!std::isfinite(beta)) {
+    set_error("GMRES: non-finite residual norm (NaN or Inf in the data or the iteration)");
+    return KFBI_ERR_NUMERIC;
+  }
   int cyc = 0;
   for (; cyc < max_cycles && beta > tol_abs; ++cyc) {
     prof_count(c, ST_KRYLOV);
@@ -367,7 +370,10 @@ static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const do
       if (pending >= 0) {
         const double* f = nullptr;
         KFBI_TRY(wait_flags(c, pending, &f));
-        if (f[3] != 0.0) return KFBI_ERR_NUMERIC;
+        if (f[3] != 0.0) {
+          set_error("GMRES: non-finite Arnoldi vector");
+          return KFBI_ERR_NUMERIC;
+        }
         est = f[0];
         if (est <= tol_abs || f[1] != 0.0) {
           const bool broke = f[1] != 0.0;
@@ -382,7 +388,10 @@ static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const do
     if (pending >= 0) {             // the last step's flags (cycle ended at m steps)
       const double* f = nullptr;
       KFBI_TRY(wait_flags(c, pending, &f));
-      if (f[3] != 0.0) return KFBI_ERR_NUMERIC;
+      if (f[3] != 0.0) {
+          set_error("GMRES: non-finite Arnoldi vector");
+          return KFBI_ERR_NUMERIC;
+        }
     }
     prof_count(c, ST_KRYLOV, 2);
     const size_t lsm = sizeof(double) * (size_t)k * (k + 1);
@@ -397,7 +406,10 @@ static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const do
     norm_kernel<<<1, 1024, 0, st>>>(r, M, c.scal, 2);
     KFBI_TRY(read_scal(c, 4));
     beta = c.h_pinned[2];
-    if (!std::isfinite(beta)) return KFBI_ERR_NUMERIC;
+    if (!std::isfinite(beta)) {
+      set_error("GMRES: non-finite residual norm (NaN or Inf in the data or the iteration)");
+      return KFBI_ERR_NUMERIC;
+    }
   }
   *res_out = beta;
   if (cycles_out) *cycles_out = cyc;
@@ -416,6 +428,8 @@ kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const 
   double* phi = c.vecs + 4 * M;
   double* d = c.vecs + 5 * M;
   Counters cnt;
+  // bounded waits that give up during this solve are reported by this solve
+  KFBI_CUDA_TRY(cudaMemsetAsync(c.err_flag + 2, 0, sizeof(int), st));
   // g_hat = g - (Y f)^+
   KFBI_TRY(interface_solve(c, acc, nullptr, f_grid, f_ctrl, nullptr, nullptr, d));
   ++cnt.applies64;
@@ -474,7 +488,8 @@ kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const 
 // ends (the batch starts after work already on it and is complete when the call returns).
 kfbi_status batch_solve(kfbi_ctx* ctxs, int count, int nrhs, const double* const* f_grid,
                         const double* const* f_ctrl, const double* const* g_ctrl,
-                        double* const* u_grid, kfbi_solve_info* info, cudaStream_t stream) {
+                        double* const* u_grid, double* const* dens_out, kfbi_solve_info* info,
+                        cudaStream_t stream) {
   int dev = 0;
   KFBI_CUDA_TRY(cudaGetDevice(&dev));
   std::vector<int> order(count);
@@ -515,7 +530,8 @@ kfbi_status batch_solve(kfbi_ctx* ctxs, int count, int nrhs, const double* const
       c.stream = st;
       for (int r = 0; r < nrhs; ++r) {
         const int q = p * nrhs + r;
-        const kfbi_status s = solve_bvp(c, f_grid[q], f_ctrl[q], g_ctrl[q], u_grid[q], nullptr,
+        const kfbi_status s = solve_bvp(c, f_grid[q], f_ctrl[q], g_ctrl[q], u_grid[q],
+                                        dens_out ? dens_out[q] : nullptr,
                                         info ? info + q : nullptr);
         if (s == KFBI_ERR_NOT_CONVERGED) {
           not_converged[w] = 1;

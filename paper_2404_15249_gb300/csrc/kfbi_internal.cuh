@@ -192,7 +192,9 @@ struct Ctx {
   cudaEvent_t gm_ev[2] = {nullptr, nullptr};   // Arnoldi-step flag copies done
   double* gm_part = nullptr;       // per-block partial dot products
   unsigned* gm_counter = nullptr;  // blocks done in the current multi-dot
-  int* err_flag = nullptr;     // device error flag
+  int* err_flag = nullptr;     // device error flags: [0] geometry, [2] bounded wait expired
+  int poll_limit = 1 << 20;    // polls of a staged-copy wait before it gives up (a test
+                               // lowers it through KFBI_TEST_POLL_LIMIT at setup)
 
   int64_t bytes = 0;
   int n_inside = 0;
@@ -266,7 +268,8 @@ kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const 
 kfbi_status alloc_gmres(Ctx& c, int m);
 kfbi_status batch_solve(kfbi_ctx* ctxs, int count, int nrhs, const double* const* f_grid,
                         const double* const* f_ctrl, const double* const* g_ctrl,
-                        double* const* u_grid, kfbi_solve_info* info, cudaStream_t stream);
+                        double* const* u_grid, double* const* dens_out, kfbi_solve_info* info,
+                        cudaStream_t stream);
 
 }  // namespace kfbi
 

@@ -46,3 +46,30 @@ def test_traffic_only_for_the_current_source():
     else:
         assert got is None
     assert bench.traffic_for("no_such_kernel", N) is None
+
+
+def test_dst_stage_roofline_counts_dense_and_sparse_box_solves():
+    # per solve: 42 plain applies (sparse right-hand side: one sparse x-transform and one
+    # row pass each) and 28 dense box solves (two row passes each), over 5 profiled solves
+    solves = 5
+    stages = {"dst_rows_f32": (28.0, solves * (42 + 2 * 28)), "sparse_x_f32": (11.0, solves * 42),
+              "dst_tri_f32": (11.5, solves * 70), "dst_cols_f32": (5.0, solves * 70),
+              "transpose": (10.7, solves * 98), "krylov": (11.0, solves * 300)}
+    r = bench.dst_stage_roofline(stages, N, solves)
+    assert r["sparse_box_solves"] == pytest.approx(42)
+    assert r["dense_box_solves"] == pytest.approx(28)
+    nbytes = (24 * 28 + 16 * 42) * (N - 1) ** 2
+    assert r["algorithmic_bytes"] == pytest.approx(nbytes)
+    ms = (28.0 + 11.0 + 11.5 + 5.0 + 10.7) / solves          # krylov is not a DST stage
+    assert r["ms"] == pytest.approx(ms)
+    assert r["frac"] == pytest.approx(nbytes / (ms / 1e3) / 1e9 / r["peak"])
+
+
+def test_fp64_roofline_uses_the_measured_peak():
+    stages = {"dst_rows_f64": (100.0, 200), "dst_cols_f64": (50.0, 100), "krylov": (10.0, 50)}
+    r = bench.fp64_roofline(stages, N, {"fp64_tflops": 1.2, "fp32_tflops": 70.0})
+    flops = N * 5.0 * N * 12
+    assert r["kernel"] == "rows_kernel<double>"
+    assert r["achieved"] == pytest.approx(flops / (100.0 / 200 / 1e3) / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1.2)
+    assert bench.fp64_roofline(stages, N, None) is None

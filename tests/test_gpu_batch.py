@@ -59,3 +59,63 @@ def test_batch_matches_one_at_a_time():
             q += 1
     for ctx, _, _ in probs:
         ctx.close()
+
+
+# Problems of the batched configuration (256 random stars, 4 right-hand sides each) that
+# the oracle comparison covers: the three whose grid lines graze the interface (a row or
+# column crossing pair dropped by the grazing rule: problems 23, 161, 175), the geometry
+# whose discrete K_D has a spurious small eigenvalue (problem 213, the largest error
+# against the exact solution), and the first problem of every grid size of the list.
+BATCH_SPECIAL = (23, 161, 175, 213)
+BATCH_PER_SIZE = (30, 4, 16, 6, 5, 13, 2, 38, 1)   # N = 64, 96, ..., 1024
+
+
+def test_batched_configuration_matches_the_fp64_oracle():
+    """kfbi_batch_solve (mixed precision, GMRES(50) to 1e-10) on a sample of the batched
+    configuration against the FP64 oracle's solve of each (problem, right-hand side): the
+    density within 1e-6 relative, and u closer to the oracle's u than the oracle's u is to
+    the exact solution (below the discretisation error)."""
+    import oracle as O
+    cfg = W.config_batch(256, 4)
+    picks = list(BATCH_SPECIAL) + list(BATCH_PER_SIZE)
+    dev = torch.device("cuda")
+    ctxs, fg, fc, gc, ub, dens, meta = [], [], [], [], [], [], []
+    for idx in picks:
+        prob, sols = cfg[idx]
+        ctxs.append(K.Kfbi2D(prob.iface.pts, prob.iface.normals, prob.iface.curv, prob.N,
+                             prob.kappa, precision=K.KFBI_MIXED_FP32, gmres_m=50,
+                             max_restarts=40, tol=1e-10))
+        for r, sol in enumerate(sols):
+            q = W.Problem(prob.iface, prob.N, prob.kappa, sol)
+            fg.append(torch.as_tensor(q.f_grid(), device=dev))
+            fc.append(torch.as_tensor(q.f_ctrl(), device=dev))
+            gc.append(torch.as_tensor(q.g_ctrl(), device=dev))
+            ub.append(torch.empty((prob.N + 1,) * 2, dtype=torch.float64, device=dev))
+            dens.append(torch.empty(prob.iface.M, dtype=torch.float64, device=dev))
+            meta.append((idx, r, q))
+    infos = K.batch_solve(ctxs, fg, fc, gc, ub, 4, dens_out=dens)
+    assert all(i["converged"] for i in infos), [m[:2] for m, i in zip(meta, infos) if not i["converged"]]
+    geoms = {}
+    worst = []
+    for k, ((idx, r, q), info) in enumerate(zip(meta, infos)):
+        if q.N > 384 and r > 0:
+            continue                       # larger grids: the first right-hand side only
+        if idx not in geoms:
+            geoms[idx] = O.Geometry2D(q.iface.pts, q.iface.normals, q.iface.curv, q.N, q.kappa)
+        g = geoms[idx]
+        u_o, phi_o, info_o = O.solve_bvp(g, q.f_grid(), q.f_ctrl(), q.g_ctrl(), tol=1e-10, m=50,
+                                         max_restarts=40)
+        assert info_o["converged"]
+        phi = dens[k].cpu().numpy()
+        d_rel = np.max(np.abs(phi - phi_o)) / np.max(np.abs(phi_o))
+        u = ub[k].cpu().numpy()
+        e_gpu = np.max(np.abs(u - u_o)[g.inside])
+        e_disc = np.max(np.abs(u_o - q.u_grid())[g.inside])
+        worst.append((d_rel, idx, r))
+        assert d_rel <= 1e-6, (idx, r, d_rel)
+        assert e_gpu < e_disc, (idx, r, e_gpu, e_disc)
+    print("batched configuration vs the FP64 oracle: worst density error "
+          f"{max(worst)[0]:.3e} (problem {max(worst)[1]}, rhs {max(worst)[2]}), "
+          f"{len(worst)} solves compared")
+    for c in ctxs:
+        c.close()
