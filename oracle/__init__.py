@@ -8,6 +8,15 @@ module is ``kfbi_workloads`` (seeded input generators, no method arithmetic).
 
 Every function follows the method as the paper states it (Sec. 2.1-2.2, Alg. 1-5),
 with the readings of unstated details written out in each docstring.
+
+Each function is pinned to facts outside itself (tests/test_oracle_pins.py,
+tests/test_oracle3d_pins.py): box solves to dense LU and exact eigen-pairs; the applies to
+the double layer of a constant (the indicator of Omega), to closed-form box double-layer
+potentials on a circle (also on circles grazing a grid row, which exercises the grazing
+rule of Geometry2D) and on a sphere (through the 3-D apply and its fitted-density split),
+to exactly reproduced piecewise quadratics, and to the spectrum of the continuous operator
+(the 3-D split); GMRES and Richardson to a dense solve of the assembled operator; the BVP
+to second-order convergence on manufactured solutions; error_norms to hand-computed values.
 """
 from .kfbi2d import (GeometryError, Geometry2D, jumps_cartesian, box_solve_dst,
                      box_solve_dense, correct_rhs, interpolate_plus, apply_interface,

@@ -73,3 +73,74 @@ def circle_double_layer_plus(k, R, c0, kappa, theta):
     Y = c0[1] + R * np.sin(theta)
     vin = free_space(k, R, kappa, np.full_like(theta, R), theta, np.ones_like(theta, dtype=bool))
     return vin + box_correction(vout_side, kappa, X, Y)
+
+
+# ---------------------------------------------------------------------------- sphere (3-D)
+def _radial(l, kappa, r):
+    """(inside, outside) radial functions and their r-derivatives of the separated
+    solutions f(r) Y_l of Lap v - kappa^2 v = 0: r^l and r^-(l+1) for kappa = 0, else the
+    modified spherical Bessel functions i_l(kappa r) and k_l(kappa r)."""
+    if kappa == 0.0:
+        return (r ** l, l * r ** (l - 1.0) if l > 0 else 0.0 * r,
+                r ** (-l - 1.0), -(l + 1.0) * r ** (-l - 2.0))
+    x = kappa * r
+    return (special.spherical_in(l, x), kappa * special.spherical_in(l, x, derivative=True),
+            special.spherical_kn(l, x), kappa * special.spherical_kn(l, x, derivative=True))
+
+
+def sphere_free_space(l, poly, R, c0, kappa, X, inside):
+    """Free-space double-layer potential of the density p(x - c0) on the sphere |x - c0| = R,
+    p a homogeneous harmonic polynomial of degree l (poly(d) evaluates it on (..., 3)
+    offsets): v = f(r) p(d) / r^l with f = A (inside) or B (outside) times the radial
+    functions, A and B from [v] = p and [d_r v] = 0 at r = R.  For kappa = 0:
+    A R^l = (l + 1)/(2l + 1), B R^-(l+1) = -l/(2l + 1)."""
+    d = X - np.asarray(c0)
+    r = np.sqrt(np.sum(d * d, axis=-1))
+    fi, dfi, fo, dfo = _radial(l, kappa, R)
+    # A fi - B fo = R^l,  A dfi - B dfo = 0
+    det = -fi * dfo + fo * dfi
+    A = -R ** l * dfo / det
+    B = -R ** l * dfi / det
+    gi, _, go, _ = _radial(l, kappa, r)
+    ang = poly(d) / np.where(r > 0, r, 1.0) ** l
+    return np.where(inside, A * gi, B * go) * ang
+
+
+def cube_correction(g_face, kappa, X, terms=40, quad=160):
+    """w at points X (..., 3) with (Lap - kappa^2) w = 0 in [-1,1]^3 and w = g_face(axis,
+    side, P) on the face x_axis = side (P the (Q, Q, 3) face points): the sum over the six
+    faces of the textbook double sine series
+      sum_{m,n} c_mn sin(m pi (s+1)/2) sin(n pi (t+1)/2) sinh(mu d) / sinh(2 mu),
+      mu = sqrt((pi/2)^2 (m^2 + n^2) + kappa^2), d the distance from the opposite face,
+    c_mn by Gauss-Legendre quadrature of the face data."""
+    q, wq = np.polynomial.legendre.leggauss(quad)
+    m = np.arange(1, terms + 1)
+    S = np.sin(np.outer(m, q + 1.0) * np.pi / 2.0) * wq[None, :]      # (terms, quad)
+    mu = np.sqrt((np.pi / 2.0) ** 2 * (m[:, None] ** 2 + m[None, :] ** 2) + kappa ** 2)
+    Xf = X.reshape(-1, 3)
+    w = np.zeros(Xf.shape[0])
+    for axis in range(3):
+        o1, o2 = [a for a in range(3) if a != axis]
+        for side in (-1.0, 1.0):
+            P = np.zeros((quad, quad, 3))
+            P[..., axis] = side
+            P[..., o1] = q[:, None]
+            P[..., o2] = q[None, :]
+            c = S @ g_face(axis, side, P) @ S.T                        # (terms, terms)
+            d = (Xf[:, axis] + 1.0) if side > 0 else (1.0 - Xf[:, axis])
+            s1 = np.sin(np.outer(Xf[:, o1] + 1.0, m) * np.pi / 2.0)    # (npts, terms)
+            s2 = np.sin(np.outer(Xf[:, o2] + 1.0, m) * np.pi / 2.0)
+            # sinh(mu d) / sinh(2 mu) without overflow
+            ratio = np.exp(mu[None] * (d[:, None, None] - 2.0)) * \
+                (1.0 - np.exp(-2.0 * mu[None] * d[:, None, None])) / (1.0 - np.exp(-4.0 * mu[None]))
+            w += np.einsum("pm,pn,mn,pmn->p", s1, s2, c, ratio, optimize=True)
+    return w.reshape(X.shape[:-1])
+
+
+def sphere_double_layer_plus(l, poly, R, c0, kappa, pts):
+    """Exact K_D p = v^+ at points pts on the sphere (box potential of [-1,1]^3): the
+    inside free-space field plus the cube correction with w = -v_out on the faces."""
+    def face(axis, side, P):
+        return -sphere_free_space(l, poly, R, c0, kappa, P, np.zeros(P.shape[:-1], dtype=bool))
+    vin = sphere_free_space(l, poly, R, c0, kappa, pts, np.ones(pts.shape[:-1], dtype=bool))
+    return vin + cube_correction(face, kappa, pts)

@@ -15,11 +15,19 @@ P9   least-squares surface derivatives of a linear function on a sphere against 
 P10  local truncation: quadratic v+ and v- with their exact jumps make the corrected
      7-point system exact at every interior node;
 P11  interpolation reproduces v+ exactly for quadratic v+ and v-;
+P4s  the double-layer apply (reading S10 included) converges at second order to the
+     closed-form box double-layer potential of a harmonic-polynomial density on a sphere
+     (free-space Y_l field with coefficients (l+1)/(2l+1) inside, -l/(2l+1) outside, or
+     the modified spherical Bessel pair for kappa > 0, plus the cube's double sine series);
+S10  spectrum of the assembled discrete K_D on a sphere: the continuous operator 1/2 I + W
+     has its spectrum in (1/2, 1] accumulating only at 1/2 (W compact), so every
+     eigenvalue must have real part in [0.4, 1.05] and most must lie near 1/2;
 plus planted mistakes that these pins must catch, and the geometry errors."""
 import numpy as np
 import pytest
 
 import kfbi_workloads.surfaces3d as S3
+from closed_forms import sphere_double_layer_plus
 from oracle import GeometryError
 from oracle import kfbi3d as O3
 
@@ -260,3 +268,72 @@ def test_surface_near_the_box_boundary_is_rejected():
     I = S3.intersect(S3.sphere(0.9), 16)
     with pytest.raises(GeometryError):
         O3.Geometry3D(I.pts, I.normals, I.shape, 16, 0.0)
+
+
+# ------------------------------------------------------------------------------- P4s
+SPHERE_POLYS = {   # homogeneous harmonic polynomials of degree l in the offset d = x - c
+    1: lambda d: d[..., 2],
+    2: lambda d: d[..., 0] * d[..., 1],
+    3: lambda d: d[..., 2] * (2 * d[..., 2] ** 2 - 3 * d[..., 0] ** 2 - 3 * d[..., 1] ** 2),
+}
+
+
+@pytest.mark.parametrize("kappa,l", [(0.0, 1), (0.0, 3), (2.0, 2)])
+def test_p4_sphere_closed_form_second_order(kappa, l):
+    """K_D p through apply_double_layer (jumps of the fitted density plus half the fit's
+    residual, reading S10) against the exact box double-layer potential on the sphere
+    R = 0.5: relative max error ratio about 4 (or better) per grid doubling."""
+    R, c0 = 0.5, np.asarray(S3.CENTER)
+    errs = []
+    for N in (16, 32, 64):
+        g, I = geom(S3.sphere(R), N, kappa)
+        out = O3.apply_double_layer(g, SPHERE_POLYS[l](I.pts - c0))
+        ex = sphere_double_layer_plus(l, SPHERE_POLYS[l], R, c0, kappa, I.pts)
+        errs.append(np.abs(out - ex).max() / np.abs(ex).max())
+    ratios = [errs[0] / errs[1], errs[1] / errs[2]]
+    assert min(ratios) > 3.5 and errs[2] < 5e-3, (errs, ratios)
+
+
+# ------------------------------------------------------------------------------- S10
+def _sphere_spectrum(variant="correct", N=16):
+    g, I = geom(S3.sphere(), N)
+    if variant == "correct":
+        apply = lambda p: O3.apply_double_layer(g, p)
+    elif variant == "factor_one":          # the whole fit residual instead of half of it
+        apply = lambda p: O3.apply_interface(g, phi=p) + (p - g.fitted(p))
+    else:                                  # raw point values in the jumps, no identity part
+        orig = g.surface_derivs
+
+        def raw(dens):
+            _, gr, H = orig(dens)
+            return np.asarray(dens, dtype=np.float64), gr, H
+        g.surface_derivs = raw
+        apply = lambda p: O3.apply_interface(g, phi=p)
+    K = np.stack([apply(e) for e in np.eye(g.P)], axis=1)
+    return np.linalg.eigvals(K)
+
+
+def _spectrum_pin(ev):
+    re = ev.real
+    near_half = np.mean(np.abs(re - 0.5) < 0.05)
+    return (re.min() >= 0.4 and re.max() <= 1.05 and np.abs(ev.imag).max() <= 0.05
+            and near_half >= 0.8 and abs(np.median(re) - 0.5) <= 0.02), (re.min(), re.max(),
+                                                                          near_half, np.median(re))
+
+
+def test_s10_spectrum_of_the_discrete_operator_on_a_sphere():
+    """Reading S10 pinned by the operator it discretises: on a sphere (kappa = 0, N = 16)
+    the eigenvalues of the assembled K_D lie in [0.4, 1.05] with small imaginary parts,
+    1 is one of them (the constant density), and they accumulate at 1/2."""
+    ev = _sphere_spectrum("correct")
+    ok, stats = _spectrum_pin(ev)
+    assert ok, stats
+    assert np.min(np.abs(ev - 1.0)) <= 1e-10
+
+
+@pytest.mark.parametrize("variant", ["factor_one", "raw_values"])
+def test_planted_s10_slips_fail_the_spectrum_pin(variant):
+    """Adding the whole fit residual (eigenvalues pile up at 1, not 1/2) or putting the raw
+    point values into the jumps (spurious eigenvalues near 0) fails the spectral pin."""
+    ok, stats = _spectrum_pin(_sphere_spectrum(variant))
+    assert not ok, stats

@@ -102,6 +102,65 @@ def test_p4_constant_density_kappa0_is_exact():
     assert np.max(np.abs(out - circle_double_layer_plus(0, 0.5, C0, 0.0, th))) < 1e-12
 
 
+def _grazing_circle(N, R=0.5):
+    """A circle whose top lies 0.04 h^2 / R above the grid row y_j nearest 0.4, centred
+    0.4 h to the right of the node x = 0: the row meets it in two points 0.28 h either side
+    of the centre, strictly inside the arm (x_i, x_i+1), whose end labels both say
+    outside (a grid line grazing the interface)."""
+    h = 2.0 / N
+    j = int(round(1.4 / h))
+    c0 = (-1.0 + (N // 2) * h + 0.4 * h, -1.0 + j * h - R + 0.04 * h * h / R)
+    return W.circle(2 * N, R, c0), c0, j
+
+
+@pytest.mark.parametrize("kappa,k", [(0.0, 1), (0.0, 3), (10.0, 3)])
+def test_p4_grazing_row_keeps_second_order(kappa, k):
+    """Reading R5 (grazing pairs): on a circle that grazes a grid row at every N, the row's
+    two crossings are dropped (no label changes there, no correction) and the closed-form
+    double-layer potential (P4) still converges at second order with P4's bounds."""
+    R = 0.5
+    errs = []
+    for N in (64, 128, 256):
+        iface, c0, j = _grazing_circle(N, R)
+        g = geom_of(iface, N, kappa)
+        assert len(g.row_lists[j]) == 2 and not g.inside[j].any()   # the grazing pair
+        th = 2 * np.pi * np.arange(iface.M) / iface.M
+        out = O.apply_double_layer(g, np.cos(k * th))
+        errs.append(np.max(np.abs(out - circle_double_layer_plus(k, R, c0, kappa, th))))
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert errs[-1] < 1e-4
+    assert min(ratios) > 3.0 and np.sqrt(ratios[0] * ratios[1]) > 3.5, (errs, ratios)
+
+
+@pytest.mark.parametrize("mistake", ["pair_kept", "one_dropped"])
+def test_planted_grazing_slips_are_caught(monkeypatch, mistake):
+    """Keeping a grazing pair, or dropping only one of its crossings, leaves crossings that
+    match no label change on the row: the geometry is rejected instead of silently
+    corrected."""
+    import oracle.kfbi2d as K
+    iface, _, _ = _grazing_circle(128)
+    geom_of(iface, 128, 0.0)                          # the correct rule accepts it
+    if mistake == "pair_kept":
+        monkeypatch.setattr(K, "GRAZE_CURV", -1.0)
+    else:
+        orig = K.Geometry2D._match_line
+
+        def drop_one(self, labels, lst, coord, curv):
+            order = lst[np.argsort(coord[lst], kind="stable")]
+            flips = np.nonzero(labels[1:] != labels[:-1])[0]
+            if order.size == flips.size + 2:         # a grazing pair is present: keep one
+                for q in range(order.size - 1):
+                    a0, a1 = coord[order[q]], coord[order[q + 1]]
+                    t = int(np.floor((a0 - self.lo) / self.h))
+                    if a1 < self.xs[t + 1] and labels[t] == labels[t + 1]:
+                        lst = np.delete(order, q + 1)
+                        break
+            return orig(self, labels, lst, coord, curv)
+        monkeypatch.setattr(K.Geometry2D, "_match_line", drop_one)
+    with pytest.raises(O.GeometryError):
+        geom_of(iface, 128, 0.0)
+
+
 # ------------------------------------------------------------------ P5
 @pytest.mark.parametrize("case", ["poisson_flower", "helmholtz_ellipse"])
 def test_p5_manufactured_bvp_second_order(case):
@@ -143,9 +202,10 @@ def test_p7_richardson_reaches_gmres_density():
     ghat = prob.g_ctrl() - O.apply_volume(g, prob.f_grid(), prob.f_ctrl())
     Kf = lambda p: O.apply_double_layer(g, p)
     phi_g, _ = O.gmres(Kf, ghat, tol=1e-12)
-    phi_r, info = O.richardson(Kf, ghat, gamma=1.0, tol=1e-11)
+    tol = 1e-11
+    phi_r, info = O.richardson(Kf, ghat, gamma=1.0, tol=tol)
     assert info["converged"]
-    assert np.max(np.abs(phi_r - phi_g)) <= 10 * 1e-11 * np.max(np.abs(phi_g)) * 10
+    assert np.max(np.abs(phi_r - phi_g)) <= 10 * tol * np.max(np.abs(phi_g))
 
 
 # ------------------------------------------------------------------ P8
@@ -307,3 +367,21 @@ def test_node_on_interface_tie_is_consistent():
     g = geom_of(prob.iface, 128, 0.0)
     out = O.apply_double_layer(g, np.ones(256))
     assert np.max(np.abs(out - 1.0)) < 1e-12
+
+
+# ------------------------------------------------------------------ error norms (Sec. 5)
+def test_error_norms_by_hand():
+    """Max norm and l2 norm over the nodes inside Omega (reading C14: N in the l2 norm is the
+    number of nodes inside Omega): a unit error at one inside node of 9 gives 1 and 1/3;
+    errors at outside nodes are ignored."""
+    inside = np.zeros((5, 5), dtype=bool)
+    inside[1:4, 1:4] = True
+    u = np.zeros((5, 5))
+    u[2, 2] = 1.0
+    u[0, 0] = 7.0                                   # outside Omega: not counted
+    e_inf, e_l2 = O.error_norms(u, np.zeros((5, 5)), inside)
+    assert e_inf == 1.0
+    assert e_l2 == pytest.approx(1.0 / 3.0, rel=1e-15)
+    u[1, 3] = -2.0                                  # two inside errors: sqrt((1 + 4) / 9)
+    e_inf, e_l2 = O.error_norms(u, np.zeros((5, 5)), inside)
+    assert e_inf == 2.0 and e_l2 == pytest.approx(np.sqrt(5.0 / 9.0), rel=1e-15)
