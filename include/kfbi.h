@@ -127,7 +127,9 @@ typedef struct {
                             FP64 (row: 0 = 16/24 values per thread, 1 = 8/12; column:
                             bit 0 = 256-thread blocks, bit 1 = 8/12 values per thread,
                             bit 2 = transposed pass: transpose, row-wise y-transforms,
-                            transpose back) */
+                            transpose back; 8 = FP32 y-pass on the row layout: recursive
+                            filters along y for the modes >= tri_first_mode, the transform
+                            pair for the lower ones) */
   int dim;               /* 2 or 3                                                        */
   int n_crossings_z;     /* 3-D: points on z-lines; 0 in 2-D                              */
   int tri_first_mode;    /* 2-D FP32 box solves: x-modes k >= this are solved along y by

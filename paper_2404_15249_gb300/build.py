@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkfbi.so")
 SOURCES = ["dst.cu", "dst_f32.cu", "dst_f64.cu", "setup2d.cu", "apply2d.cu", "gmres.cu", "capi.cu",
-           "box_static.cu", "kfbi3d.cu", "dst3d.cu", "dst_tc.cu", "dst_tri.cu", "probe.cu"]
+           "box_static.cu", "kfbi3d.cu", "dst3d.cu", "dst_tc.cu", "dst_tri.cu", "dst_ycol.cu", "probe.cu"]
 ARCH = os.environ.get("KFBI_ARCH", "103a")
 
 

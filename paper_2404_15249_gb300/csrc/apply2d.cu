@@ -147,67 +147,132 @@ __global__ void split_kernel(long n, const double* __restrict__ b, float* __rest
 }
 
 // ------------------------------------------------------------------ sparse plain apply
-// The double-layer right-hand side is nonzero only at irregular nodes, so the plain FP32
-// apply evaluates the first sine transform (along x) directly on them (the same DST-I sums,
-// in another order), written straight into the transposed layout of the column pass:
-// X[k][j] = sum over irregular (i, j) of b_ij sin(pi i k / N).  With theta = pi i k / N the
-// modes k, N - k, N/2 + k and N/2 - k share one (cos theta, sin theta):
-//   sin(pi i (N - k) / N)   = (-1)^(i+1) sin theta,
+// The double- (single-) layer right-hand side is nonzero only at irregular nodes, so the
+// plain FP32 apply fuses the correction gather (Alg. 2) with the first sine transform
+// (along x, Alg. 4) and writes the transformed rows straight into the work grid:
+//   X[j][k] = sum over irregular (i, j) of b_ij sin(pi i k / N).
+// One CTA per grid row j: its threads first form b_ij for the row's irregular nodes from
+// the density (FP64 weights per crossed arm, as correction_kernel) into shared memory,
+// then thread t accumulates the modes k = t + s T (s < S, k < N/4) and, by the symmetries
+// of the sine with theta = pi i k / N,
+//   sin(pi i (N - k) / N)    = (-1)^(i+1) sin theta,
 //   sin(pi i (N/2 +- k) / N) = sin(pi i / 2 +- theta) = +-sin theta or cos theta by i mod 4,
-// so a thread takes one row j and SPARSE_KB consecutive modes k in [0, N/4] and fills four
-// output rows; along k the pair (cos, sin) follows by rotation from the table value at the
-// block's first mode (SPARSE_KB steps).
-constexpr int SPARSE_KB = 8;
+// the modes N - k, N/2 + k and N/2 - k as well; (cos, sin) of theta start from the exact
+// table value at k = t and advance by the rotation through pi i T / N (S steps).  Mode N/4
+// (and 3N/4) comes from the table directly.  Rows without irregular nodes are zero.
+constexpr int SPX_THREADS_MAX = 256;
+constexpr int SPX_NODES = 64;          // irregular nodes of a row held in shared memory at once
 
-__global__ void __launch_bounds__(128)
-    sparse_rows_t_kernel(int N, const int* __restrict__ irr_node, const int* __restrict__ rowptr,
-                         const float* __restrict__ B, const float2* __restrict__ tw,
-                         float* __restrict__ X) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int k0 = blockIdx.y * SPARSE_KB;
-  const int Q = N / 4, H = N / 2;
-  if (j >= N) return;
-  float a1[SPARSE_KB], a2[SPARSE_KB], a3[SPARSE_KB], a4[SPARSE_KB];
+template <int S>
+__global__ void __launch_bounds__(SPX_THREADS_MAX)
+    sparse_rows_kernel(int N, int M, const int* __restrict__ irr_node,
+                       const int* __restrict__ rowptr, const int* __restrict__ arm_ptr,
+                       const int* __restrict__ arm_seg, const double* __restrict__ wgt,
+                       const double* __restrict__ dens, const float2* __restrict__ tw,
+                       float* __restrict__ X) {
+  __shared__ int s_i[SPX_NODES];
+  __shared__ float s_b[SPX_NODES];
+  const int j = blockIdx.x, t = threadIdx.x, T = blockDim.x;
+  const int Q = N / 4, H = N / 2, N2 = 2 * N;
+  const int n0 = j > 0 ? rowptr[j - 1] : 0, n1 = j > 0 ? rowptr[j] : 0;
+  float* row = X + (size_t)j * N;
+  if (n1 == n0) {                                     // no irregular node: the row is zero
+    for (int k = t; k < N; k += T) row[k] = 0.f;
+    return;
+  }
+  float a1[S], a2[S], a3[S], a4[S];
 #pragma unroll
-  for (int kk = 0; kk < SPARSE_KB; ++kk) a1[kk] = a2[kk] = a3[kk] = a4[kk] = 0.f;
-  if (j > 0) {
-    for (int n = rowptr[j - 1]; n < rowptr[j]; ++n) {
-      const int node = irr_node[n];
-      const int i = node - j * N;
-      const float b = B[node];
-      const float2 t0 = tw[(int)(((long)i * k0) % (2 * N))], ti = tw[i];
+  for (int s = 0; s < S; ++s) a1[s] = a2[s] = a3[s] = a4[s] = 0.f;
+  float aq = 0.f, a3q = 0.f;                          // modes N/4, 3N/4 (thread 0)
+  for (int base = n0; base < n1; base += SPX_NODES) {
+    const int cnt = min(SPX_NODES, n1 - base);
+    __syncthreads();                                  // previous batch consumed
+    for (int q = t; q < cnt; q += T) {                // correction gather of node base + q
+      const int n = base + q;
+      double acc = 0.0;
+      for (int a = arm_ptr[n]; a < arm_ptr[n + 1]; ++a) {
+        const int sg = arm_seg[a];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) acc += wgt[6 * a + r] * dens[wrap(sg - 2 + r, M)];
+      }
+      s_i[q] = irr_node[n] - j * N;
+      s_b[q] = (float)acc;
+    }
+    __syncthreads();
+    for (int q = 0; q < cnt; ++q) {
+      const int i = s_i[q];
+      const float b = s_b[q];
+      const float2 t0 = tw[(int)(((long)i * t) % N2)], td = tw[(int)(((long)i * T) % N2)];
       float cs = t0.x, sn = -t0.y;
-      const float C = ti.x, S = -ti.y;
+      const float C = td.x, Sd = -td.y;
       const bool odd = i & 1;
-      const float p2 = odd ? b : -b;                          // mode N - k
-      const float p3 = ((i & 3) == 0 || (i & 3) == 1) ? b : -b; // mode N/2 + k
-      const float p4 = odd ? p3 : -p3;                        // mode N/2 - k
+      const float p2 = odd ? b : -b;                              // mode N - k
+      const float p3 = ((i & 3) == 0 || (i & 3) == 1) ? b : -b;   // mode N/2 + k
+      const float p4 = odd ? p3 : -p3;                            // mode N/2 - k
 #pragma unroll
-      for (int kk = 0; kk < SPARSE_KB; ++kk) {
-        const float t = odd ? cs : sn;
-        a1[kk] = fmaf(b, sn, a1[kk]);
-        a2[kk] = fmaf(p2, sn, a2[kk]);
-        a3[kk] = fmaf(p3, t, a3[kk]);
-        a4[kk] = fmaf(p4, t, a4[kk]);
-        const float cn = cs * C - sn * S;
-        sn = fmaf(sn, C, cs * S);
+      for (int s = 0; s < S; ++s) {
+        const float tt = odd ? cs : sn;
+        a1[s] = fmaf(b, sn, a1[s]);
+        a2[s] = fmaf(p2, sn, a2[s]);
+        a3[s] = fmaf(p3, tt, a3[s]);
+        a4[s] = fmaf(p4, tt, a4[s]);
+        const float cn = cs * C - sn * Sd;
+        sn = fmaf(sn, C, cs * Sd);
         cs = cn;
+      }
+      if (t == 0) {
+        aq = fmaf(b, -tw[(int)(((long)i * Q) % N2)].y, aq);
+        a3q = fmaf(b, -tw[(int)(((long)i * 3 * Q) % N2)].y, a3q);
       }
     }
   }
-  // every mode written exactly once: k in [0, N/4], N - k and N/2 - k for 0 < k < N/4,
-  // N/2 + k for 0 <= k <= N/4 (X[0] = 0)
+  // every mode written exactly once: k in [0, N/4) with N/2 + k, and N - k, N/2 - k for
+  // 0 < k < N/4; then N/4 and 3N/4 (X[0] = 0)
 #pragma unroll
-  for (int kk = 0; kk < SPARSE_KB; ++kk) {
-    const int k = k0 + kk;
-    if (k > Q) break;
-    X[(size_t)k * N + j] = (k == 0) ? 0.f : a1[kk];
-    X[(size_t)(H + k) * N + j] = a3[kk];
-    if (k > 0 && k < Q) {
-      X[(size_t)(N - k) * N + j] = a2[kk];
-      X[(size_t)(H - k) * N + j] = a4[kk];
+  for (int s = 0; s < S; ++s) {
+    const int k = t + s * T;
+    if (k >= Q) break;
+    row[k] = (k == 0) ? 0.f : a1[s];
+    row[H + k] = a3[s];
+    if (k > 0) {
+      row[N - k] = a2[s];
+      row[H - k] = a4[s];
     }
   }
+  if (t == 0) {
+    row[Q] = aq;
+    row[3 * Q] = a3q;
+  }
+}
+
+template <int S>
+static void launch_sparse_rows(Ctx& c, int T, const double* wgt, const double* dens, float* X) {
+  sparse_rows_kernel<S><<<c.N, T, 0, c.stream>>>(c.N, c.M, c.irr_node, c.irr_rowptr, c.arm_ptr,
+                                                 c.arm_seg, wgt, dens,
+                                                 reinterpret_cast<const float2*>(c.t32.tw), X);
+}
+
+// threads per row: N/4 rounded up to a warp, at most 256; S = ceil(N/4 / T) steps
+static kfbi_status sparse_rows(Ctx& c, const double* wgt, const double* dens, float* X) {
+  const int Q = c.N / 4;
+  const int T = Q >= SPX_THREADS_MAX ? SPX_THREADS_MAX : ((Q + 31) / 32) * 32;
+  const int S = (Q + T - 1) / T;
+  const int pr = prof_begin(c, ST_SPARSE);
+  switch (S) {
+    case 1: launch_sparse_rows<1>(c, T, wgt, dens, X); break;
+    case 2: launch_sparse_rows<2>(c, T, wgt, dens, X); break;
+    case 3: launch_sparse_rows<3>(c, T, wgt, dens, X); break;
+    case 4: launch_sparse_rows<4>(c, T, wgt, dens, X); break;
+    case 6: launch_sparse_rows<6>(c, T, wgt, dens, X); break;
+    case 8: launch_sparse_rows<8>(c, T, wgt, dens, X); break;
+    default:
+      prof_end(c, pr);
+      set_error("sparse x-transform: N = %d not supported", c.N);
+      return KFBI_ERR_UNSUPPORTED;
+  }
+  prof_end(c, pr);
+  KFBI_CUDA_TRY(cudaGetLastError());
+  return KFBI_OK;
 }
 
 // ------------------------------------------------------------------ grid kernels
@@ -375,22 +440,16 @@ kfbi_status apply_potential(Ctx& c, Layer layer, int precision, const double* de
     return interp<double>(c, c.V64, nullptr, nullptr, d, s, nullptr, out);
   }
   const int steps = refine_steps_of(precision);
+  if (steps == 0 && precision != KFBI_TF32X3 && c.irr_rowptr && c.dim == 2) {
+    // correction fused with the first x-transform (sparse right-hand side), then the rest
+    // of the box solve on the transformed rows
+    KFBI_TRY(sparse_rows(c, d ? c.arm_wD : c.arm_wS, d ? d : s, c.V32));
+    KFBI_TRY(box_solve_after_rows_f32(c, c.V32));
+    return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out);
+  }
   KFBI_TRY(correct<float>(c, d, s, nullptr, c.B32, 0, steps ? c.B64 : nullptr));
   if (precision == KFBI_TF32X3) {                   // dense sine transforms on tensor cores
     KFBI_TRY(box_solve_tc(c, c.B32, c.V32));
-    return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out);
-  }
-  if (steps == 0 && c.irr_rowptr && c.dim == 2) {
-    // sparse first x-transform, then the dense y-transform pair and the last x-transform
-    float* X = reinterpret_cast<float*>(c.XT);
-    const float2* tw = reinterpret_cast<const float2*>(c.t32.tw);
-    int pr = prof_begin(c, ST_SPARSE);
-    sparse_rows_t_kernel<<<dim3((c.N + 127) / 128, (c.N / 4 + SPARSE_KB) / SPARSE_KB), 128, 0,
-                           c.stream>>>(c.N, c.irr_node, c.irr_rowptr, c.B32, tw, X);
-    prof_end(c, pr);
-    KFBI_CUDA_TRY(cudaGetLastError());
-    KFBI_TRY(ylines_f32(c, X));
-    KFBI_TRY(x_pass_f32(c, X, c.V32));
     return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out);
   }
   if (steps == 0) {

@@ -55,6 +55,9 @@ static void free_handle(kfbi_ctx_s* hd) {
   kfbi::free_tc(c);
   for (int i = 0; i < 2; ++i)
     if (c.gm_ev[i]) cudaEventDestroy(c.gm_ev[i]);
+  if (c.fork_ev) cudaEventDestroy(c.fork_ev);
+  if (c.join_ev) cudaEventDestroy(c.join_ev);
+  if (c.side) cudaStreamDestroy(c.side);
   delete hd;
 }
 
@@ -152,6 +155,13 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
     }                         \
   } while (0)
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.err_flag, sizeof(int) * 4));
+  if (cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c.fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c.join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    kfbi::set_error("kfbi_setup: stream or event creation failed");
+    free_handle(hd);
+    return KFBI_ERR_CUDA;
+  }
   // per point: dim coordinates, dim normal components, 1 curvature (2-D) or 6 packed
   // shape-operator entries (3-D)
   const size_t ncurv = dim == 2 ? 1 : 6;
@@ -194,8 +204,8 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
     const char* fixed = std::getenv("KFBI_DST_VARIANTS");
     int v[4];
     if (fixed && std::sscanf(fixed, "%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3]) == 4 &&
-        v[0] >= 0 && v[0] <= 1 && v[2] >= 0 && v[2] <= 1 && v[1] >= 0 && v[1] <= 7 &&
-        v[3] >= 0 && v[3] <= 7) {
+        v[0] >= 0 && v[0] <= 1 && v[2] >= 0 && v[2] <= 1 && v[1] >= 0 && v[1] <= 8 &&
+        v[3] >= 0 && v[3] <= 7 && (v[1] != 8 || (c.tri_k0 > 0 && c.tri_k0 < c.N))) {
       c.rows_variant[0] = v[0];
       c.cols_variant[0] = v[1];
       c.rows_variant[1] = v[2];

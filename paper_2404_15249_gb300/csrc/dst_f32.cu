@@ -23,4 +23,15 @@ kfbi_status ylines_f32(Ctx& c, float* X) {
                                      c.t32.lam);
 }
 
+kfbi_status box_solve_after_rows_f32(Ctx& c, float* work) {
+  return dst::box_after_rows_dispatch<float>(c, work,
+                                             reinterpret_cast<const dst::cx<float>*>(c.t32.tw),
+                                             c.t32.lam);
+}
+
+kfbi_status ylines_f32_lines(Ctx& c, float* X, int nlines) {
+  return dst::ylines_dispatch<float>(c, X, reinterpret_cast<const dst::cx<float>*>(c.t32.tw),
+                                     c.t32.lam, nlines);
+}
+
 }  // namespace kfbi

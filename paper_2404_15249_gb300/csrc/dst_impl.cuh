@@ -887,9 +887,11 @@ kfbi_status launch_ylines(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   return KFBI_OK;
 }
 
-// the y-transform pair alone on an already transposed grid (2-D, N lines)
+// the y-transform pair alone on an already transposed grid (2-D): lines [0, nlines) of X,
+// or, when nlines < 0, the lines below tri_k0 (FP32) followed by the tridiagonal pass on
+// the others
 template <typename T, int N, int EPT>
-kfbi_status launch_ylines_only(Ctx& c, T* X, const cx<T>* tw, const T* lam) {
+kfbi_status launch_ylines_only(Ctx& c, T* X, const cx<T>* tw, const T* lam, int nlines) {
   constexpr CPlan P = cplan(N, EPT);
   constexpr int lpc = yline_lpc<T, N, EPT>();
   const cx<T>* stw = nullptr;
@@ -905,7 +907,9 @@ kfbi_status launch_ylines_only(Ctx& c, T* X, const cx<T>* tw, const T* lam) {
   int blocks = (N + lpc - 1) / lpc;
   blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
   const T scale = T((2.0 / N) * (2.0 / N));
-  const int nfft = (std::is_same<T, float>::value && c.tri_k0 > 0 && c.tri_k0 < N) ? c.tri_k0 : N;
+  const bool split = nlines < 0;
+  const int nfft = !split ? nlines
+                          : ((std::is_same<T, float>::value && c.tri_k0 > 0 && c.tri_k0 < N) ? c.tri_k0 : N);
   const int fblocks = blocks < (nfft + lpc - 1) / lpc ? blocks : (nfft + lpc - 1) / lpc;
   const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
   yline_kernel<T, N, EPT, 2><<<fblocks, threads, smem, c.stream>>>(X, stw, tw, lam, T(c.kappa2),
@@ -914,19 +918,19 @@ kfbi_status launch_ylines_only(Ctx& c, T* X, const cx<T>* tw, const T* lam) {
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   if constexpr (std::is_same<T, float>::value)
-    if (nfft < N) KFBI_TRY(ytri_f32(c, X, nfft));
+    if (split && nfft < N) KFBI_TRY(ytri_f32(c, X, nfft));
   return KFBI_OK;
 }
 
 template <typename T>
-kfbi_status ylines_dispatch(Ctx& c, T* X, const cx<T>* tw, const T* lam) {
+kfbi_status ylines_dispatch(Ctx& c, T* X, const cx<T>* tw, const T* lam, int nlines = -1) {
   const bool half = (c.cols_variant[sizeof(T) == 8] & 2) != 0;
   switch (c.N) {
 #define KFBI_CASE(n)                                                                          \
   case n:                                                                                     \
     if (half && n / (default_ept(n) / 2) <= 512)                                              \
-      return launch_ylines_only<T, n, default_ept(n) / 2>(c, X, tw, lam);                     \
-    return launch_ylines_only<T, n, default_ept(n)>(c, X, tw, lam);
+      return launch_ylines_only<T, n, default_ept(n) / 2>(c, X, tw, lam, nlines);             \
+    return launch_ylines_only<T, n, default_ept(n)>(c, X, tw, lam, nlines);
     KFBI_CASE(32) KFBI_CASE(48) KFBI_CASE(64) KFBI_CASE(96) KFBI_CASE(128) KFBI_CASE(192)
     KFBI_CASE(256) KFBI_CASE(384) KFBI_CASE(512) KFBI_CASE(768) KFBI_CASE(1024)
     KFBI_CASE(1536) KFBI_CASE(2048) KFBI_CASE(3072) KFBI_CASE(4096) KFBI_CASE(6144)
@@ -957,6 +961,8 @@ template <typename T, int N>
 kfbi_status launch_cols_v(Ctx& c, T* V, const cx<T>* tw, const T* lam, int variant) {
   constexpr int E = default_ept(N);
   constexpr int EH = E / 2;
+  if constexpr (std::is_same<T, float>::value)
+    if (variant & 8) return ypass_rows_f32(c, V);
   const bool small = variant & 1, half = (variant & 2) != 0;
   if (variant & 4) {
     if (half && N / EH <= 512) return launch_ylines<T, N, EH>(c, V, tw, lam);
@@ -994,7 +1000,10 @@ kfbi_status autotune(Ctx& c, T* V, const cx<T>* tw, const T* lam, int* rows_choi
     if (ms < best) { best = ms; *rows_choice = v; }
   }
   best = 1e30f;
-  for (int v : {0, 1, 2, 3, 4, 6}) {
+  // FP32 2-D with well-conditioned modes: also the y-pass on the row layout (variant 8)
+  const bool rowpass = std::is_same<T, float>::value && c.dim == 2 && c.tri_k0 > 0 && c.tri_k0 < N;
+  for (int v : {0, 1, 2, 3, 4, 6, 8}) {
+    if (v == 8 && !rowpass) continue;
     float ms = 0.f;
     KFBI_TRY(time_it([&] { return launch_cols_v<T, N>(c, V, tw, lam, v); }, &ms));
     if (ms < best) { best = ms; *cols_choice = v; }
@@ -1011,6 +1020,30 @@ kfbi_status box_solve_n(Ctx& c, const T* rhs, T* work, const cx<T>* tw, const T*
   KFBI_TRY((launch_cols_v<T, N>(c, work, tw, lam, cv)));
   KFBI_TRY((launch_rows_v<T, N>(c, work, work, tw, T(1), rv)));
   return KFBI_OK;
+}
+
+// the box solve after its first row pass: the column pass and the last row pass on work
+template <typename T, int N>
+kfbi_status box_after_rows_n(Ctx& c, T* work, const cx<T>* tw, const T* lam) {
+  const int rv = c.rows_variant[sizeof(T) == 8], cv = c.cols_variant[sizeof(T) == 8];
+  KFBI_TRY((launch_cols_v<T, N>(c, work, tw, lam, cv)));
+  KFBI_TRY((launch_rows_v<T, N>(c, work, work, tw, T(1), rv)));
+  return KFBI_OK;
+}
+
+template <typename T>
+kfbi_status box_after_rows_dispatch(Ctx& c, T* work, const cx<T>* tw, const T* lam) {
+  switch (c.N) {
+#define KFBI_CASE(n) \
+  case n: return box_after_rows_n<T, n>(c, work, tw, lam);
+    KFBI_CASE(32) KFBI_CASE(48) KFBI_CASE(64) KFBI_CASE(96) KFBI_CASE(128) KFBI_CASE(192)
+    KFBI_CASE(256) KFBI_CASE(384) KFBI_CASE(512) KFBI_CASE(768) KFBI_CASE(1024)
+    KFBI_CASE(1536) KFBI_CASE(2048) KFBI_CASE(3072) KFBI_CASE(4096) KFBI_CASE(6144)
+    KFBI_CASE(8192)
+#undef KFBI_CASE
+  }
+  set_error("box solve: no compiled plan for N = %d", c.N);
+  return KFBI_ERR_UNSUPPORTED;
 }
 
 template <typename T>

@@ -105,6 +105,8 @@ struct Ctx {
   double lo = -1, hi = 1, h = 0, kappa = 0, kappa2 = 0;
   kfbi_options opt{};
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;              // second stream of the row-layout y-pass
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   FftPlan plan{};
 
   // interface (device, FP64)
@@ -221,6 +223,13 @@ kfbi_status box_solve_f64(Ctx& c, const double* rhs, double* work);
 // and the last half of the box solve: transpose X back into V and transform its rows
 kfbi_status ylines_f32(Ctx& c, float* X);
 kfbi_status x_pass_f32(Ctx& c, const float* X, float* V);
+// the y-transform pair on lines [0, nlines) of the transposed FP32 grid X only
+kfbi_status ylines_f32_lines(Ctx& c, float* X, int nlines);
+// FP32 2-D: the box solve after its first row pass (column pass variant + last row pass)
+kfbi_status box_solve_after_rows_f32(Ctx& c, float* work);
+// FP32 2-D y-pass on the row layout: recursive filters for the modes k >= tri_k0, the
+// transform pair (side stream) for the others (dst_ycol.cu)
+kfbi_status ypass_rows_f32(Ctx& c, float* V);
 kfbi_status init_box_tables(Ctx& c);
 kfbi_status autotune_f32(Ctx& c);   // column-pass variant per precision, on scratch grids
 kfbi_status autotune_f64(Ctx& c);

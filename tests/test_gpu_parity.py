@@ -263,3 +263,32 @@ def test_fp32_box_solve_with_and_without_the_tridiagonal_pass(kappa):
         ref = O.box_solve_dst(b, N, geom.h, kappa * kappa)
         assert rel(ctx.box_solve(b, K.KFBI_MIXED_FP32).cpu().numpy(), ref) < 2e-5
         ctx.close()
+
+
+@pytest.mark.parametrize("N", [64, 96, 256, 384, 1024])
+@pytest.mark.parametrize("variant", [0, 4, 8])
+def test_fp32_column_pass_variants(N, variant, monkeypatch):
+    """Each FP32 y-pass variant, fixed at setup (KFBI_DST_VARIANTS): the staged column tiles
+    (0), the transposed pass with the tridiagonal elimination (4) and the row-layout pass
+    with the recursive filters and the transform pair on a side stream (8), on grids whose
+    sizes leave ragged chunks and warm-ups longer than a chunk: the FP32 box solve and the
+    plain FP32 apply (correction fused with the first x-transform) within 2e-5 of the
+    oracle."""
+    monkeypatch.setenv("KFBI_DST_VARIANTS", f"0,{variant},0,6")
+    kappa = 3.0
+    prob = W.Problem(W.flower(2 * N), N, kappa, W.manufactured_sinpi(kappa))
+    ctx, geom = make(prob)
+    monkeypatch.delenv("KFBI_DST_VARIANTS")
+    assert ctx.info()["dst_variant"][1] == variant
+    rng = np.random.default_rng(N + variant)
+    b = np.zeros((N + 1, N + 1))
+    b[1:N, 1:N] = rng.standard_normal((N - 1, N - 1))
+    ref = O.box_solve_dst(b, N, geom.h, kappa * kappa)
+    assert rel(ctx.box_solve(b, K.KFBI_MIXED_FP32).cpu().numpy(), ref) < 2e-5
+    phi = W.random_density(prob.iface.M, seed=N)
+    ref = O.apply_double_layer(geom, phi)
+    assert rel(ctx.apply_layer_potential(phi, 0, K.KFBI_MIXED_FP32).cpu().numpy(), ref) < 2e-5
+    psi = W.random_density(prob.iface.M, seed=N + 1)
+    ref = O.apply_interface(geom, psi=psi)
+    assert rel(ctx.apply_layer_potential(psi, 1, K.KFBI_MIXED_FP32).cpu().numpy(), ref) < 2e-5
+    ctx.close()
