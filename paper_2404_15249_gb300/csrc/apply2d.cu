@@ -151,17 +151,29 @@ __global__ void split_kernel(long n, const double* __restrict__ b, float* __rest
 // plain FP32 apply fuses the correction gather (Alg. 2) with the first sine transform
 // (along x, Alg. 4) and writes the transformed rows straight into the work grid:
 //   X[j][k] = sum over irregular (i, j) of b_ij sin(pi i k / N).
-// One CTA per grid row j: its threads first form b_ij for the row's irregular nodes from
-// the density (FP64 weights per crossed arm, as correction_kernel) into shared memory,
-// then thread t accumulates the modes k = t + s T (s < S, k < N/4) and, by the symmetries
-// of the sine with theta = pi i k / N,
+// One CTA per grid row j (T threads in W = T/32 warps).  Warp w prepares the row's nodes
+// q = w, w + W, ...: lanes over (crossed arm, weight) pairs form b_ij from the density (up
+// to 4 x 6 FP64 products gathered at once, summed by shuffles), and the node's phase
+// tables go to shared memory: e^{i pi i l / N} for the lanes l < 32, e^{i pi i 32 v / N}
+// for the warps v < W, and the rotation e^{i pi i T / N}.  Then thread t = 32 v + l
+// accumulates the modes k = t + s T (s < S, k < N/4), starting from the product of its
+// lane and warp factors and advancing by the rotation, and by the symmetries of the sine
+// with theta = pi i k / N,
 //   sin(pi i (N - k) / N)    = (-1)^(i+1) sin theta,
 //   sin(pi i (N/2 +- k) / N) = sin(pi i / 2 +- theta) = +-sin theta or cos theta by i mod 4,
-// the modes N - k, N/2 + k and N/2 - k as well; (cos, sin) of theta start from the exact
-// table value at k = t and advance by the rotation through pi i T / N (S steps).  Mode N/4
-// (and 3N/4) comes from the table directly.  Rows without irregular nodes are zero.
+// the modes N - k, N/2 + k and N/2 - k as well.  Modes N/4 and 3N/4 come from table
+// values kept with the node.  Rows without irregular nodes are zero.
 constexpr int SPX_THREADS_MAX = 256;
-constexpr int SPX_NODES = 64;          // irregular nodes of a row held in shared memory at once
+constexpr int SPX_NODES = 32;          // irregular nodes of a row held in shared memory at once
+
+// x mod 2N for 0 <= x < 2^31 with x / 2N < 2^20 (the float quotient is then off by at most
+// one, corrected by one step either way)
+__device__ __forceinline__ int mod_2n(int x, int n2, float inv_n2) {
+  int r = x - n2 * (int)((float)x * inv_n2);
+  r += r < 0 ? n2 : 0;
+  r -= r >= n2 ? n2 : 0;
+  return r;
+}
 
 template <int S>
 __global__ void __launch_bounds__(SPX_THREADS_MAX)
@@ -170,14 +182,19 @@ __global__ void __launch_bounds__(SPX_THREADS_MAX)
                        const int* __restrict__ arm_seg, const double* __restrict__ wgt,
                        const double* __restrict__ dens, const float2* __restrict__ tw,
                        float* __restrict__ X) {
-  __shared__ int s_i[SPX_NODES];
-  __shared__ float s_b[SPX_NODES];
+  constexpr int WMAX = SPX_THREADS_MAX / 32;
+  __shared__ float2 s_lane[SPX_NODES][32];
+  __shared__ float2 s_warp[SPX_NODES][WMAX];
+  __shared__ float4 s_node[SPX_NODES];   // (b, rotation cos, rotation sin, i as bits)
+  __shared__ float2 s_q[SPX_NODES];      // sin(pi i / 4), sin(3 pi i / 4)
   const int j = blockIdx.x, t = threadIdx.x, T = blockDim.x;
+  const int lane = t & 31, warp = t >> 5, nwarps = T >> 5;
   const int Q = N / 4, H = N / 2, N2 = 2 * N;
+  const float inv_n2 = 1.f / (float)N2;
   const int n0 = j > 0 ? rowptr[j - 1] : 0, n1 = j > 0 ? rowptr[j] : 0;
   float* row = X + (size_t)j * N;
   if (n1 == n0) {                                     // no irregular node: the row is zero
-    for (int k = t; k < N; k += T) row[k] = 0.f;
+    for (int k = 4 * t; k < N; k += 4 * T) *reinterpret_cast<float4*>(row + k) = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
   float a1[S], a2[S], a3[S], a4[S];
@@ -187,24 +204,36 @@ __global__ void __launch_bounds__(SPX_THREADS_MAX)
   for (int base = n0; base < n1; base += SPX_NODES) {
     const int cnt = min(SPX_NODES, n1 - base);
     __syncthreads();                                  // previous batch consumed
-    for (int q = t; q < cnt; q += T) {                // correction gather of node base + q
+    for (int q = warp; q < cnt; q += nwarps) {
       const int n = base + q;
-      double acc = 0.0;
-      for (int a = arm_ptr[n]; a < arm_ptr[n + 1]; ++a) {
-        const int sg = arm_seg[a];
+      const int a0 = arm_ptr[n], na = arm_ptr[n + 1] - a0;
+      const int i = irr_node[n] - j * N;
+      const int a = lane / 6, r = lane - 6 * (lane / 6);
+      double v = 0.0;
+      if (lane < 24 && a < na)
+        v = wgt[6 * (a0 + a) + r] * dens[wrap(arm_seg[a0 + a] - 2 + r, M)];
 #pragma unroll
-        for (int r = 0; r < 6; ++r) acc += wgt[6 * a + r] * dens[wrap(sg - 2 + r, M)];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      const float2 pl = tw[mod_2n(i * lane, N2, inv_n2)];
+      s_lane[q][lane] = make_float2(pl.x, -pl.y);
+      if (lane < nwarps) {
+        const float2 pw = tw[mod_2n(i * 32 * lane, N2, inv_n2)];
+        s_warp[q][lane] = make_float2(pw.x, -pw.y);
       }
-      s_i[q] = irr_node[n] - j * N;
-      s_b[q] = (float)acc;
+      if (lane == 0) {
+        const float2 rt = tw[mod_2n(i * T, N2, inv_n2)];
+        s_node[q] = make_float4((float)v, rt.x, -rt.y, __int_as_float(i));
+        s_q[q] = make_float2(-tw[mod_2n(i * Q, N2, inv_n2)].y, -tw[mod_2n(i * 3 * Q, N2, inv_n2)].y);
+      }
     }
     __syncthreads();
     for (int q = 0; q < cnt; ++q) {
-      const int i = s_i[q];
-      const float b = s_b[q];
-      const float2 t0 = tw[(int)(((long)i * t) % N2)], td = tw[(int)(((long)i * T) % N2)];
-      float cs = t0.x, sn = -t0.y;
-      const float C = td.x, Sd = -td.y;
+      const float4 nd = s_node[q];
+      const int i = __float_as_int(nd.w);
+      const float b = nd.x;
+      const float2 pl = s_lane[q][lane], pw = s_warp[q][warp];
+      float cs = pl.x * pw.x - pl.y * pw.y;           // e^{i pi i t / N}, t = 32 warp + lane
+      float sn = fmaf(pl.x, pw.y, pl.y * pw.x);
       const bool odd = i & 1;
       const float p2 = odd ? b : -b;                              // mode N - k
       const float p3 = ((i & 3) == 0 || (i & 3) == 1) ? b : -b;   // mode N/2 + k
@@ -216,13 +245,15 @@ __global__ void __launch_bounds__(SPX_THREADS_MAX)
         a2[s] = fmaf(p2, sn, a2[s]);
         a3[s] = fmaf(p3, tt, a3[s]);
         a4[s] = fmaf(p4, tt, a4[s]);
-        const float cn = cs * C - sn * Sd;
-        sn = fmaf(sn, C, cs * Sd);
-        cs = cn;
+        if (s + 1 < S) {
+          const float cn = cs * nd.y - sn * nd.z;
+          sn = fmaf(sn, nd.y, cs * nd.z);
+          cs = cn;
+        }
       }
       if (t == 0) {
-        aq = fmaf(b, -tw[(int)(((long)i * Q) % N2)].y, aq);
-        a3q = fmaf(b, -tw[(int)(((long)i * 3 * Q) % N2)].y, a3q);
+        aq = fmaf(b, s_q[q].x, aq);
+        a3q = fmaf(b, s_q[q].y, a3q);
       }
     }
   }

@@ -961,8 +961,6 @@ template <typename T, int N>
 kfbi_status launch_cols_v(Ctx& c, T* V, const cx<T>* tw, const T* lam, int variant) {
   constexpr int E = default_ept(N);
   constexpr int EH = E / 2;
-  if constexpr (std::is_same<T, float>::value)
-    if (variant & 8) return ypass_rows_f32(c, V);
   const bool small = variant & 1, half = (variant & 2) != 0;
   if (variant & 4) {
     if (half && N / EH <= 512) return launch_ylines<T, N, EH>(c, V, tw, lam);
@@ -976,8 +974,12 @@ kfbi_status launch_cols_v(Ctx& c, T* V, const cx<T>* tw, const T* lam, int varia
   return launch_cols<T, N, E, 512>(c, V, tw, lam);
 }
 
+template <typename T, int N>
+kfbi_status box_after_rows_n(Ctx& c, T* work, const cx<T>* tw, const T* lam);
+
 // Time every variant of both passes on the context's scratch work grid and keep the
-// fastest for this precision.
+// fastest for this precision (a column variant is timed with the row pass that follows
+// it, since the row-layout y-pass hands that pass its own grid).
 template <typename T, int N>
 kfbi_status autotune(Ctx& c, T* V, const cx<T>* tw, const T* lam, int* rows_choice,
                      int* cols_choice) {
@@ -1000,35 +1002,44 @@ kfbi_status autotune(Ctx& c, T* V, const cx<T>* tw, const T* lam, int* rows_choi
     if (ms < best) { best = ms; *rows_choice = v; }
   }
   best = 1e30f;
+  int best_v = 0;
   // FP32 2-D with well-conditioned modes: also the y-pass on the row layout (variant 8)
   const bool rowpass = std::is_same<T, float>::value && c.dim == 2 && c.tri_k0 > 0 && c.tri_k0 < N;
   for (int v : {0, 1, 2, 3, 4, 6, 8}) {
     if (v == 8 && !rowpass) continue;
     float ms = 0.f;
-    KFBI_TRY(time_it([&] { return launch_cols_v<T, N>(c, V, tw, lam, v); }, &ms));
-    if (ms < best) { best = ms; *cols_choice = v; }
+    KFBI_TRY(time_it([&] {
+      *cols_choice = v;
+      return box_after_rows_n<T, N>(c, V, tw, lam);
+    }, &ms));
+    if (ms < best) { best = ms; best_v = v; }
   }
+  *cols_choice = best_v;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return KFBI_OK;
 }
 
+// the box solve after its first row pass: the column pass and the last row pass on work
+// (the row-layout y-pass writes its own grid, which the last row pass reads)
 template <typename T, int N>
-kfbi_status box_solve_n(Ctx& c, const T* rhs, T* work, const cx<T>* tw, const T* lam) {
+kfbi_status box_after_rows_n(Ctx& c, T* work, const cx<T>* tw, const T* lam) {
   const int rv = c.rows_variant[sizeof(T) == 8], cv = c.cols_variant[sizeof(T) == 8];
-  KFBI_TRY((launch_rows_v<T, N>(c, rhs, work, tw, T(1), rv)));
+  if constexpr (std::is_same<T, float>::value)
+    if (cv & 8) {
+      KFBI_TRY(ypass_rows_f32(c, work, ypass_out(c)));
+      return launch_rows_v<T, N>(c, ypass_out(c), work, tw, T(1), rv);
+    }
   KFBI_TRY((launch_cols_v<T, N>(c, work, tw, lam, cv)));
   KFBI_TRY((launch_rows_v<T, N>(c, work, work, tw, T(1), rv)));
   return KFBI_OK;
 }
 
-// the box solve after its first row pass: the column pass and the last row pass on work
 template <typename T, int N>
-kfbi_status box_after_rows_n(Ctx& c, T* work, const cx<T>* tw, const T* lam) {
-  const int rv = c.rows_variant[sizeof(T) == 8], cv = c.cols_variant[sizeof(T) == 8];
-  KFBI_TRY((launch_cols_v<T, N>(c, work, tw, lam, cv)));
-  KFBI_TRY((launch_rows_v<T, N>(c, work, work, tw, T(1), rv)));
-  return KFBI_OK;
+kfbi_status box_solve_n(Ctx& c, const T* rhs, T* work, const cx<T>* tw, const T* lam) {
+  const int rv = c.rows_variant[sizeof(T) == 8];
+  KFBI_TRY((launch_rows_v<T, N>(c, rhs, work, tw, T(1), rv)));
+  return box_after_rows_n<T, N>(c, work, tw, lam);
 }
 
 template <typename T>

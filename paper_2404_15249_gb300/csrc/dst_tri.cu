@@ -175,7 +175,9 @@ int tri_first_mode(const Ctx& c) {
     const double sk = std::sin(M_PI * k / (2.0 * c.N));
     const double mu = 4.0 * sk * sk + h2 * c.kappa2;           // -D h^2 - 2
     const double cst = 2.0 / ((2.0 + mu) + std::sqrt((2.0 + mu) * (2.0 + mu) - 4.0));
-    if (cst <= TRI_CMAX) return k;
+    // rounded up to a multiple of 32: the filter pass then moves whole 128-byte rows of
+    // 32 modes (the extra modes take the transform pair, accurate for every mode)
+    if (cst <= TRI_CMAX) return ((k + 31) / 32) * 32 < c.N ? ((k + 31) / 32) * 32 : c.N;
   }
   return c.N;
 }

@@ -15,66 +15,110 @@
 // coalesced 128-byte segment) and one chunk of MC rows: it runs F+ down from w rows past its
 // chunk (the truncated tail weighs c^w <= 1e-8), keeps the chunk's values in registers,
 // continues F+ over the w rows before the chunk while summing the causal state
-// u_{s-1} = sum_m c^m z_{s-1-m}, then runs F- forward over the chunk.  Low modes (k < k0)
-// are copied out by a narrow transpose, take the sine-transform pair along y (yline_kernel)
-// on a side stream while the filters run, and are copied back.
+// u_{s-1} = sum_m c^m z_{s-1-m}, then runs F- forward over the chunk.  The warm-ups read
+// rows of the neighbouring chunks, which other warps own, so the pass is out of place: it
+// reads V and writes the result grid Y.  Low modes (k < k0) are copied out by a narrow
+// transpose, take the sine-transform pair along y (yline_kernel) on a side stream while
+// the filters run, and are copied into Y.
 #include <cmath>
+#include <cstdint>
 
 #include "kfbi_internal.cuh"
 
 namespace kfbi {
 namespace {
 
-constexpr int YC_W = 97;            // longest warm-up: 0.825^97 < 1e-8
-constexpr int YC_THREADS = 256;     // 8 warps: 8 consecutive chunks of the same 32 modes
+constexpr int YC_W = 97;            // longest warm-up (before rounding up to 16): 0.825^97 < 1e-8
+constexpr int YC_WARPS = 8;         // warps per CTA: 8 consecutive chunks of the same 32 modes
+constexpr int YC_THREADS = 32 * YC_WARPS;
 
-template <int MC>
-__global__ void __launch_bounds__(YC_THREADS)
-    ycol_filter_kernel(float* __restrict__ V, int N, int k0, const float* __restrict__ lam,
-                       float h2, float h2k2, float scale) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int k = k0 + blockIdx.x * 32 + lane;
-  const int s = (blockIdx.y * (YC_THREADS / 32) + warp) * MC;     // first row of the chunk
-  if (s >= N) return;                                              // uniform per warp
-  const bool act = k < N;
-  const int kk = act ? k : N - 1;                                  // idle lanes read a valid column
-  const float mu = 2.f + (h2k2 - h2 * lam[kk]);
-  const float c = 2.f / (mu + sqrtf(fmaf(mu, mu, -4.f)));          // root of c^2 - mu c + 1 in (0, 1)
-  float cw = c;                                                    // the warp's largest c sets w
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) cw = fmaxf(cw, __shfl_xor_sync(0xffffffffu, cw, o));
-  const int w = min(YC_W, (int)ceilf(-18.43f / logf(cw)) + 1);
-  const float* col = V + kk;
+// c of mode k: the root in (0, 1) of c^2 - mu c + 1, mu = 2 + h^2 (kappa^2 - lambda_k)
+__device__ __forceinline__ float filter_c(const float* lam, int k, float h2, float h2k2) {
+  const float mu = 2.f + (h2k2 - h2 * lam[k]);
+  return 2.f / (mu + sqrtf(fmaf(mu, mu, -4.f)));
+}
+
+// The filters of one chunk [s, s + MC) of one mode (column col, coefficient c) with W rows
+// of warm-up each side; INNER: every row read lies in [0, N) (row 0 holds zeros), else rows
+// outside follow the odd 2N-periodic extension (|j| < 2N here, so one shift by 2N and one
+// mirror suffice).  Rows are read in unrolled batches of 16 so that many loads are in
+// flight.  Returns the chunk's solution rows in r.
+template <int MC, bool INNER>
+__device__ __forceinline__ void filter_chunk(const float* __restrict__ col, int N, int s, int W,
+                                             float c, float g, float (&r)[MC]) {
+  constexpr int B = 16;
   const int N2 = 2 * N;
-  auto ext = [&](int j) -> float {                                 // odd 2N-periodic extension
-    int m = j % N2;
-    m += m < 0 ? N2 : 0;
-    if (m == 0 || m == N) return 0.f;
-    return m < N ? col[(size_t)m * N] : -col[(size_t)(N2 - m) * N];
+  auto load = [&](int j) -> float {
+    if constexpr (INNER) {
+      return col[(size_t)j * N];
+    } else {
+      int m = j;
+      m += m < 0 ? N2 : 0;
+      m -= m >= N2 ? N2 : 0;
+      const bool neg = m > N;
+      const int src = neg ? N2 - m : m;
+      const float x = (m != 0 && m != N) ? col[(size_t)src * N] : 0.f;
+      return neg ? -x : x;
+    }
   };
   const int e = s + MC;
   float z = 0.f;
-  for (int j = e + w - 1; j >= e; --j) z = fmaf(c, z, ext(j));     // F+ warm-up
-  float r[MC];
+  for (int jb = e + W - B; jb >= e; jb -= B) {                     // F+ warm-up, far end first
+    float x[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) x[u] = load(jb + u);
+#pragma unroll
+    for (int u = B - 1; u >= 0; --u) z = fmaf(c, z, x[u]);
+  }
+#pragma unroll
+  for (int i = 0; i < MC; ++i) r[i] = col[(size_t)(s + i) * N];
 #pragma unroll
   for (int i = MC - 1; i >= 0; --i) {                              // F+ over the chunk
-    z = fmaf(c, z, col[(size_t)(s + i) * N]);
+    z = fmaf(c, z, r[i]);
     r[i] = z;
   }
   float u = 0.f, p = 1.f;                                          // causal state entering s
-  for (int j = s - 1; j >= s - w; --j) {
-    z = fmaf(c, z, ext(j));
-    u = fmaf(p, z, u);
-    p *= c;
+  for (int jb = s - B; jb >= s - W; jb -= B) {
+    float x[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) x[q] = load(jb + q);
+#pragma unroll
+    for (int q = B - 1; q >= 0; --q) {
+      z = fmaf(c, z, x[q]);
+      u = fmaf(p, z, u);
+      p *= c;
+    }
   }
-  const float g = -c * h2 * scale;
 #pragma unroll
   for (int i = 0; i < MC; ++i) {                                   // F- over the chunk
     u = fmaf(c, u, r[i]);
     r[i] = u * g;
   }
+}
+
+// Warp w of CTA (g, b) owns modes k0 + 32 g + lane and chunk b YC_WARPS + w of MC rows; W
+// comes from the group's lowest mode, whose c is the largest, rounded up to a multiple of
+// 16.  Every access is one coalesced 128-byte row segment (the group's 32 modes; k0 is a
+// multiple of 32).
+template <int MC>
+__global__ void __launch_bounds__(YC_THREADS)
+    ycol_filter_kernel(const float* __restrict__ V, float* __restrict__ Y, int N, int k0,
+                       const float* __restrict__ lam, float h2, float h2k2, float scale) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int kb = k0 + blockIdx.x * 32;
+  const int k = kb + lane;
+  const int s = (blockIdx.y * YC_WARPS + warp) * MC;               // first row of the chunk
+  if (s >= N) return;                                              // uniform per warp
+  const bool act = k < N;
+  const int kk = act ? k : N - 1;                                  // idle lanes read a valid column
+  const int W = (min(YC_W, (int)ceilf(-18.43f / logf(filter_c(lam, kb, h2, h2k2))) + 1) + 15) / 16 * 16;
+  const float c = filter_c(lam, kk, h2, h2k2);
+  const float g = -c * h2 * scale;
+  float r[MC];
+  if (s - W >= 0 && s + MC + W <= N) filter_chunk<MC, true>(V + kk, N, s, W, c, g, r);
+  else filter_chunk<MC, false>(V + kk, N, s, W, c, g, r);
   if (!act) return;
-  float* out = V + k;
+  float* out = Y + k;
 #pragma unroll
   for (int i = 0; i < MC; ++i) out[(size_t)(s + i) * N] = (s + i == 0) ? 0.f : r[i];
 }
@@ -97,12 +141,12 @@ __global__ void transpose_block_kernel(const float* __restrict__ in, int ld_in,
 }
 
 template <int MC>
-kfbi_status launch_filter(Ctx& c, float* V, int k0) {
+kfbi_status launch_filter(Ctx& c, const float* V, float* Y, int k0) {
   const int N = c.N;
-  const dim3 grid((N - k0 + 31) / 32, (N / MC + YC_THREADS / 32 - 1) / (YC_THREADS / 32));
+  const dim3 grid((N - k0 + 31) / 32, (N + YC_WARPS * MC - 1) / (YC_WARPS * MC));
   const int pr = prof_begin(c, ST_TRI);
   ycol_filter_kernel<MC><<<grid, YC_THREADS, 0, c.stream>>>(
-      V, N, k0, c.t32.lam, (float)(c.h * c.h), (float)(c.h * c.h * c.kappa2), (float)(2.0 / N));
+      V, Y, N, k0, c.t32.lam, (float)(c.h * c.h), (float)(c.h * c.h * c.kappa2), (float)(2.0 / N));
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
@@ -120,12 +164,12 @@ kfbi_status transpose_block(Ctx& c, const float* in, int ld_in, float* out, int 
 
 }  // namespace
 
-// the y-pass of the FP32 2-D box solve on V in place (row layout); the low modes k < tri_k0
-// run the transform pair in the context's transposed scratch on the side stream
-kfbi_status ypass_rows_f32(Ctx& c, float* V) {
+// the y-pass of the FP32 2-D box solve from V into Y (row layout, Y != V); the low modes
+// k < tri_k0 run the transform pair in the context's transposed scratch on the side stream
+kfbi_status ypass_rows_f32(Ctx& c, const float* V, float* Y) {
   const int N = c.N, k0 = c.tri_k0;
-  if (k0 <= 0 || k0 >= N) {
-    set_error("row-layout y-pass: no well-conditioned modes at N = %d", N);
+  if (k0 <= 0 || k0 >= N || k0 % 32 != 0 || N % 32 != 0) {
+    set_error("row-layout y-pass: needs 0 < k0 < N, both multiples of 32 (N = %d, k0 = %d)", N, k0);
     return KFBI_ERR_UNSUPPORTED;
   }
   float* L = reinterpret_cast<float*>(c.XT);                       // k0 x N low-mode lines
@@ -136,14 +180,14 @@ kfbi_status ypass_rows_f32(Ctx& c, float* V) {
   c.stream = c.side;                                               // launches go to the side stream
   kfbi_status st = transpose_block(c, V, N, L, N, N, k0);          // L[k][j] = V[j][k]
   if (st == KFBI_OK) st = ylines_f32_lines(c, L, k0);
-  if (st == KFBI_OK) st = transpose_block(c, L, N, V, N, k0, N);   // V[j][k] = L[k][j]
+  if (st == KFBI_OK) st = transpose_block(c, L, N, Y, N, k0, N);   // Y[j][k] = L[k][j]
   c.stream = main_st;
   KFBI_TRY(st);
   KFBI_CUDA_TRY(cudaEventRecord(c.join_ev, c.side));
   // the well-conditioned modes on the main stream, concurrently
-  if (N >= 1024) KFBI_TRY(launch_filter<64>(c, V, k0));
-  else if (N >= 256) KFBI_TRY(launch_filter<32>(c, V, k0));
-  else KFBI_TRY(launch_filter<16>(c, V, k0));
+  if (N >= 1024) KFBI_TRY(launch_filter<64>(c, V, Y, k0));
+  else if (N >= 256) KFBI_TRY(launch_filter<32>(c, V, Y, k0));
+  else KFBI_TRY(launch_filter<16>(c, V, Y, k0));
   KFBI_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev, 0));      // join
   return KFBI_OK;
 }

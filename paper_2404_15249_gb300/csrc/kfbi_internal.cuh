@@ -227,9 +227,11 @@ kfbi_status x_pass_f32(Ctx& c, const float* X, float* V);
 kfbi_status ylines_f32_lines(Ctx& c, float* X, int nlines);
 // FP32 2-D: the box solve after its first row pass (column pass variant + last row pass)
 kfbi_status box_solve_after_rows_f32(Ctx& c, float* work);
-// FP32 2-D y-pass on the row layout: recursive filters for the modes k >= tri_k0, the
-// transform pair (side stream) for the others (dst_ycol.cu)
-kfbi_status ypass_rows_f32(Ctx& c, float* V);
+// FP32 2-D y-pass on the row layout from V into Y (Y != V): recursive filters for the
+// modes k >= tri_k0, the transform pair (side stream) for the others (dst_ycol.cu); its
+// result grid is ypass_out(c), the second half of the transposed scratch XT
+kfbi_status ypass_rows_f32(Ctx& c, const float* V, float* Y);
+inline float* ypass_out(Ctx& c) { return reinterpret_cast<float*>(c.XT) + (size_t)c.N * c.N; }
 kfbi_status init_box_tables(Ctx& c);
 kfbi_status autotune_f32(Ctx& c);   // column-pass variant per precision, on scratch grids
 kfbi_status autotune_f64(Ctx& c);
