@@ -51,11 +51,17 @@ static void free_handle(kfbi_ctx_s* hd) {
     cudaFree(c.basis); cudaFree(c.hess); cudaFree(c.givens); cudaFree(c.gvec);
     cudaFree(c.hcol); cudaFree(c.yvec); cudaFree(c.gm_part); cudaFree(c.gm_counter);
   }
+  kfbi::drop_step_graphs(c);
+  if (c.gm_j) cudaFree(c.gm_j);
   if (c.h_pinned) cudaFreeHost(c.h_pinned);
   kfbi::free_tc(c);
   for (int i = 0; i < 2; ++i)
     if (c.gm_ev[i]) cudaEventDestroy(c.gm_ev[i]);
+  if (c.own) cudaStreamSynchronize(c.own);
   if (c.fork_ev) cudaEventDestroy(c.fork_ev);
+  if (c.own_in) cudaEventDestroy(c.own_in);
+  if (c.own_out) cudaEventDestroy(c.own_out);
+  if (c.own) cudaStreamDestroy(c.own);
   if (c.join_ev) cudaEventDestroy(c.join_ev);
   if (c.side) cudaStreamDestroy(c.side);
   delete hd;
@@ -133,6 +139,9 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
   c.stream = (cudaStream_t)stream;
   c.plan = plan;
   c.dim = dim;
+  // KFBI_GRAPHS=0: the Arnoldi steps are launched kernel by kernel instead of as graphs
+  if (const char* e = std::getenv("KFBI_GRAPHS"))
+    if (e[0] == '0') c.graphs_ok = false;
   // KFBI_TEST_POLL_LIMIT (tests of the failure path only): polls of a staged-copy wait
   // before it records a timeout; 0 makes every such wait give up at once
   if (const char* e = std::getenv("KFBI_TEST_POLL_LIMIT")) {
@@ -156,8 +165,11 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
   } while (0)
   SETUP_TRY(kfbi::alloc_bytes(c, (void**)&c.err_flag, sizeof(int) * 4));
   if (cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c.own, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c.fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c.join_ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c.join_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c.own_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c.own_out, cudaEventDisableTiming) != cudaSuccess) {
     kfbi::set_error("kfbi_setup: stream or event creation failed");
     free_handle(hd);
     return KFBI_ERR_CUDA;

@@ -43,27 +43,32 @@ constexpr int DOT_T = 256;
 
 static inline int dot_blocks(int M) { return (M + DOT_CHUNK - 1) / DOT_CHUNK; }
 
+// With jp (the Arnoldi step index in device memory, so that one captured launch serves
+// every step) nb = *jp + 1 and the grid covers the largest nb: blocks b >= nb only count.
 __global__ void __launch_bounds__(DOT_T) multidot_kernel(const double* __restrict__ V, int ld,
-                                                         int M, int nb,
+                                                         int M, int nb, const int* jp,
                                                          const double* __restrict__ w,
                                                          double* part, int pld,
                                                          unsigned* counter,
                                                          double* __restrict__ h) {
   __shared__ double sh[32];
   __shared__ bool last;
+  if (jp) nb = *jp + 1;
   const int b = blockIdx.y, x0 = blockIdx.x * DOT_CHUNK;
-  const double* v = V + (size_t)b * ld;
-  double a[DOT_CHUNK / DOT_T];
+  if (b < nb) {
+    const double* v = V + (size_t)b * ld;
+    double a[DOT_CHUNK / DOT_T];
 #pragma unroll
-  for (int q = 0; q < DOT_CHUNK / DOT_T; ++q) {
-    const int x = x0 + threadIdx.x + q * DOT_T;
-    a[q] = x < M ? v[x] * w[x] : 0.0;
+    for (int q = 0; q < DOT_CHUNK / DOT_T; ++q) {
+      const int x = x0 + threadIdx.x + q * DOT_T;
+      a[q] = x < M ? v[x] * w[x] : 0.0;
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < DOT_CHUNK / DOT_T; ++q) t += a[q];
+    t = block_sum(t, sh);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * pld + b] = t;
   }
-  double t = 0.0;
-#pragma unroll
-  for (int q = 0; q < DOT_CHUNK / DOT_T; ++q) t += a[q];
-  t = block_sum(t, sh);
-  if (threadIdx.x == 0) part[(size_t)blockIdx.x * pld + b] = t;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1;
@@ -81,12 +86,14 @@ __global__ void __launch_bounds__(DOT_T) multidot_kernel(const double* __restric
 // w += sign * sum_{b < cnt} h[b] V_b  (coefficients staged in shared memory, eight
 // independent loads in flight per thread).  With nrm_out: also ||w||_2 of the updated w,
 // from per-block partial sums added in block order by the last block to finish.
+// (cnt = *jp + 1 when jp is given: the Arnoldi step index in device memory)
 __global__ void mv_update_kernel(double* __restrict__ w, const double* __restrict__ V, int ld,
-                                 int M, const double* __restrict__ h, int cnt, double sign,
-                                 double* part, unsigned* counter, double* nrm_out) {
+                                 int M, const double* __restrict__ h, int cnt, const int* jp,
+                                 double sign, double* part, unsigned* counter, double* nrm_out) {
   extern __shared__ double hs[];
   __shared__ double sh[32];
   __shared__ bool last;
+  if (jp) cnt = *jp + 1;
   for (int b = threadIdx.x; b < cnt; b += blockDim.x) hs[b] = h[b];
   __syncthreads();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -144,15 +151,23 @@ __global__ void scale_kernel(double* dst, const double* src, int M, const double
   if (x < M) dst[x] = src[x] / scal[slot];
 }
 
-// Start of a cycle: V_0 = r / beta, g = beta e_1.  scal: [0] |g_{j+1}|, [1] breakdown,
-// [2] beta, [3] NaN seen.
-__global__ void cycle_start_kernel(double* V0, const double* r, int M, double* gvec, int m,
-                                   double* scal) {
+// Start of a cycle: V_0 = r / beta (also into vin, the input of the next apply), g = beta
+// e_1, step index 0.  scal: [0] |g_{j+1}|, [1] breakdown, [2] beta, [3] NaN seen.
+__global__ void cycle_start_kernel(double* V0, double* vin, const double* r, int M, double* gvec,
+                                   int m, double* scal, int* jp) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const double beta = scal[2];
-  if (x < M) V0[x] = r[x] / beta;
+  if (x < M) {
+    const double v = r[x] / beta;
+    V0[x] = v;
+    vin[x] = v;
+  }
   if (x <= m) gvec[x] = (x == 0) ? beta : 0.0;
+  if (x == 0) *jp = 0;
 }
+
+// next Arnoldi step
+__global__ void advance_kernel(int* jp) { *jp += 1; }
 
 // Finish Arnoldi step j (nrm = ||w||, formed by the second update): V_{j+1} = w / nrm
 // by every block; block 0 also forms column j of the Hessenberg matrix (h1 + h2 from the
@@ -160,16 +175,24 @@ __global__ void cycle_start_kernel(double* V0, const double* r, int M, double* g
 // and updates the least-squares right-hand side g.  The column and the rotations are
 // staged in shared memory (dynamic: (m + 1) + 2m doubles) so the sequential rotation loop
 // runs on shared-memory operands.
-__global__ void finish_kernel(int j, int m, int M, const double* __restrict__ w, double* V, int ld,
-                              const double* __restrict__ h1, const double* __restrict__ h2,
+// The step index j is read from device memory (jp); the flags scal[0..3] of the step are
+// also written into host-mapped memory flags[4 (j mod 2) + 0..3] for the host to read one
+// step behind, and V_{j+1} into vin, the input of the next apply.
+__global__ void finish_kernel(const int* jp, int m, int M, const double* __restrict__ w, double* V,
+                              int ld, const double* __restrict__ h1, const double* __restrict__ h2,
                               const double* __restrict__ nrm_in, double* hess, double* giv,
-                              double* gvec, double* scal) {
+                              double* gvec, double* scal, double* vin, double* flags) {
   extern __shared__ double dyn[];
+  const int j = *jp;
   const double nrm = *nrm_in;
   const double beta = scal[2];
   const bool breakdown = !(nrm > 1e-14 * beta);
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (!breakdown && x < M) V[(size_t)(j + 1) * ld + x] = w[x] / nrm;
+  if (!breakdown && x < M) {
+    const double v = w[x] / nrm;
+    V[(size_t)(j + 1) * ld + x] = v;
+    vin[x] = v;
+  }
   if (blockIdx.x != 0) return;
   double* col = dyn;                 // m + 1
   double* gs = dyn + (m + 1);        // 2m
@@ -196,6 +219,12 @@ __global__ void finish_kernel(int j, int m, int M, const double* __restrict__ w,
     scal[0] = fabs(sn * gj);
     scal[1] = breakdown ? 1.0 : 0.0;
     scal[3] = (isfinite(nrm) && isfinite(den)) ? 0.0 : 1.0;
+    double* f = flags + 4 * (j & 1);
+    f[0] = scal[0];
+    f[1] = scal[1];
+    f[2] = scal[2];
+    f[3] = scal[3];
+    __threadfence_system();
   }
   __syncthreads();
   double* hc = hess + (size_t)j * (m + 1);
@@ -238,8 +267,23 @@ struct Counters {
 
 static inline int vb(int M) { return (M + 255) / 256; }
 
+void drop_step_graphs(Ctx& c) {
+  for (int p = 0; p < kStepGraphs; ++p)
+    if (c.step_exec[p]) {
+      cudaGraphExecDestroy(c.step_exec[p]);
+      c.step_exec[p] = nullptr;
+    }
+}
+
 kfbi_status alloc_gmres(Ctx& c, int m) {
+  if (!c.gm_j) KFBI_CUDA_TRY(cudaMalloc((void**)&c.gm_j, sizeof(int)));
+  if (!c.d_flags) {
+    void* p = nullptr;
+    KFBI_CUDA_TRY(cudaHostGetDevicePointer(&p, c.h_pinned, 0));
+    c.d_flags = static_cast<double*>(p) + 8;
+  }
   if (c.gm_m >= m && c.basis) return KFBI_OK;
+  drop_step_graphs(c);           // captured with the old workspace
   if (c.basis) {
     cudaFree(c.basis); cudaFree(c.hess); cudaFree(c.givens); cudaFree(c.gvec);
     cudaFree(c.hcol); cudaFree(c.yvec); cudaFree(c.gm_part); cudaFree(c.gm_counter);
@@ -274,11 +318,9 @@ static kfbi_status read_scal(Ctx& c, int n) {
   return KFBI_OK;
 }
 
-// Arnoldi-step flags through two pinned slots (h_pinned[8..11], [12..15]) and two events
+// Arnoldi-step flags through two host-mapped slots (h_pinned[8..11], [12..15], written by
+// finish_kernel) and two events
 static kfbi_status post_flags(Ctx& c, int j) {
-  double* slot = c.h_pinned + 8 + 4 * (j & 1);
-  KFBI_CUDA_TRY(cudaMemcpyAsync(slot, c.scal, sizeof(double) * 4, cudaMemcpyDeviceToHost,
-                                c.stream));
   KFBI_CUDA_TRY(cudaEventRecord(c.gm_ev[j & 1], c.stream));
   return KFBI_OK;
 }
@@ -298,6 +340,80 @@ struct Relax {
   int pick(double est) const { return est > th[0] ? tier[0] : (est > th[1] ? tier[1] : tier[2]); }
 };
 
+// One Arnoldi step with the matvec in precision `prec`: the apply of vin (V_j) into w, the
+// two classical Gram-Schmidt passes against V_0..V_j, the normalisation into V_{j+1} (and
+// vin) with the Givens update, and the step index advance.  j lives in device memory, so
+// this launch sequence is the same at every step.
+static kfbi_status arnoldi_step(Ctx& c, int prec) {
+  const int M = c.M, m = c.opt.gmres_m;
+  cudaStream_t st = c.stream;
+  double* w = c.vecs + M;
+  double* vin = c.vecs + 6 * M;
+  double* h1 = c.hcol;
+  double* h2 = c.hcol + (m + 1);
+  KFBI_TRY(apply_potential(c, Layer::Double, prec, vin, w));
+  const int pk = prof_begin(c, ST_KRYLOV);
+  prof_count(c, ST_KRYLOV, 5);
+  const size_t hsm = sizeof(double) * (m + 1);
+  const dim3 dg(dot_blocks(M), m + 1);
+  multidot_kernel<<<dg, DOT_T, 0, st>>>(c.basis, M, M, 0, c.gm_j, w, c.gm_part, m + 1,
+                                        c.gm_counter, h1);
+  mv_update_kernel<<<vb(M), 256, hsm, st>>>(w, c.basis, M, M, h1, 0, c.gm_j, -1.0, nullptr,
+                                            nullptr, nullptr);
+  multidot_kernel<<<dg, DOT_T, 0, st>>>(c.basis, M, M, 0, c.gm_j, w, c.gm_part, m + 1,
+                                        c.gm_counter, h2);
+  mv_update_kernel<<<vb(M), 256, hsm, st>>>(w, c.basis, M, M, h2, 0, c.gm_j, -1.0, c.gm_part,
+                                            c.gm_counter, c.scal + 5);
+  finish_kernel<<<vb(M), 256, sizeof(double) * (3 * m + 1), st>>>(
+      c.gm_j, m, M, w, c.basis, M, h1, h2, c.scal + 5, c.hess, c.givens, c.gvec, c.scal, vin,
+      c.d_flags);
+  advance_kernel<<<1, 1, 0, st>>>(c.gm_j);
+  prof_end(c, pk);
+  KFBI_CUDA_TRY(cudaGetLastError());
+  return KFBI_OK;
+}
+
+// The Arnoldi step as one CUDA graph per matvec precision, captured on first use (the
+// kernels and their arguments are the same at every step of every cycle of this context),
+// launched with one call; direct launches while the stage timers run or if capture is not
+// possible.  A graph's kernel launches are added to the launch counters at every replay.
+static kfbi_status launch_step(Ctx& c, int prec) {
+  if (c.prof.on || !c.graphs_ok || prec < 0 || prec >= kStepGraphs) return arnoldi_step(c, prec);
+  if (c.graph_m != c.opt.gmres_m) {   // captured with another restart length
+    drop_step_graphs(c);
+    c.graph_m = c.opt.gmres_m;
+  }
+  if (!c.step_exec[prec]) {
+    long long before[KFBI_NSTAGES];
+    for (int s = 0; s < KFBI_NSTAGES; ++s) before[s] = c.prof.launches[s];
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      c.graphs_ok = false;
+      return arnoldi_step(c, prec);
+    }
+    const kfbi_status body = arnoldi_step(c, prec);
+    const cudaError_t ec = cudaStreamEndCapture(c.stream, &g);
+    for (int s = 0; s < KFBI_NSTAGES; ++s) {   // captured, not run: counted per replay
+      c.step_launches[prec][s] = c.prof.launches[s] - before[s];
+      c.prof.launches[s] = before[s];
+    }
+    cudaGraphExec_t ex = nullptr;
+    const bool ok = body == KFBI_OK && ec == cudaSuccess && g &&
+                    cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {                   // nothing ran: take the step with direct launches
+      cudaGetLastError();
+      c.graphs_ok = false;
+      return arnoldi_step(c, prec);
+    }
+    c.step_exec[prec] = ex;
+  }
+  KFBI_CUDA_TRY(cudaGraphLaunch(c.step_exec[prec], c.stream));
+  for (int s = 0; s < KFBI_NSTAGES; ++s) c.prof.launches[s] += c.step_launches[prec][s];
+  return KFBI_OK;
+}
+
 // GMRES(m) on K_D for rhs, x in/out (x_zero: start from 0), FP64 Arnoldi, matvec
 // precision chosen per step by `relax`.  Every cycle ends with the true residual formed
 // with the FP64-accurate apply prec_true (an iterative-refinement step).  Stops when the
@@ -308,10 +424,7 @@ static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const do
   const int M = c.M, m = c.opt.gmres_m;   // workspace is sized for c.gm_m >= m
   cudaStream_t st = c.stream;
   double* r = c.vecs;            // residual
-  double* w = c.vecs + M;        // Krylov image
   double* tmp = c.vecs + 2 * M;
-  double* h1 = c.hcol;
-  double* h2 = c.hcol + (m + 1);
   if (x_zero) {
     KFBI_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * M, st));
     KFBI_CUDA_TRY(cudaMemcpyAsync(r, rhs, sizeof(double) * M, cudaMemcpyDeviceToDevice, st));
@@ -331,7 +444,8 @@ static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const do
   int cyc = 0;
   for (; cyc < max_cycles && beta > tol_abs; ++cyc) {
     prof_count(c, ST_KRYLOV);
-    cycle_start_kernel<<<vb(M > m + 1 ? M : m + 1), 256, 0, st>>>(c.basis, r, M, c.gvec, m, c.scal);
+    cycle_start_kernel<<<vb(M > m + 1 ? M : m + 1), 256, 0, st>>>(c.basis, c.vecs + 6 * M, r, M,
+                                                                   c.gvec, m, c.scal, c.gm_j);
     // The host runs one Arnoldi step ahead of the device: the flags of step j (residual
     // estimate, breakdown, NaN) are copied to a pinned slot behind step j's kernels and
     // read only after step j + 1 has been enqueued, so the device never idles on a host
@@ -345,26 +459,10 @@ static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const do
     int pending = -1;
     for (int j = 0; j < m; ++j) {
       const int prec = relax.pick(est);
-      KFBI_TRY(apply_K(c, prec, c.basis + (size_t)j * M, w, cnt));
+      if (prec == KFBI_MIXED_FP32 || prec == KFBI_TF32X3) ++cnt.applies32;
+      else ++cnt.applies64;   // FP64-accurate
+      KFBI_TRY(launch_step(c, prec));
       ++cnt.iters;
-      const int pk = prof_begin(c, ST_KRYLOV);
-      {
-        prof_count(c, ST_KRYLOV, 4);
-        const size_t hsm = sizeof(double) * (j + 1);
-        const dim3 dg(dot_blocks(M), j + 1);
-        multidot_kernel<<<dg, DOT_T, 0, st>>>(c.basis, M, M, j + 1, w, c.gm_part, m + 1,
-                                              c.gm_counter, h1);
-        mv_update_kernel<<<vb(M), 256, hsm, st>>>(w, c.basis, M, M, h1, j + 1, -1.0, nullptr,
-                                                  nullptr, nullptr);
-        multidot_kernel<<<dg, DOT_T, 0, st>>>(c.basis, M, M, j + 1, w, c.gm_part, m + 1,
-                                              c.gm_counter, h2);
-        mv_update_kernel<<<vb(M), 256, hsm, st>>>(w, c.basis, M, M, h2, j + 1, -1.0,
-                                                  c.gm_part, c.gm_counter, c.scal + 5);
-        finish_kernel<<<vb(M), 256, sizeof(double) * (3 * m + 1), st>>>(
-            j, m, M, w, c.basis, M, h1, h2, c.scal + 5, c.hess, c.givens, c.gvec, c.scal);
-      }
-      prof_end(c, pk);
-      KFBI_CUDA_TRY(cudaGetLastError());
       KFBI_TRY(post_flags(c, j));
       k = j + 1;
       if (pending >= 0) {
@@ -397,8 +495,9 @@ static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const do
     const size_t lsm = sizeof(double) * (size_t)k * (k + 1);
     const bool staged = lsm <= 48 * 1024;
     lsq_kernel<<<1, 256, staged ? lsm : 0, st>>>(k, m, c.hess, c.gvec, c.yvec, staged ? 1 : 0);
-    mv_update_kernel<<<vb(M), 256, sizeof(double) * k, st>>>(x, c.basis, M, M, c.yvec, k, 1.0,
-                                                            nullptr, nullptr, nullptr);
+    mv_update_kernel<<<vb(M), 256, sizeof(double) * k, st>>>(x, c.basis, M, M, c.yvec, k,
+                                                            nullptr, 1.0, nullptr, nullptr,
+                                                            nullptr);
     KFBI_CUDA_TRY(cudaGetLastError());
     KFBI_TRY(apply_K(c, prec_true, x, tmp, cnt));
     prof_count(c, ST_KRYLOV, 2);
@@ -416,8 +515,31 @@ static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const do
   return KFBI_OK;
 }
 
+static kfbi_status solve_bvp_on(Ctx& c, const double* f_grid, const double* f_ctrl,
+                                const double* g_ctrl, double* u_grid, double* dens_out,
+                                kfbi_solve_info* info);
+
+// The solve runs on the context's own non-blocking stream (the captured Arnoldi-step graphs
+// need a stream that can be captured; the legacy default stream cannot), joined to the
+// caller's stream at both ends: it starts after the work already queued there, and the
+// caller's stream waits for it.
 kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const double* g_ctrl,
                       double* u_grid, double* dens_out, kfbi_solve_info* info) {
+  const cudaStream_t caller = c.stream;
+  if (!c.own) return solve_bvp_on(c, f_grid, f_ctrl, g_ctrl, u_grid, dens_out, info);
+  KFBI_CUDA_TRY(cudaEventRecord(c.own_in, caller));
+  KFBI_CUDA_TRY(cudaStreamWaitEvent(c.own, c.own_in, 0));
+  c.stream = c.own;
+  const kfbi_status s = solve_bvp_on(c, f_grid, f_ctrl, g_ctrl, u_grid, dens_out, info);
+  c.stream = caller;
+  KFBI_CUDA_TRY(cudaEventRecord(c.own_out, c.own));
+  KFBI_CUDA_TRY(cudaStreamWaitEvent(caller, c.own_out, 0));
+  return s;
+}
+
+static kfbi_status solve_bvp_on(Ctx& c, const double* f_grid, const double* f_ctrl,
+                                const double* g_ctrl, double* u_grid, double* dens_out,
+                                kfbi_solve_info* info) {
   const int M = c.M;
   cudaStream_t st = c.stream;
   KFBI_TRY(alloc_gmres(c, c.opt.gmres_m));

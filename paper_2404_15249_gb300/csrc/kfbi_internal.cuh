@@ -98,6 +98,8 @@ struct Prof {
 };
 
 // ------------------------------------------------------------------ context
+constexpr int kStepGraphs = 5;   // precisions KFBI_FP64 .. KFBI_TF32X3
+
 struct Ctx {
   // problem (dim 2: M control points on a curve; dim 3: M grid-line intersection points)
   int dim = 2;
@@ -106,6 +108,8 @@ struct Ctx {
   kfbi_options opt{};
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;              // second stream of the row-layout y-pass
+  cudaStream_t own = nullptr;               // the context's stream for BVP solves
+  cudaEvent_t own_in = nullptr, own_out = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   FftPlan plan{};
 
@@ -191,7 +195,14 @@ struct Ctx {
   double* vecs = nullptr;      // 6 x M scratch vectors
   double* yvec = nullptr;      // m
   double* h_pinned = nullptr;  // pinned host mirror of scal (16 doubles)
-  cudaEvent_t gm_ev[2] = {nullptr, nullptr};   // Arnoldi-step flag copies done
+  cudaEvent_t gm_ev[2] = {nullptr, nullptr};   // Arnoldi steps done (their flags written)
+  int* gm_j = nullptr;         // Arnoldi step index within the cycle (device)
+  double* d_flags = nullptr;   // device address of h_pinned + 8 (host-mapped flag slots)
+  // one captured CUDA graph per matvec precision for the whole Arnoldi step
+  cudaGraphExec_t step_exec[kStepGraphs] = {};
+  long long step_launches[kStepGraphs][KFBI_NSTAGES] = {};
+  bool graphs_ok = true;       // false: direct launches (KFBI_GRAPHS=0, or capture failed)
+  int graph_m = 0;             // restart length the graphs were captured with
   double* gm_part = nullptr;       // per-block partial dot products
   unsigned* gm_counter = nullptr;  // blocks done in the current multi-dot
   int* err_flag = nullptr;     // device error flags: [0] geometry, [2] bounded wait expired
@@ -277,6 +288,7 @@ kfbi_status inside_mask3(Ctx& c, uint8_t* mask);
 kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const double* g_ctrl,
                       double* u_grid, double* dens_out, kfbi_solve_info* info);
 kfbi_status alloc_gmres(Ctx& c, int m);
+void drop_step_graphs(Ctx& c);   // the captured Arnoldi-step graphs (recaptured on use)
 kfbi_status batch_solve(kfbi_ctx* ctxs, int count, int nrhs, const double* const* f_grid,
                         const double* const* f_ctrl, const double* const* g_ctrl,
                         double* const* u_grid, double* const* dens_out, kfbi_solve_info* info,
