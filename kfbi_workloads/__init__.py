@@ -106,36 +106,44 @@ def ellipse(M: int, a: float = 0.7, b: float = 0.4, rot_deg: float = 30.0, cente
 # ---------------------------------------------------------------- manufactured solutions
 @dataclass
 class Manufactured:
-    """u(x, y) and f = Lap(u) - kappa^2 u, both vectorised over numpy arrays."""
+    """u(x, y) and f = Lap(u) - kappa^2 u, both vectorised over numpy arrays; grad(x, y)
+    returns (u_x, u_y) (the Neumann data of the Neumann BVP)."""
     u: callable
     f: callable
     name: str
     kappa: float
+    grad: callable = None
 
 
 def manufactured_sinpi(kappa: float = 0.0) -> Manufactured:
     """u = sin(pi x) cos(pi y); f = -(2 pi^2 + kappa^2) u."""
     u = lambda x, y: np.sin(np.pi * x) * np.cos(np.pi * y)
-    return Manufactured(u, lambda x, y: -(2 * np.pi ** 2 + kappa ** 2) * u(x, y), "sinpi", kappa)
+    g = lambda x, y: (np.pi * np.cos(np.pi * x) * np.cos(np.pi * y),
+                      -np.pi * np.sin(np.pi * x) * np.sin(np.pi * y))
+    return Manufactured(u, lambda x, y: -(2 * np.pi ** 2 + kappa ** 2) * u(x, y), "sinpi", kappa, g)
 
 
 def manufactured_exp_sin2y(kappa: float) -> Manufactured:
     """u = exp(x) sin(2y); Lap u = (1 - 4) u, so f = -(3 + kappa^2) u."""
     u = lambda x, y: np.exp(x) * np.sin(2 * y)
-    return Manufactured(u, lambda x, y: -(3.0 + kappa ** 2) * u(x, y), "exp_sin2y", kappa)
+    g = lambda x, y: (np.exp(x) * np.sin(2 * y), 2.0 * np.exp(x) * np.cos(2 * y))
+    return Manufactured(u, lambda x, y: -(3.0 + kappa ** 2) * u(x, y), "exp_sin2y", kappa, g)
 
 
 def manufactured_sincos(w1: float, w2: float, kappa: float) -> Manufactured:
     """u = sin(w1 x) cos(w2 y); f = -(w1^2 + w2^2 + kappa^2) u."""
     u = lambda x, y: np.sin(w1 * x) * np.cos(w2 * y)
+    g = lambda x, y: (w1 * np.cos(w1 * x) * np.cos(w2 * y), -w2 * np.sin(w1 * x) * np.sin(w2 * y))
     return Manufactured(u, lambda x, y: -(w1 * w1 + w2 * w2 + kappa ** 2) * u(x, y),
-                        f"sincos({w1:.3f},{w2:.3f})", kappa)
+                        f"sincos({w1:.3f},{w2:.3f})", kappa, g)
 
 
 def manufactured_harmonic_ctx() -> Manufactured:
     """u = e^x cos y + e^y sin x (harmonic, kappa = 0)."""
     u = lambda x, y: np.exp(x) * np.cos(y) + np.exp(y) * np.sin(x)
-    return Manufactured(u, lambda x, y: 0.0 * x, "exp_harmonic", 0.0)
+    g = lambda x, y: (np.exp(x) * np.cos(y) + np.exp(y) * np.cos(x),
+                      -np.exp(x) * np.sin(y) + np.exp(y) * np.sin(x))
+    return Manufactured(u, lambda x, y: 0.0 * x, "exp_harmonic", 0.0, g)
 
 
 def grid_nodes(N: int, lo: float = -1.0, hi: float = 1.0):
@@ -171,6 +179,12 @@ class Problem:
     def g_ctrl(self) -> np.ndarray:
         p = self.iface.pts
         return self.sol.u(p[:, 0], p[:, 1])
+
+    def gn_ctrl(self) -> np.ndarray:
+        """Neumann data d_n u = grad u . n at the control points (outward normals)."""
+        p, n = self.iface.pts, self.iface.normals
+        gx, gy = self.sol.grad(p[:, 0], p[:, 1])
+        return gx * n[:, 0] + gy * n[:, 1]
 
 
 def config_poisson_flower(N: int = 128, M: int = 256) -> Problem:

@@ -21,10 +21,14 @@ to second-order convergence on manufactured solutions; error_norms to hand-compu
 from .kfbi2d import (GeometryError, Geometry2D, jumps_cartesian, box_solve_dst,
                      box_solve_dense, correct_rhs, interpolate_plus, apply_interface,
                      apply_double_layer, apply_volume, combined_grid_solution, gmres,
-                     richardson, solve_bvp, error_norms, lagrange_basis)
+                     richardson, solve_bvp, error_norms, lagrange_basis,
+                     interpolate_plus_grad, apply_interface_dn, apply_single_layer,
+                     apply_single_layer_dn, apply_volume_dn, solve_neumann_bvp)
 
 __all__ = ["GeometryError", "Geometry2D", "jumps_cartesian", "box_solve_dst",
            "box_solve_dense", "correct_rhs", "interpolate_plus", "apply_interface",
            "apply_double_layer", "apply_volume", "combined_grid_solution", "gmres",
-           "richardson", "solve_bvp", "error_norms", "lagrange_basis"]
+           "richardson", "solve_bvp", "error_norms", "lagrange_basis",
+           "interpolate_plus_grad", "apply_interface_dn", "apply_single_layer",
+           "apply_single_layer_dn", "apply_volume_dn", "solve_neumann_bvp"]
 from . import kfbi3d  # noqa: E402  (3-D oracle: oracle.kfbi3d)

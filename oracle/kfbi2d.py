@@ -42,7 +42,9 @@ CPU predecessor; the readings used here (derived from the interface conditions) 
       second-order Taylor expansion of the jump about z added; v^+(z) is the value at z
       of the quadratic through the 6 corrected values (6x6 solve);
   R9  box solve: sine transform in y, tridiagonal (Thomas) solve in x per mode, inverse
-      sine transform (Alg. 4), dense sine matrix from a table sin(pi m / N).
+      sine transform (Alg. 4), dense sine matrix from a table sin(pi m / N);
+  R10 Neumann data d_n u (Procedure 2): n . grad of the same 6-point quadratic as R8 at z;
+      the Neumann BVP uses the single-layer density psi ([v] = 0, [d_n v] = psi).
 """
 from __future__ import annotations
 
@@ -436,6 +438,23 @@ def interpolate_plus(geom: Geometry2D, v, jumps_ctrl):
     return coef[:, 0]
 
 
+def interpolate_plus_grad(geom: Geometry2D, v, jumps_ctrl):
+    """v^+ and grad v^+ at every control point (R8 with R10): the quadratic fitted to the
+    same 6 corrected values as interpolate_plus, and its gradient at z.  Returns the
+    values (M,) and the gradients (M, 2)."""
+    J, G, H = jumps_ctrl
+    z = geom.pts
+    I, Jn = geom.ctrl_nodes_i, geom.ctrl_nodes_j
+    px, py = geom.xs[I], geom.xs[Jn]
+    d = np.stack([px - z[:, 0:1], py - z[:, 1:2]], axis=2)
+    taylor = J[:, None] + np.einsum("md,mkd->mk", G, d) + 0.5 * np.einsum("mkd,mde,mke->mk", d, H, d)
+    vals = v[Jn, I] + np.where(geom.inside[Jn, I], 0.0, taylor)
+    xi, eta = d[:, :, 0] / geom.h, d[:, :, 1] / geom.h
+    V = np.stack([np.ones_like(xi), xi, eta, xi * xi, xi * eta, eta * eta], axis=2)
+    coef = np.linalg.solve(V, vals[:, :, None])[:, :, 0]
+    return coef[:, 0], coef[:, 1:3] / geom.h
+
+
 # ----------------------------------------------------------------- Sec. 2.2 / Alg. 1
 def apply_interface(geom: Geometry2D, phi=None, psi=None, f_ctrl=None, F_grid=None,
                     solver=box_solve_dst, return_all=False):
@@ -448,6 +467,46 @@ def apply_interface(geom: Geometry2D, phi=None, psi=None, f_ctrl=None, F_grid=No
     if return_all:
         return out, b, v
     return out
+
+
+def apply_interface_dn(geom: Geometry2D, phi=None, psi=None, f_ctrl=None, F_grid=None,
+                       solver=box_solve_dst):
+    """d_n v^+ = n . grad v^+ at the control points of the interface problem (the Neumann
+    data of Procedure 2, reading R10)."""
+    jc = geom.jumps_at_crossings(phi, psi, f_ctrl)
+    b = correct_rhs(geom, jc, F_grid)
+    v = solver(b, geom.N, geom.h, geom.kappa2)
+    _, grad = interpolate_plus_grad(geom, v, geom.jumps_at_controls(phi, psi, f_ctrl))
+    return np.sum(grad * geom.normals, axis=1)
+
+
+def apply_single_layer(geom, psi, **kw):
+    """v^+ of the single layer (reading C18: [v] = 0, [d_n v] = psi, F = 0)."""
+    return apply_interface(geom, psi=psi, **kw)
+
+
+def apply_single_layer_dn(geom, psi, **kw):
+    """K_N psi = d_n v^+ of the single layer: the operator of the Neumann BIE."""
+    return apply_interface_dn(geom, psi=psi, **kw)
+
+
+def apply_volume_dn(geom, f_grid, f_ctrl, **kw):
+    """d_n (Y f)^+ on Gamma."""
+    return apply_interface_dn(geom, f_ctrl=f_ctrl, F_grid=f_grid, **kw)
+
+
+def solve_neumann_bvp(geom: Geometry2D, f_grid, f_ctrl, gn_ctrl, tol=1e-10, m=50,
+                      max_restarts=20):
+    """Neumann BVP d_n u = g_N on Gamma (Procedures 2-3 with the single-layer density):
+    u = V psi + Y f in Omega, so d_n(V psi)^+ = g_N - d_n(Y f)^+ is solved for psi by GMRES,
+    then u is the inside-node solution of the interface problem with [d_n v] = psi and
+    F = zero-extended f.  Needs kappa > 0 (for kappa = 0 the interior Neumann problem
+    determines u only up to a constant and K_N is singular)."""
+    ghat = np.asarray(gn_ctrl, dtype=np.float64) - apply_volume_dn(geom, f_grid, f_ctrl)
+    psi, info = gmres(lambda p: apply_single_layer_dn(geom, p), ghat, m=m, tol=tol,
+                      max_restarts=max_restarts)
+    _, _, v = apply_interface(geom, psi=psi, f_ctrl=f_ctrl, F_grid=f_grid, return_all=True)
+    return np.where(geom.inside, v, 0.0), psi, info
 
 
 def apply_double_layer(geom, phi, **kw):

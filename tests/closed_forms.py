@@ -144,3 +144,91 @@ def sphere_double_layer_plus(l, poly, R, c0, kappa, pts):
         return -sphere_free_space(l, poly, R, c0, kappa, P, np.zeros(P.shape[:-1], dtype=bool))
     vin = sphere_free_space(l, poly, R, c0, kappa, pts, np.ones(pts.shape[:-1], dtype=bool))
     return vin + cube_correction(face, kappa, pts)
+
+
+# ------------------------------------------------------------------ circle single layer (2-D)
+def free_space_single(k, R, kappa, r, theta, inside):
+    """Free-space single-layer field of the density cos(k theta) on the circle: [v] = 0 and
+    [d_r v] = cos(k theta) (inside minus outside), decaying at infinity:
+      kappa = 0 (k >= 1): v_in = R/(2k) (r/R)^k cos k theta, v_out = R/(2k) (R/r)^k cos k theta;
+      kappa > 0:          v_in = R K_k(x) I_k(kappa r) cos k theta,
+                          v_out = R I_k(x) K_k(kappa r) cos k theta,  x = kappa R
+    (continuity by construction; the derivative jump from the Wronskian)."""
+    if kappa == 0.0:
+        return np.where(inside, R / (2 * k) * (r / R) ** k,
+                        R / (2 * k) * (R / r) ** k) * np.cos(k * theta)
+    x = kappa * R
+    vin = R * special.kv(k, x) * special.iv(k, kappa * r)
+    vout = R * special.iv(k, x) * special.kv(k, kappa * r)
+    return np.where(inside, vin, vout) * np.cos(k * theta)
+
+
+def free_space_single_dr_in(k, R, kappa):
+    """d_r v_in at r = R of free_space_single, as the factor of cos(k theta)."""
+    if kappa == 0.0:
+        return 0.5
+    x = kappa * R
+    return R * kappa * special.kv(k, x) * special.ivp(k, x)
+
+
+def box_correction_grad(g_side, kappa, X, Y, terms=160, quad=1200):
+    """Gradient (wx, wy) at (X, Y) of the box correction w of box_correction: each sine
+    series term differentiated along the side and across it."""
+    s, wq = np.polynomial.legendre.leggauss(quad)
+    m = np.arange(1, terms + 1)
+    basis = np.sin(np.outer(m, s + 1.0) * np.pi / 2.0)
+    mu = np.sqrt((m * np.pi / 2.0) ** 2 + kappa ** 2)
+    wx = np.zeros_like(X, dtype=np.float64)
+    wy = np.zeros_like(X, dtype=np.float64)
+    for side in ("top", "bottom", "left", "right"):
+        c = basis @ (wq * g_side(side, s))
+        along = X if side in ("top", "bottom") else Y
+        if side == "top":
+            d, dd = Y + 1.0, 1.0
+        elif side == "bottom":
+            d, dd = 1.0 - Y, -1.0
+        elif side == "right":
+            d, dd = X + 1.0, 1.0
+        else:
+            d, dd = 1.0 - X, -1.0
+        D = d.reshape(1, -1)
+        ratio = np.exp(mu[:, None] * (D - 2.0)) * (1.0 - np.exp(-2.0 * mu[:, None] * D)) / \
+            (1.0 - np.exp(-4.0 * mu[:, None]))
+        dratio = mu[:, None] * np.exp(mu[:, None] * (D - 2.0)) * \
+            (1.0 + np.exp(-2.0 * mu[:, None] * D)) / (1.0 - np.exp(-4.0 * mu[:, None]))
+        arg = np.outer(m, along.reshape(-1) + 1.0) * np.pi / 2.0
+        d_along = np.sum(c[:, None] * (m[:, None] * np.pi / 2.0) * np.cos(arg) * ratio, axis=0)
+        d_across = dd * np.sum(c[:, None] * np.sin(arg) * dratio, axis=0)
+        if side in ("top", "bottom"):
+            wx += d_along.reshape(X.shape)
+            wy += d_across.reshape(X.shape)
+        else:
+            wy += d_along.reshape(X.shape)
+            wx += d_across.reshape(X.shape)
+    return wx, wy
+
+
+def circle_single_layer_plus(k, R, c0, kappa, theta):
+    """Exact v^+ and d_n v^+ on the circle of the box single-layer potential of cos(k theta)
+    (free-space field plus the box correction w = -v_out on the box boundary)."""
+    def vout_side(side, s):
+        if side == "top":
+            x, y = s, np.ones_like(s)
+        elif side == "bottom":
+            x, y = s, -np.ones_like(s)
+        elif side == "right":
+            x, y = np.ones_like(s), s
+        else:
+            x, y = -np.ones_like(s), s
+        r = np.hypot(x - c0[0], y - c0[1])
+        th = np.arctan2(y - c0[1], x - c0[0])
+        return -free_space_single(k, R, kappa, r, th, np.zeros_like(r, dtype=bool))
+
+    X = c0[0] + R * np.cos(theta)
+    Y = c0[1] + R * np.sin(theta)
+    v = free_space_single(k, R, kappa, np.full_like(theta, R), theta,
+                          np.ones_like(theta, dtype=bool)) + box_correction(vout_side, kappa, X, Y)
+    wx, wy = box_correction_grad(vout_side, kappa, X, Y)
+    dn = free_space_single_dr_in(k, R, kappa) * np.cos(k * theta) + \
+        wx * np.cos(theta) + wy * np.sin(theta)
+    return v, dn

@@ -385,3 +385,86 @@ def test_error_norms_by_hand():
     u[1, 3] = -2.0                                  # two inside errors: sqrt((1 + 4) / 9)
     e_inf, e_l2 = O.error_norms(u, np.zeros((5, 5)), inside)
     assert e_inf == 2.0 and e_l2 == pytest.approx(np.sqrt(5.0 / 9.0), rel=1e-15)
+
+
+# ------------------------------------------------------------------ single layer, Neumann BVP
+@pytest.mark.parametrize("kappa,k", [(0.0, 1), (0.0, 3), (1.0, 2), (10.0, 3)])
+def test_p4_single_layer_circle_closed_form(kappa, k):
+    """Reading C18 (single layer by the interface problem [v] = 0, [d_n v] = psi) and R10
+    (Neumann data from the gradient of the interpolating quadratic) against the closed-form
+    box single-layer potential of cos(k theta) on a circle: v^+ converges at second order,
+    d_n v^+ at order 1.5 or better."""
+    from closed_forms import circle_single_layer_plus
+    R = 0.5
+    ev, ed = [], []
+    for N in (64, 128, 256):
+        iface = W.circle(2 * N, R, C0)
+        g = geom_of(iface, N, kappa)
+        th = 2 * np.pi * np.arange(iface.M) / iface.M
+        psi = np.cos(k * th)
+        v_ex, dn_ex = circle_single_layer_plus(k, R, C0, kappa, th)
+        ev.append(np.max(np.abs(O.apply_single_layer(g, psi) - v_ex)))
+        ed.append(np.max(np.abs(O.apply_single_layer_dn(g, psi) - dn_ex)))
+    rv = [ev[i] / ev[i + 1] for i in range(2)]
+    rd = [ed[i] / ed[i + 1] for i in range(2)]
+    assert ev[-1] < 2e-5 and min(rv) > 2.2 and np.sqrt(rv[0] * rv[1]) > 3.5, (ev, rv)
+    assert ed[-1] < 1e-3 and min(rd) > 2.8, (ed, rd)
+
+
+def test_p11_gradient_reproduces_piecewise_quadratics():
+    """R10: the gradient of the corrected interpolating quadratic at z is grad v^+ exactly
+    for quadratic v+ and v- with their exact jumps."""
+    N = 64
+    iface = W.flower(2 * N)
+    g = geom_of(iface, N, 0.0)
+    vp, vm, jumps = _piecewise_quadratic(g)
+    _, X, Y = W.grid_nodes(N)
+    v = np.where(g.inside, vp(X, Y), vm(X, Y))
+    val, grad = O.interpolate_plus_grad(g, v, jumps(g.pts))
+    x, y = g.pts[:, 0], g.pts[:, 1]
+    assert np.max(np.abs(val - vp(x, y))) <= 1e-12
+    assert np.max(np.abs(grad[:, 0] - (0.3 + x + 0.25 * y))) <= 1e-10
+    assert np.max(np.abs(grad[:, 1] - (-0.2 + 0.25 * x - 0.8 * y))) <= 1e-10
+
+
+@pytest.mark.parametrize("shape,kappa", [("ellipse", 1.0), ("flower", 10.0)])
+def test_p5_neumann_bvp_second_order(shape, kappa):
+    """Neumann BVP (Procedures 2-3 with the single-layer density): u = exp(x) sin(2y),
+    d_n u given at the control points; max and l2 errors of u fall about 4x per doubling."""
+    errs = []
+    for N in (64, 128, 256):
+        prob = W.config_helmholtz(N, kappa, shape)
+        g = geom_of(prob.iface, N, kappa)
+        u, psi, info = O.solve_neumann_bvp(g, prob.f_grid(), prob.f_ctrl(), prob.gn_ctrl(), tol=1e-10)
+        assert info["converged"]
+        errs.append(O.error_norms(u, prob.u_grid(), g.inside))
+    for q in (0, 1):
+        r = [errs[i][q] / errs[i + 1][q] for i in range(2)]
+        assert min(r) > 3.0 and np.sqrt(r[0] * r[1]) > 3.5, (errs, r)
+
+
+def test_p6_neumann_gmres_matches_dense_solve():
+    """GMRES on the single-layer Neumann operator K_N against LU of the assembled K_N."""
+    N, M, kappa = 16, 32, 2.0
+    prob = W.Problem(W.circle(M, 0.45, C0), N, kappa, W.manufactured_exp_sin2y(kappa))
+    g = geom_of(prob.iface, N, kappa)
+    K = np.stack([O.apply_single_layer_dn(g, e) for e in np.eye(M)], axis=1)
+    ghat = prob.gn_ctrl() - O.apply_volume_dn(g, prob.f_grid(), prob.f_ctrl())
+    psi_lu = np.linalg.solve(K, ghat)
+    _, psi, info = O.solve_neumann_bvp(g, prob.f_grid(), prob.f_ctrl(), prob.gn_ctrl(), tol=1e-13)
+    assert info["converged"] and np.max(np.abs(psi - psi_lu)) <= 1e-11 * np.max(np.abs(psi_lu))
+
+
+def test_planted_normal_sign_breaks_the_single_layer_pin(monkeypatch):
+    """Extracting the Neumann data along the inward normal fails the closed-form d_n pin."""
+    from closed_forms import circle_single_layer_plus
+    import oracle.kfbi2d as K
+    N, R, k, kappa = 128, 0.5, 2, 1.0
+    iface = W.circle(2 * N, R, C0)
+    th = 2 * np.pi * np.arange(iface.M) / iface.M
+    _, dn_ex = circle_single_layer_plus(k, R, C0, kappa, th)
+    good = np.max(np.abs(K.apply_single_layer_dn(geom_of(iface, N, kappa), np.cos(k * th)) - dn_ex))
+    orig = K.interpolate_plus_grad
+    monkeypatch.setattr(K, "interpolate_plus_grad", lambda g, v, j: (lambda r: (r[0], -r[1]))(orig(g, v, j)))
+    bad = np.max(np.abs(K.apply_single_layer_dn(geom_of(iface, N, kappa), np.cos(k * th)) - dn_ex))
+    assert bad > 50 * good
