@@ -255,6 +255,34 @@ kfbi_status kfbi_solve_bvp(kfbi_ctx ctx, const double* d_f_grid, const double* d
                            const double* d_g_ctrl, double* d_u_grid, double* d_density_out,
                            kfbi_solve_info* h_info, void* stream);
 
+/* Neumann data of a layer potential (Procedure 2 of Sec. 4.4, "extract d_n u"): the
+   interior normal derivative d_n v^+ at the control points of the interface problem of
+   kfbi_apply_layer_potential (same layers and precisions), taken as n . grad of the
+   quadratic fitted to the same 6 corrected grid values at each control point (outward n).
+   For KFBI_SINGLE_LAYER this is the operator K_N psi of the Neumann BIE.  2-D only
+   (KFBI_ERR_UNSUPPORTED in 3-D).  d_density, d_out: M values.  Asynchronous. */
+kfbi_status kfbi_apply_layer_potential_dn(kfbi_ctx ctx, int layer, int precision,
+                                          const double* d_density, double* d_out, void* stream);
+
+/* d_n (Y f)^+ at the control points (the volume term of the Neumann BIE); arguments as
+   kfbi_apply_volume.  2-D only.  Asynchronous. */
+kfbi_status kfbi_apply_volume_dn(kfbi_ctx ctx, int precision, const double* d_f_grid,
+                                 const double* d_f_ctrl, double* d_out, void* stream);
+
+/* Neumann BVP  Lap u - kappa^2 u = f in Omega, d_n u = g_N on Gamma (Procedures 2-3 of
+   Sec. 4.4 with the single-layer density psi; the single layer is the interface problem
+   [v] = 0, [d_n v] = psi): u = V psi + Y f in Omega, so
+   K_N psi = d_n (V psi)^+ = g_N - d_n (Y f)^+ is solved by GMRES(m) exactly as
+   kfbi_solve_bvp solves K_D phi = g_hat (same solver options, FP64 or relaxed mixed
+   precision), then u is the inside-node solution of the interface problem with
+   [d_n v] = psi and F = zero-extended f.  kappa must be positive (for kappa = 0 the
+   interior Neumann problem fixes u only up to a constant and K_N is singular).
+   d_gn_ctrl: g_N at the M control points (outward normal derivative); d_density_out: psi
+   (M) or NULL; other arguments as kfbi_solve_bvp.  2-D only.  Synchronising. */
+kfbi_status kfbi_solve_neumann_bvp(kfbi_ctx ctx, const double* d_f_grid, const double* d_f_ctrl,
+                                   const double* d_gn_ctrl, double* d_u_grid,
+                                   double* d_density_out, kfbi_solve_info* h_info, void* stream);
+
 /* Node labels: d_mask[(N+1)^2] = 1 inside Omega, 0 outside.  Asynchronous. */
 kfbi_status kfbi_get_inside_mask(kfbi_ctx ctx, uint8_t* d_mask, void* stream);
 

@@ -89,6 +89,9 @@ _SIGS = {
     "kfbi_box_solve_static": (I, [I, D, D, D, I, P, P, P]),
     "kfbi_box_solve_static_check": (I, [P]),
     "kfbi_solve_bvp": (I, [P, P, P, P, P, P, ctypes.POINTER(SolveInfo), P]),
+    "kfbi_solve_neumann_bvp": (I, [P, P, P, P, P, P, ctypes.POINTER(SolveInfo), P]),
+    "kfbi_apply_layer_potential_dn": (I, [P, I, I, P, P, P]),
+    "kfbi_apply_volume_dn": (I, [P, I, P, P, P, P]),
     "kfbi_get_inside_mask": (I, [P, P, P]),
     "kfbi_get_info": (I, [P, ctypes.POINTER(CtxInfo)]),
     "kfbi_set_solver": (I, [P, I, I, I, D, D]),
@@ -207,6 +210,37 @@ class Kfbi2D:
                                                 _ptr(out), _stream_ptr(self.stream)),
                "kfbi_apply_layer_potential")
         return out
+
+    def apply_layer_potential_dn(self, density, layer=KFBI_SINGLE_LAYER, precision=KFBI_FP64,
+                                 out=None):
+        """kfbi_apply_layer_potential_dn: d_n v^+ at the control points (2-D)."""
+        d = self._vec(density)
+        out = self._new(self.M) if out is None else self._out(out, self.M)
+        _check(lib().kfbi_apply_layer_potential_dn(self.handle, int(layer), int(precision), _ptr(d),
+                                                   _ptr(out), _stream_ptr(self.stream)),
+               "kfbi_apply_layer_potential_dn")
+        return out
+
+    def apply_volume_dn(self, f_grid, f_ctrl, precision=KFBI_FP64):
+        """kfbi_apply_volume_dn: d_n (Y f)^+ at the control points (2-D)."""
+        fg, fc = self._vec(f_grid), self._vec(f_ctrl)
+        out = self._new(self.M)
+        _check(lib().kfbi_apply_volume_dn(self.handle, int(precision), _ptr(fg), _ptr(fc),
+                                          _ptr(out), _stream_ptr(self.stream)), "kfbi_apply_volume_dn")
+        return out
+
+    def solve_neumann_bvp(self, f_grid, f_ctrl, gn_ctrl, u_out=None, dens_out=None,
+                          allow_not_converged=False):
+        """kfbi_solve_neumann_bvp: (u grid, single-layer density psi, info) (2-D)."""
+        fg, fc, gc = self._vec(f_grid), self._vec(f_ctrl), self._vec(gn_ctrl)
+        u = self._grid() if u_out is None else u_out
+        psi = self._new(self.M) if dens_out is None else dens_out
+        info = SolveInfo()
+        st = lib().kfbi_solve_neumann_bvp(self.handle, _ptr(fg), _ptr(fc), _ptr(gc), _ptr(u),
+                                          _ptr(psi), ctypes.byref(info), _stream_ptr(self.stream))
+        if not (allow_not_converged and st == KFBI_ERR_NOT_CONVERGED):
+            _check(st, "kfbi_solve_neumann_bvp")
+        return u, psi, info.as_dict()
 
     def apply_volume(self, f_grid, f_ctrl, precision=KFBI_FP64):
         fg, fc = self._vec(f_grid), self._vec(f_ctrl)

@@ -409,14 +409,16 @@ static kfbi_status correct(Ctx& c, const double* dens, const double* psi, const 
   return KFBI_OK;
 }
 
+// v^+ at the control points, or with dn the normal derivative d_n v^+ (the same gather with
+// the weights of n . grad of the fitted quadratic)
 template <typename T>
 static kfbi_status interp(Ctx& c, const T* v1, const float* v2, const float* v3,
                           const double* dens, const double* psi, const double* fctl,
-                          double* out) {
+                          double* out, bool dn = false) {
   const int pr = prof_begin(c, ST_INTERP);
-  interp_kernel<T><<<(c.M + 127) / 128, 128, 0, c.stream>>>(c.M, c.ctrl_node, c.ctrl_w,
-                                                            c.ctrl_cD, c.ctrl_cS, c.ctrl_eF, v1,
-                                                            v2, v3, dens, psi, fctl, out);
+  interp_kernel<T><<<(c.M + 127) / 128, 128, 0, c.stream>>>(
+      c.M, c.ctrl_node, dn ? c.ctrl_wn : c.ctrl_w, dn ? c.ctrl_cDn : c.ctrl_cD,
+      dn ? c.ctrl_cSn : c.ctrl_cS, dn ? c.ctrl_eFn : c.ctrl_eF, v1, v2, v3, dens, psi, fctl, out);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
@@ -461,14 +463,21 @@ static kfbi_status refined_solve(Ctx& c, const float* b32, const float* bhi, con
 }
 
 // ------------------------------------------------------------------ apply
-kfbi_status apply_potential(Ctx& c, Layer layer, int precision, const double* dens, double* out) {
-  if (c.dim == 3) return apply_potential3(c, layer, precision, dens, out);
+kfbi_status apply_potential(Ctx& c, Layer layer, int precision, const double* dens, double* out,
+                            bool dn) {
+  if (c.dim == 3) {
+    if (dn) {
+      set_error("normal derivative of a layer potential: 2-D only");
+      return KFBI_ERR_UNSUPPORTED;
+    }
+    return apply_potential3(c, layer, precision, dens, out);
+  }
   const double* d = layer == Layer::Double ? dens : nullptr;
   const double* s = layer == Layer::Single ? dens : nullptr;
   if (precision == KFBI_FP64) {
     KFBI_TRY(correct<double>(c, d, s, nullptr, c.B64, 0));
     KFBI_TRY(box_solve_f64(c, c.B64, c.V64));
-    return interp<double>(c, c.V64, nullptr, nullptr, d, s, nullptr, out);
+    return interp<double>(c, c.V64, nullptr, nullptr, d, s, nullptr, out, dn);
   }
   const int steps = refine_steps_of(precision);
   if (steps == 0 && precision != KFBI_TF32X3 && c.irr_rowptr && c.dim == 2) {
@@ -476,30 +485,30 @@ kfbi_status apply_potential(Ctx& c, Layer layer, int precision, const double* de
     // of the box solve on the transformed rows
     KFBI_TRY(sparse_rows(c, d ? c.arm_wD : c.arm_wS, d ? d : s, c.V32));
     KFBI_TRY(box_solve_after_rows_f32(c, c.V32));
-    return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out);
+    return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out, dn);
   }
   KFBI_TRY(correct<float>(c, d, s, nullptr, c.B32, 0, steps ? c.B64 : nullptr));
   if (precision == KFBI_TF32X3) {                   // dense sine transforms on tensor cores
     KFBI_TRY(box_solve_tc(c, c.B32, c.V32));
-    return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out);
+    return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out, dn);
   }
   if (steps == 0) {
     KFBI_TRY(box_solve_f32(c, c.B32, c.V32));
-    return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out);
+    return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out, dn);
   }
   KFBI_TRY(refined_solve(c, c.B32, nullptr, nullptr, steps));
-  return interp<float>(c, c.V32, c.U32, steps > 1 ? c.T32 : nullptr, d, s, nullptr, out);
+  return interp<float>(c, c.V32, c.U32, steps > 1 ? c.T32 : nullptr, d, s, nullptr, out, dn);
 }
 
 // ------------------------------------------------------------------ dense interface solves
 // F~ + corrections in FP64 in V64 (work layout)
 static kfbi_status dense_rhs64(Ctx& c, const double* dens, const double* f_grid,
-                               const double* f_ctrl) {
+                               const double* f_ctrl, const double* psi = nullptr) {
   prof_count(c, ST_GRID);
   rhs_dense_kernel<double><<<rows_grid(c.N, c.N), 256, 0, c.stream>>>(c.N, f_grid, c.inside,
                                                                       c.V64);
   KFBI_CUDA_TRY(cudaGetLastError());
-  return correct<double>(c, dens, nullptr, f_ctrl, c.V64, 1);
+  return correct<double>(c, dens, psi, f_ctrl, c.V64, 1);
 }
 
 // refined FP32 solve of the FP64 right-hand side in V64, split into an exact pair
@@ -513,22 +522,28 @@ static kfbi_status refined_dense(Ctx& c, int steps) {
 
 kfbi_status interface_solve(Ctx& c, int precision, const double* dens, const double* f_grid,
                             const double* f_ctrl, double* rhs_grid, double* v_grid,
-                            double* out) {
-  if (c.dim == 3) return interface_solve3(c, precision, dens, f_grid, f_ctrl, rhs_grid, v_grid, out);
+                            double* out, const double* psi, bool dn) {
+  if (c.dim == 3) {
+    if (psi || dn) {
+      set_error("interface solve with a single-layer density or a normal derivative: 2-D only");
+      return KFBI_ERR_UNSUPPORTED;
+    }
+    return interface_solve3(c, precision, dens, f_grid, f_ctrl, rhs_grid, v_grid, out);
+  }
   const int steps = refine_steps_of(precision);
   if (precision == KFBI_FP64 || steps > 0) {
-    KFBI_TRY(dense_rhs64(c, dens, f_grid, f_ctrl));
+    KFBI_TRY(dense_rhs64(c, dens, f_grid, f_ctrl, psi));
     if (rhs_grid) KFBI_TRY(to_grid<double>(c, c.V64, nullptr, nullptr, nullptr, rhs_grid));
     if (precision == KFBI_FP64) {
       KFBI_TRY(box_solve_f64(c, c.V64, c.V64));
       if (v_grid) KFBI_TRY(to_grid<double>(c, c.V64, nullptr, nullptr, nullptr, v_grid));
-      if (out) KFBI_TRY(interp<double>(c, c.V64, nullptr, nullptr, dens, nullptr, f_ctrl, out));
+      if (out) KFBI_TRY(interp<double>(c, c.V64, nullptr, nullptr, dens, psi, f_ctrl, out, dn));
       return KFBI_OK;
     }
     KFBI_TRY(refined_dense(c, steps));
     const float* v3 = steps > 1 ? c.T32 : nullptr;
     if (v_grid) KFBI_TRY(to_grid<float>(c, c.V32, c.U32, v3, nullptr, v_grid));
-    if (out) KFBI_TRY(interp<float>(c, c.V32, c.U32, v3, dens, nullptr, f_ctrl, out));
+    if (out) KFBI_TRY(interp<float>(c, c.V32, c.U32, v3, dens, psi, f_ctrl, out, dn));
     return KFBI_OK;
   }
   // plain FP32
@@ -536,20 +551,26 @@ kfbi_status interface_solve(Ctx& c, int precision, const double* dens, const dou
   prof_count(c, ST_GRID);
   rhs_dense_kernel<float><<<rows_grid(c.N, c.N), 256, 0, c.stream>>>(c.N, f_grid, c.inside, W);
   KFBI_CUDA_TRY(cudaGetLastError());
-  KFBI_TRY(correct<float>(c, dens, nullptr, f_ctrl, W, 1));
+  KFBI_TRY(correct<float>(c, dens, psi, f_ctrl, W, 1));
   if (rhs_grid) KFBI_TRY(to_grid<float>(c, W, nullptr, nullptr, nullptr, rhs_grid));
   if (precision == KFBI_TF32X3) KFBI_TRY(box_solve_tc(c, W, W));
   else KFBI_TRY(box_solve_f32(c, W, W));
   if (v_grid) KFBI_TRY(to_grid<float>(c, W, nullptr, nullptr, nullptr, v_grid));
-  if (out) KFBI_TRY(interp<float>(c, W, nullptr, nullptr, dens, nullptr, f_ctrl, out));
+  if (out) KFBI_TRY(interp<float>(c, W, nullptr, nullptr, dens, psi, f_ctrl, out, dn));
   return KFBI_OK;
 }
 
 // u on the grid: inside nodes of the combined solve (Phi = phi, F = f~), zero elsewhere
 kfbi_status combined_u(Ctx& c, int precision, const double* dens, const double* f_grid,
-                       const double* f_ctrl, double* u_grid) {
-  if (c.dim == 3) return combined_u3(c, precision, dens, f_grid, f_ctrl, u_grid);
-  KFBI_TRY(dense_rhs64(c, dens, f_grid, f_ctrl));
+                       const double* f_ctrl, double* u_grid, const double* psi) {
+  if (c.dim == 3) {
+    if (psi) {
+      set_error("grid solution with a single-layer density: 2-D only");
+      return KFBI_ERR_UNSUPPORTED;
+    }
+    return combined_u3(c, precision, dens, f_grid, f_ctrl, u_grid);
+  }
+  KFBI_TRY(dense_rhs64(c, dens, f_grid, f_ctrl, psi));
   if (precision == KFBI_FP64) {
     KFBI_TRY(box_solve_f64(c, c.V64, c.V64));
     return to_grid<double>(c, c.V64, nullptr, nullptr, c.inside, u_grid);

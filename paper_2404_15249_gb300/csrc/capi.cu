@@ -316,7 +316,58 @@ kfbi_status kfbi_solve_bvp(kfbi_ctx ctx, const double* d_f_grid, const double* d
     kfbi::set_error("kfbi_solve_bvp: bad argument");
     return KFBI_ERR_ARG;
   }
-  return kfbi::solve_bvp(*c, d_f_grid, d_f_ctrl, d_g_ctrl, d_u_grid, d_density_out, h_info);
+  return kfbi::solve_bvp(*c, d_f_grid, d_f_ctrl, d_g_ctrl, d_u_grid, d_density_out, h_info,
+                         kfbi::kOpDirichlet);
+}
+
+kfbi_status kfbi_solve_neumann_bvp(kfbi_ctx ctx, const double* d_f_grid, const double* d_f_ctrl,
+                                   const double* d_gn_ctrl, double* d_u_grid,
+                                   double* d_density_out, kfbi_solve_info* h_info, void* stream) {
+  Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
+  if (!c || !d_f_grid || !d_f_ctrl || !d_gn_ctrl) {
+    kfbi::set_error("kfbi_solve_neumann_bvp: bad argument");
+    return KFBI_ERR_ARG;
+  }
+  if (c->dim != 2) {
+    kfbi::set_error("kfbi_solve_neumann_bvp: 2-D only");
+    return KFBI_ERR_UNSUPPORTED;
+  }
+  return kfbi::solve_bvp(*c, d_f_grid, d_f_ctrl, d_gn_ctrl, d_u_grid, d_density_out, h_info,
+                         kfbi::kOpNeumann);
+}
+
+kfbi_status kfbi_apply_layer_potential_dn(kfbi_ctx ctx, int layer, int precision,
+                                          const double* d_density, double* d_out, void* stream) {
+  Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
+  if (!c || !d_density || !d_out || (layer != KFBI_DOUBLE_LAYER && layer != KFBI_SINGLE_LAYER) ||
+      !kfbi::valid_precision(precision)) {
+    kfbi::set_error("kfbi_apply_layer_potential_dn: bad argument");
+    return KFBI_ERR_ARG;
+  }
+  if (c->dim != 2) {
+    kfbi::set_error("kfbi_apply_layer_potential_dn: 2-D only");
+    return KFBI_ERR_UNSUPPORTED;
+  }
+  if (tc_refused(*c, precision, "kfbi_apply_layer_potential_dn")) return KFBI_ERR_UNSUPPORTED;
+  return kfbi::apply_potential(*c, layer == KFBI_DOUBLE_LAYER ? kfbi::Layer::Double
+                                                              : kfbi::Layer::Single,
+                               precision, d_density, d_out, true);
+}
+
+kfbi_status kfbi_apply_volume_dn(kfbi_ctx ctx, int precision, const double* d_f_grid,
+                                 const double* d_f_ctrl, double* d_out, void* stream) {
+  Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
+  if (!c || !d_f_grid || !d_f_ctrl || !d_out || !kfbi::valid_precision(precision)) {
+    kfbi::set_error("kfbi_apply_volume_dn: bad argument");
+    return KFBI_ERR_ARG;
+  }
+  if (c->dim != 2) {
+    kfbi::set_error("kfbi_apply_volume_dn: 2-D only");
+    return KFBI_ERR_UNSUPPORTED;
+  }
+  if (tc_refused(*c, precision, "kfbi_apply_volume_dn")) return KFBI_ERR_UNSUPPORTED;
+  return kfbi::interface_solve(*c, precision, nullptr, d_f_grid, d_f_ctrl, nullptr, nullptr, d_out,
+                               nullptr, true);
 }
 
 kfbi_status kfbi_get_inside_mask(kfbi_ctx ctx, uint8_t* d_mask, void* stream) {

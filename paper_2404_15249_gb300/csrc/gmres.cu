@@ -268,11 +268,12 @@ struct Counters {
 static inline int vb(int M) { return (M + 255) / 256; }
 
 void drop_step_graphs(Ctx& c) {
-  for (int p = 0; p < kStepGraphs; ++p)
-    if (c.step_exec[p]) {
-      cudaGraphExecDestroy(c.step_exec[p]);
-      c.step_exec[p] = nullptr;
-    }
+  for (int o = 0; o < kOps; ++o)
+    for (int p = 0; p < kStepGraphs; ++p)
+      if (c.step_exec[o][p]) {
+        cudaGraphExecDestroy(c.step_exec[o][p]);
+        c.step_exec[o][p] = nullptr;
+      }
 }
 
 kfbi_status alloc_gmres(Ctx& c, int m) {
@@ -305,10 +306,17 @@ kfbi_status alloc_gmres(Ctx& c, int m) {
   return KFBI_OK;
 }
 
+// The operator of the BIE being solved: K_D = v^+ of the double layer (Dirichlet BVP) or
+// K_N = d_n v^+ of the single layer (Neumann BVP)
+static kfbi_status op_apply(Ctx& c, int precision, const double* x, double* y) {
+  if (c.gm_op == kOpNeumann) return apply_potential(c, Layer::Single, precision, x, y, true);
+  return apply_potential(c, Layer::Double, precision, x, y);
+}
+
 static kfbi_status apply_K(Ctx& c, int precision, const double* x, double* y, Counters& cnt) {
   if (precision == KFBI_MIXED_FP32 || precision == KFBI_TF32X3) ++cnt.applies32;
   else ++cnt.applies64;   // FP64-accurate
-  return apply_potential(c, Layer::Double, precision, x, y);
+  return op_apply(c, precision, x, y);
 }
 
 static kfbi_status read_scal(Ctx& c, int n) {
@@ -351,7 +359,7 @@ static kfbi_status arnoldi_step(Ctx& c, int prec) {
   double* vin = c.vecs + 6 * M;
   double* h1 = c.hcol;
   double* h2 = c.hcol + (m + 1);
-  KFBI_TRY(apply_potential(c, Layer::Double, prec, vin, w));
+  KFBI_TRY(op_apply(c, prec, vin, w));
   const int pk = prof_begin(c, ST_KRYLOV);
   prof_count(c, ST_KRYLOV, 5);
   const size_t hsm = sizeof(double) * (m + 1);
@@ -383,7 +391,9 @@ static kfbi_status launch_step(Ctx& c, int prec) {
     drop_step_graphs(c);
     c.graph_m = c.opt.gmres_m;
   }
-  if (!c.step_exec[prec]) {
+  cudaGraphExec_t& exec = c.step_exec[c.gm_op][prec];
+  long long* counts = c.step_launches[c.gm_op][prec];
+  if (!exec) {
     long long before[KFBI_NSTAGES];
     for (int s = 0; s < KFBI_NSTAGES; ++s) before[s] = c.prof.launches[s];
     cudaGraph_t g = nullptr;
@@ -395,7 +405,7 @@ static kfbi_status launch_step(Ctx& c, int prec) {
     const kfbi_status body = arnoldi_step(c, prec);
     const cudaError_t ec = cudaStreamEndCapture(c.stream, &g);
     for (int s = 0; s < KFBI_NSTAGES; ++s) {   // captured, not run: counted per replay
-      c.step_launches[prec][s] = c.prof.launches[s] - before[s];
+      counts[s] = c.prof.launches[s] - before[s];
       c.prof.launches[s] = before[s];
     }
     cudaGraphExec_t ex = nullptr;
@@ -407,10 +417,10 @@ static kfbi_status launch_step(Ctx& c, int prec) {
       c.graphs_ok = false;
       return arnoldi_step(c, prec);
     }
-    c.step_exec[prec] = ex;
+    exec = ex;
   }
-  KFBI_CUDA_TRY(cudaGraphLaunch(c.step_exec[prec], c.stream));
-  for (int s = 0; s < KFBI_NSTAGES; ++s) c.prof.launches[s] += c.step_launches[prec][s];
+  KFBI_CUDA_TRY(cudaGraphLaunch(exec, c.stream));
+  for (int s = 0; s < KFBI_NSTAGES; ++s) c.prof.launches[s] += counts[s];
   return KFBI_OK;
 }
 
@@ -515,32 +525,39 @@ static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const do
   return KFBI_OK;
 }
 
-static kfbi_status solve_bvp_on(Ctx& c, const double* f_grid, const double* f_ctrl,
+static kfbi_status solve_bvp_on(Ctx& c, int op, const double* f_grid, const double* f_ctrl,
                                 const double* g_ctrl, double* u_grid, double* dens_out,
                                 kfbi_solve_info* info);
 
 // The solve runs on the context's own non-blocking stream (the captured Arnoldi-step graphs
 // need a stream that can be captured; the legacy default stream cannot), joined to the
 // caller's stream at both ends: it starts after the work already queued there, and the
-// caller's stream waits for it.
+// caller's stream waits for it.  op: kOpDirichlet (g = u on Gamma, double-layer density)
+// or kOpNeumann (g = d_n u on Gamma, single-layer density).
 kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const double* g_ctrl,
-                      double* u_grid, double* dens_out, kfbi_solve_info* info) {
+                      double* u_grid, double* dens_out, kfbi_solve_info* info, int op) {
   const cudaStream_t caller = c.stream;
-  if (!c.own) return solve_bvp_on(c, f_grid, f_ctrl, g_ctrl, u_grid, dens_out, info);
+  if (!c.own) return solve_bvp_on(c, op, f_grid, f_ctrl, g_ctrl, u_grid, dens_out, info);
   KFBI_CUDA_TRY(cudaEventRecord(c.own_in, caller));
   KFBI_CUDA_TRY(cudaStreamWaitEvent(c.own, c.own_in, 0));
   c.stream = c.own;
-  const kfbi_status s = solve_bvp_on(c, f_grid, f_ctrl, g_ctrl, u_grid, dens_out, info);
+  const kfbi_status s = solve_bvp_on(c, op, f_grid, f_ctrl, g_ctrl, u_grid, dens_out, info);
   c.stream = caller;
   KFBI_CUDA_TRY(cudaEventRecord(c.own_out, c.own));
   KFBI_CUDA_TRY(cudaStreamWaitEvent(caller, c.own_out, 0));
   return s;
 }
 
-static kfbi_status solve_bvp_on(Ctx& c, const double* f_grid, const double* f_ctrl,
+static kfbi_status solve_bvp_on(Ctx& c, int op, const double* f_grid, const double* f_ctrl,
                                 const double* g_ctrl, double* u_grid, double* dens_out,
                                 kfbi_solve_info* info) {
   const int M = c.M;
+  const bool neumann = op == kOpNeumann;
+  if (neumann && c.dim != 2) {
+    set_error("Neumann BVP: 2-D only");
+    return KFBI_ERR_UNSUPPORTED;
+  }
+  c.gm_op = op;
   cudaStream_t st = c.stream;
   KFBI_TRY(alloc_gmres(c, c.opt.gmres_m));
   // precision of every step that must be FP64-accurate: FP64 transforms in the plain FP64
@@ -552,8 +569,8 @@ static kfbi_status solve_bvp_on(Ctx& c, const double* f_grid, const double* f_ct
   Counters cnt;
   // bounded waits that give up during this solve are reported by this solve
   KFBI_CUDA_TRY(cudaMemsetAsync(c.err_flag + 2, 0, sizeof(int), st));
-  // g_hat = g - (Y f)^+
-  KFBI_TRY(interface_solve(c, acc, nullptr, f_grid, f_ctrl, nullptr, nullptr, d));
+  // g_hat = g - (Y f)^+  (Neumann: g - d_n (Y f)^+)
+  KFBI_TRY(interface_solve(c, acc, nullptr, f_grid, f_ctrl, nullptr, nullptr, d, nullptr, neumann));
   ++cnt.applies64;
   prof_count(c, ST_KRYLOV, 2);
   sub_kernel<<<vb(M), 256, 0, st>>>(ghat, g_ctrl, d, M);
@@ -577,9 +594,10 @@ static kfbi_status solve_bvp_on(Ctx& c, const double* f_grid, const double* f_ct
     KFBI_TRY(gmres_run(c, relax, acc, ghat, phi, true, tol_abs, c.opt.max_restarts + 1, cnt,
                        &res, &cycles));
   }
-  // u = W phi + Y f on inside nodes
+  // u = W phi + Y f (Neumann: V psi + Y f) on inside nodes
   if (u_grid) {
-    KFBI_TRY(combined_u(c, acc, phi, f_grid, f_ctrl, u_grid));
+    if (neumann) KFBI_TRY(combined_u(c, acc, nullptr, f_grid, f_ctrl, u_grid, phi));
+    else KFBI_TRY(combined_u(c, acc, phi, f_grid, f_ctrl, u_grid));
     ++cnt.applies64;
   }
   if (dens_out)
@@ -588,7 +606,7 @@ static kfbi_status solve_bvp_on(Ctx& c, const double* f_grid, const double* f_ct
   KFBI_CUDA_TRY(cudaMemcpyAsync(&timeout, c.err_flag + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
   KFBI_CUDA_TRY(cudaStreamSynchronize(st));
   if (timeout) {
-    set_error("kfbi_solve_bvp: a staged line copy did not complete (bounded wait expired)");
+    set_error("BVP solve: a staged line copy did not complete (bounded wait expired)");
     return KFBI_ERR_TIMEOUT;
   }
   const double rel = gnorm > 0 ? res / gnorm : 0.0;
@@ -654,7 +672,7 @@ kfbi_status batch_solve(kfbi_ctx* ctxs, int count, int nrhs, const double* const
         const int q = p * nrhs + r;
         const kfbi_status s = solve_bvp(c, f_grid[q], f_ctrl[q], g_ctrl[q], u_grid[q],
                                         dens_out ? dens_out[q] : nullptr,
-                                        info ? info + q : nullptr);
+                                        info ? info + q : nullptr, kOpDirichlet);
         if (s == KFBI_ERR_NOT_CONVERGED) {
           not_converged[w] = 1;
         } else if (s != KFBI_OK) {

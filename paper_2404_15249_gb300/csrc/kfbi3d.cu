@@ -364,14 +364,21 @@ __global__ void jumps3_kernel(int P, double h, double kappa2, const int* __restr
                               const int* __restrict__ idx, const double* __restrict__ wts,
                               const double* __restrict__ nrm, const double* __restrict__ shape,
                               const double* __restrict__ frame, const double* __restrict__ dens,
-                              const double* __restrict__ fctl, double* jmp, double* fit) {
+                              const double* __restrict__ psi, const double* __restrict__ fctl,
+                              double* jmp, double* fit) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   double c[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double cp[3] = {0.0, 0.0, 0.0};     // fitted psi: value and the two tangential slopes
   if (dens)
     for (int m = ptr[p]; m < ptr[p + 1]; ++m) {
       const double v = dens[idx[m]];
       for (int r = 0; r < 6; ++r) c[r] += wts[6 * (long)m + r] * v;
+    }
+  if (psi)
+    for (int m = ptr[p]; m < ptr[p + 1]; ++m) {
+      const double v = psi[idx[m]];
+      for (int r = 0; r < 3; ++r) cp[r] += wts[6 * (long)m + r] * v;
     }
   const double Fj = fctl ? fctl[p] : 0.0;
   const double n[3] = {nrm[3 * p], nrm[3 * p + 1], nrm[3 * p + 2]};
@@ -387,10 +394,23 @@ __global__ void jumps3_kernel(int P, double h, double kappa2, const int* __restr
   for (int a = 0; a < 3; ++a) gG[a] = g1 * t[0][a] + g2 * t[1][a];
   double SgG[3];
   for (int a = 0; a < 3; ++a) SgG[a] = S[a][0] * gG[0] + S[a][1] * gG[1] + S[a][2] * gG[2];
-  const double mixed[2] = {-(t[0][0] * SgG[0] + t[0][1] * SgG[1] + t[0][2] * SgG[2]),
-                           -(t[1][0] * SgG[0] + t[1][1] * SgG[1] + t[1][2] * SgG[2])};
-  const double tan_[2][2] = {{H11, H12}, {H12, H22}};
-  const double nn = Fj + kappa2 * c[0] - (H11 + H22);
+  // single layer: [v_n] = psi~, the tangential block gains psi~ II (II_su = t_s . S t_u), the
+  // mixed terms the tangential gradient of psi, the normal-normal term -tr(S) psi~
+  const double ps = cp[0];
+  double II[2][2];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      double v = 0.0;
+      for (int q = 0; q < 3; ++q)
+        for (int r = 0; r < 3; ++r) v += t[a][q] * S[q][r] * t[b][r];
+      II[a][b] = v;
+    }
+  const double mixed[2] = {cp[1] * inv_h - (t[0][0] * SgG[0] + t[0][1] * SgG[1] + t[0][2] * SgG[2]),
+                           cp[2] * inv_h - (t[1][0] * SgG[0] + t[1][1] * SgG[1] + t[1][2] * SgG[2])};
+  const double tan_[2][2] = {{H11 + ps * II[0][0], H12 + ps * II[0][1]},
+                             {H12 + ps * II[1][0], H22 + ps * II[1][1]}};
+  const double nn = Fj + kappa2 * c[0] - (H11 + H22) - (S[0][0] + S[1][1] + S[2][2]) * ps;
+  for (int a = 0; a < 3; ++a) gG[a] += ps * n[a];
   double H[3][3];
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) {
@@ -760,11 +780,12 @@ kfbi_status setup_geometry3(Ctx& c) {
 }
 
 // ============================================================================ apply
-static kfbi_status jumps3(Ctx& c, const double* dens, const double* fctl, bool fit) {
+static kfbi_status jumps3(Ctx& c, const double* dens, const double* fctl, bool fit,
+                          const double* psi = nullptr) {
   const int pr = prof_begin(c, ST_CORR);
   jumps3_kernel<<<nblk(c.M, 128), 128, 0, c.stream>>>(c.M, c.h, c.kappa2, c.ls_ptr, c.ls_idx,
-                                                      c.ls_w, c.nrm, c.curv, c.frame, dens, fctl,
-                                                      c.jmp3, fit ? c.fit3 : nullptr);
+                                                      c.ls_w, c.nrm, c.curv, c.frame, dens, psi,
+                                                      fctl, c.jmp3, fit ? c.fit3 : nullptr);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
@@ -830,12 +851,14 @@ static kfbi_status plain_solve3(Ctx& c, int precision, const float* b, float* v)
   return precision == KFBI_TF32X3 ? box_solve_tc(c, b, v) : box_solve3_f32(c, b, v);
 }
 
-kfbi_status apply_potential3(Ctx& c, Layer layer, int precision, const double* dens, double* out) {
-  if (layer != Layer::Double) {
-    set_error("single-layer potential: 2-D only");
-    return KFBI_ERR_UNSUPPORTED;
-  }
-  KFBI_TRY(jumps3(c, dens, nullptr, true));
+// Double layer: jumps of the fitted density plus half the fit's residual at the points
+// (reading S10); single layer ([v] = 0, [d_n v] = psi): jumps of the fitted psi, no
+// identity part (dens below is then the density used only by that part: null).
+kfbi_status apply_potential3(Ctx& c, Layer layer, int precision, const double* density,
+                             double* out) {
+  const bool single = layer == Layer::Single;
+  const double* dens = single ? nullptr : density;
+  KFBI_TRY(jumps3(c, dens, nullptr, !single, single ? density : nullptr));
   const int steps = steps_of(precision);
   if (use_fp32(precision)) {
     KFBI_TRY(correct3<float>(c, c.B32, 0, steps ? c.B64 : nullptr));

@@ -99,6 +99,9 @@ struct Prof {
 
 // ------------------------------------------------------------------ context
 constexpr int kStepGraphs = 5;   // precisions KFBI_FP64 .. KFBI_TF32X3
+constexpr int kOpDirichlet = 0;  // GMRES operator: v^+ of the double layer (K_D)
+constexpr int kOpNeumann = 1;    // GMRES operator: d_n v^+ of the single layer (K_N)
+constexpr int kOps = 2;
 
 struct Ctx {
   // problem (dim 2: M control points on a curve; dim 3: M grid-line intersection points)
@@ -145,6 +148,11 @@ struct Ctx {
   double* ctrl_cD = nullptr;                  // M x 6 density weights of the jump Taylor terms
   double* ctrl_cS = nullptr;                  // M x 6 (single layer)
   double* ctrl_eF = nullptr;                  // M   f(z) weight of the jump Taylor terms
+  // the same four for the normal derivative n . grad of the fitted quadratic at z
+  double* ctrl_wn = nullptr;
+  double* ctrl_cDn = nullptr;
+  double* ctrl_cSn = nullptr;
+  double* ctrl_eFn = nullptr;
 
   // 3-D interface: line CSR per axis, least-squares stencils, interpolation stencils
   int npts_axis[3] = {0, 0, 0};
@@ -199,8 +207,10 @@ struct Ctx {
   int* gm_j = nullptr;         // Arnoldi step index within the cycle (device)
   double* d_flags = nullptr;   // device address of h_pinned + 8 (host-mapped flag slots)
   // one captured CUDA graph per matvec precision for the whole Arnoldi step
-  cudaGraphExec_t step_exec[kStepGraphs] = {};
-  long long step_launches[kStepGraphs][KFBI_NSTAGES] = {};
+  // (per BIE operator: kOpDirichlet, kOpNeumann)
+  cudaGraphExec_t step_exec[kOps][kStepGraphs] = {};
+  long long step_launches[kOps][kStepGraphs][KFBI_NSTAGES] = {};
+  int gm_op = 0;               // operator of the solve in progress
   bool graphs_ok = true;       // false: direct launches (KFBI_GRAPHS=0, or capture failed)
   int graph_m = 0;             // restart length the graphs were captured with
   double* gm_part = nullptr;       // per-block partial dot products
@@ -249,14 +259,17 @@ kfbi_status autotune_f64(Ctx& c);
 
 // apply stages (apply2d.cu)
 enum class Layer { Double, Single };
-kfbi_status apply_potential(Ctx& c, Layer layer, int precision, const double* dens, double* out);
+// dn: the normal derivative d_n v^+ at the control points instead of v^+ (2-D)
+kfbi_status apply_potential(Ctx& c, Layer layer, int precision, const double* dens, double* out,
+                            bool dn = false);
+// psi: single-layer density ([d_n v] = psi, 2-D), may be null
 kfbi_status interface_solve(Ctx& c, int precision, const double* dens, const double* f_grid,
                             const double* f_ctrl, double* rhs_grid, double* v_grid,
-                            double* out);
+                            double* out, const double* psi = nullptr, bool dn = false);
 kfbi_status box_solve_grid(Ctx& c, int precision, const double* b_grid, double* v_grid);
 kfbi_status inside_mask(Ctx& c, uint8_t* mask);
 kfbi_status combined_u(Ctx& c, int precision, const double* dens, const double* f_grid,
-                       const double* f_ctrl, double* u_grid);
+                       const double* f_ctrl, double* u_grid, const double* psi = nullptr);
 inline bool valid_precision(int p) {
   return p == KFBI_FP64 || p == KFBI_MIXED_FP32 || p == KFBI_FP32_REFINED ||
          p == KFBI_FP32_REFINED_ONCE || p == KFBI_TF32X3;
@@ -286,7 +299,7 @@ kfbi_status inside_mask3(Ctx& c, uint8_t* mask);
 
 // solver (gmres.cu)
 kfbi_status solve_bvp(Ctx& c, const double* f_grid, const double* f_ctrl, const double* g_ctrl,
-                      double* u_grid, double* dens_out, kfbi_solve_info* info);
+                      double* u_grid, double* dens_out, kfbi_solve_info* info, int op);
 kfbi_status alloc_gmres(Ctx& c, int m);
 void drop_step_graphs(Ctx& c);   // the captured Arnoldi-step graphs (recaptured on use)
 kfbi_status batch_solve(kfbi_ctx* ctxs, int count, int nrhs, const double* const* f_grid,

@@ -490,10 +490,13 @@ __global__ void arm_weights_kernel(int N, int M, double lo, double h, double kap
 // nodes c, c+-e_x, c+-e_y, c + s_x e_x + s_y e_y; closed-form quadratic interpolation
 // weights at z; the second-order Taylor expansion of the jump about z is added at
 // outside nodes, folded into density / f weights.
+// With cwn/cDn/cSn/eFn: the same for n . grad of the quadratic at z (the Neumann data d_n v^+):
+// the cardinal weights differentiated in the local coordinates (A, B) and divided by h.
 __global__ void ctrl_weights_kernel(int N, int M, double lo, double h, double kappa2,
                                     const double* pts, const double* nrm, const double* curv,
                                     const uint8_t* inside, int* cnode, double* cw, double* cD,
-                                    double* cS, double* eF, int* err) {
+                                    double* cS, double* eF, double* cwn, double* cDn,
+                                    double* cSn, double* eFn, int* err) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= M) return;
   const double zx = pts[2 * k], zy = pts[2 * k + 1];
@@ -510,38 +513,58 @@ __global__ void ctrl_weights_kernel(int N, int M, double lo, double h, double ka
   w[3] = 0.5 * B + 0.5 * B * B - 0.5 * SAB * (sy + 1);
   w[4] = -0.5 * B + 0.5 * B * B + 0.5 * SAB * (sy - 1);
   w[5] = SAB;
+  // d w / d A and d w / d B (A = (z_x - x_c)/h, B = (z_y - y_c)/h)
+  const double SA = S * A, SB = S * B;
+  const double wA[6] = {-2.0 * A + SB, 0.5 + A - 0.5 * SB * (sx + 1), -0.5 + A + 0.5 * SB * (sx - 1),
+                        -0.5 * SB * (sy + 1), 0.5 * SB * (sy - 1), SB};
+  const double wB[6] = {-2.0 * B + SA, -0.5 * SA * (sx + 1), 0.5 * SA * (sx - 1),
+                        0.5 + B - 0.5 * SA * (sy + 1), -0.5 + B + 0.5 * SA * (sy - 1), SA};
   const double dt = 2.0 * M_PI / M;
   double L0[6], L1[6], L2[6], D1[6], D2[6];
   lagrange6(0.0, L0, L1, L2);
   const CurvePoint cp = curve_point(pts, M, k, L1, L2, dt);
   surface_weights(L1, L2, dt, cp.sp, cp.spp, D1, D2);
   const double nx = nrm[2 * k], ny = nrm[2 * k + 1], tx = -ny, ty = nx, chi = curv[k];
+  double wn[6];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) wn[p] = (nx * wA[p] + ny * wB[p]) / h;
   double accD[6] = {0, 0, 0, 0, 0, 0}, accS[6] = {0, 0, 0, 0, 0, 0}, accF = 0.0;
+  double accDn[6] = {0, 0, 0, 0, 0, 0}, accSn[6] = {0, 0, 0, 0, 0, 0}, accFn = 0.0;
 #pragma unroll
   for (int p = 0; p < 6; ++p) {
     const int ii = ci + oi[p], jj = cj + oj[p];
     const bool interior = ii >= 1 && jj >= 1 && ii <= N - 1 && jj <= N - 1;
     cnode[6 * k + p] = interior ? jj * N + ii : -1;
     cw[6 * k + p] = w[p];
+    cwn[6 * k + p] = wn[p];
     if (inside[jj * (N + 1) + ii]) continue;
     const double px = grid_coord(lo, ii, h) - zx, py = grid_coord(lo, jj, h) - zy;
     const double dn = px * nx + py * ny, dtau = px * tx + py * ty;
 #pragma unroll
     for (int r = 0; r < 6; ++r) {
-      accD[r] += w[p] * (L0[r] + dtau * D1[r] +
-                         0.5 * (kappa2 * dn * dn * L0[r] + (dtau * dtau - dn * dn) * D2[r] -
-                                2.0 * chi * dn * dtau * D1[r]));
-      accS[r] += w[p] * (dn * L0[r] + 0.5 * (chi * (dtau * dtau - dn * dn) * L0[r] +
-                                             2.0 * dn * dtau * D1[r]));
+      // the jump's Taylor term at node p as weights of the density (D) and psi (S)
+      const double tD = L0[r] + dtau * D1[r] +
+                        0.5 * (kappa2 * dn * dn * L0[r] + (dtau * dtau - dn * dn) * D2[r] -
+                               2.0 * chi * dn * dtau * D1[r]);
+      const double tS = dn * L0[r] + 0.5 * (chi * (dtau * dtau - dn * dn) * L0[r] +
+                                            2.0 * dn * dtau * D1[r]);
+      accD[r] += w[p] * tD;
+      accS[r] += w[p] * tS;
+      accDn[r] += wn[p] * tD;
+      accSn[r] += wn[p] * tS;
     }
     accF += w[p] * 0.5 * dn * dn;
+    accFn += wn[p] * 0.5 * dn * dn;
   }
 #pragma unroll
   for (int r = 0; r < 6; ++r) {
     cD[6 * k + r] = accD[r];
     cS[6 * k + r] = accS[r];
+    cDn[6 * k + r] = accDn[r];
+    cSn[6 * k + r] = accSn[r];
   }
   eF[k] = accF;
+  eFn[k] = accFn;
 }
 
 // ------------------------------------------------------------------ host driver
@@ -715,10 +738,15 @@ kfbi_status setup_geometry(Ctx& c) {
   KFBI_TRY(alloc_bytes(c, (void**)&c.ctrl_cD, sizeof(double) * 6 * M));
   KFBI_TRY(alloc_bytes(c, (void**)&c.ctrl_cS, sizeof(double) * 6 * M));
   KFBI_TRY(alloc_bytes(c, (void**)&c.ctrl_eF, sizeof(double) * M));
+  KFBI_TRY(alloc_bytes(c, (void**)&c.ctrl_wn, sizeof(double) * 6 * M));
+  KFBI_TRY(alloc_bytes(c, (void**)&c.ctrl_cDn, sizeof(double) * 6 * M));
+  KFBI_TRY(alloc_bytes(c, (void**)&c.ctrl_cSn, sizeof(double) * 6 * M));
+  KFBI_TRY(alloc_bytes(c, (void**)&c.ctrl_eFn, sizeof(double) * M));
   prof_count(c, ST_SETUP);
   ctrl_weights_kernel<<<nblk(M, 128), 128, 0, st>>>(N, M, c.lo, c.h, c.kappa2, c.pts, c.nrm,
                                                     c.curv, c.inside, c.ctrl_node, c.ctrl_w,
-                                                    c.ctrl_cD, c.ctrl_cS, c.ctrl_eF, c.err_flag);
+                                                    c.ctrl_cD, c.ctrl_cS, c.ctrl_eF, c.ctrl_wn,
+                                                    c.ctrl_cDn, c.ctrl_cSn, c.ctrl_eFn, c.err_flag);
   KFBI_CUDA_TRY(cudaGetLastError());
   KFBI_CUDA_TRY(cudaMemcpyAsync(&h_err, c.err_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   KFBI_CUDA_TRY(cudaStreamSynchronize(st));

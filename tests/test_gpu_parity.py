@@ -292,3 +292,60 @@ def test_fp32_column_pass_variants(N, variant, monkeypatch):
     ref = O.apply_interface(geom, psi=psi)
     assert rel(ctx.apply_layer_potential(psi, 1, K.KFBI_MIXED_FP32).cpu().numpy(), ref) < 2e-5
     ctx.close()
+
+
+@pytest.mark.parametrize("case", ["flower128_poisson", "ellipse256_k10", "flower96_k1"])
+def test_normal_derivative_applies_parity(case):
+    """d_n v^+ of the single and double layer and of the volume term (Procedure 2's Neumann
+    data) against the oracle: FP64 and twice-refined FP32 within 1e-11 (1e-10 refined at the
+    gradient's 1/h weighting), plain FP32 within 1e-3."""
+    prob = CASES[case]()
+    ctx, geom = make(prob)
+    psi = W.random_density(prob.iface.M, seed=31)
+    ref = O.apply_single_layer_dn(geom, psi)
+    assert rel(ctx.apply_layer_potential_dn(psi, 1, K.KFBI_FP64).cpu().numpy(), ref) < 1e-11
+    assert rel(ctx.apply_layer_potential_dn(psi, 1, K.KFBI_FP32_REFINED).cpu().numpy(), ref) < 1e-10
+    assert rel(ctx.apply_layer_potential_dn(psi, 1, K.KFBI_MIXED_FP32).cpu().numpy(), ref) < 1e-3
+    refd = O.apply_interface_dn(geom, phi=psi)
+    assert rel(ctx.apply_layer_potential_dn(psi, 0, K.KFBI_FP64).cpu().numpy(), refd) < 1e-11
+    fg, fc = prob.f_grid(), prob.f_ctrl()
+    assert rel(ctx.apply_volume_dn(fg, fc).cpu().numpy(), O.apply_volume_dn(geom, fg, fc)) < 1e-11
+    ctx.close()
+
+
+NEUMANN_CASES = {
+    "ellipse128_k1": lambda: W.config_helmholtz(128, 1.0, "ellipse"),
+    "flower192_k10": lambda: W.config_helmholtz(192, 10.0, "flower"),
+}
+
+
+@pytest.mark.parametrize("case", list(NEUMANN_CASES))
+def test_solve_neumann_fp64_matches_oracle(case):
+    """Neumann BVP (single-layer density): plain FP64 GMRES against the oracle's, both run
+    to 1e-13: density and u within 1e-10."""
+    prob = NEUMANN_CASES[case]()
+    ctx, geom = make(prob, tol=1e-13)
+    fg, fc, gn = prob.f_grid(), prob.f_ctrl(), prob.gn_ctrl()
+    u, psi, info = ctx.solve_neumann_bvp(fg, fc, gn)
+    u_o, psi_o, info_o = O.solve_neumann_bvp(geom, fg, fc, gn, tol=1e-13)
+    assert info["converged"] and info_o["converged"]
+    assert rel(psi.cpu().numpy(), psi_o) < 1e-10
+    assert rel(u.cpu().numpy(), u_o) < 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", list(NEUMANN_CASES))
+def test_solve_neumann_mixed_precision(case):
+    """Mixed-precision Neumann solve (relaxed FP32 matvecs, refined FP64-accurate cycle
+    residuals): density within 1e-6 of the oracle, u closer to the oracle's than the
+    oracle's is to the exact solution."""
+    prob = NEUMANN_CASES[case]()
+    ctx, geom = make(prob, precision=K.KFBI_MIXED_FP32, tol=1e-10)
+    fg, fc, gn = prob.f_grid(), prob.f_ctrl(), prob.gn_ctrl()
+    u, psi, info = ctx.solve_neumann_bvp(fg, fc, gn)
+    u_o, psi_o, _ = O.solve_neumann_bvp(geom, fg, fc, gn, tol=1e-12)
+    assert info["converged"] and info["applies_low"] > 0
+    assert rel(psi.cpu().numpy(), psi_o) < 1e-6
+    disc = np.max(np.abs(u_o - prob.u_grid())[geom.inside])
+    assert np.max(np.abs(u.cpu().numpy() - u_o)[geom.inside]) < disc
+    ctx.close()

@@ -179,11 +179,26 @@ def test_missing_point_is_a_geometry_error():
     assert e.value.status == 2
 
 
-def test_single_layer_is_unsupported_in_3d():
+@pytest.mark.parametrize("case", ["ellipsoid32_k0", "sphere48_k2", "star64_k0"])
+def test_single_layer_apply_parity(case):
+    """3-D single layer ([v] = 0, [d_n v] = psi; jumps of the fitted psi): v^+ at the points
+    against the oracle's interface problem with psi, FP64 and refined FP32 within 1e-11,
+    plain FP32 within 1e-4."""
+    prob = CASES[case]()
+    ctx, geom = make(prob)
+    psi = S3.random_density3(geom.P, prob.iface.pts, seed=17)
+    ref = O3.apply_interface(geom, psi=psi)
+    assert rel(ctx.apply_layer_potential(psi, K.KFBI_SINGLE_LAYER, K.KFBI_FP64).cpu().numpy(), ref) < 1e-11
+    assert rel(ctx.apply_layer_potential(psi, K.KFBI_SINGLE_LAYER, K.KFBI_FP32_REFINED).cpu().numpy(), ref) < 1e-11
+    assert rel(ctx.apply_layer_potential(psi, K.KFBI_SINGLE_LAYER, K.KFBI_MIXED_FP32).cpu().numpy(), ref) < 1e-4
+    ctx.close()
+
+
+def test_neumann_data_is_unsupported_in_3d():
     prob = CASES["ellipsoid32_k0"]()
     ctx, geom = make(prob)
     with pytest.raises(K.KfbiError) as e:
-        ctx.apply_layer_potential(np.ones(geom.P), K.KFBI_SINGLE_LAYER, K.KFBI_FP64)
+        ctx.apply_layer_potential_dn(np.ones(geom.P), K.KFBI_SINGLE_LAYER, K.KFBI_FP64)
     assert e.value.status == 8
     ctx.close()
 
