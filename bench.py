@@ -56,6 +56,8 @@ def parse():
                     help="grid size of the tensor-core box-solve measurement (0: skip)")
     ap.add_argument("--batch", type=int, default=256,
                     help="problems in the batched companion measurement (0: skip)")
+    ap.add_argument("--nneu", type=int, default=2048,
+                    help="grid size of the Neumann BVP companion measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -472,6 +474,9 @@ def run_kfbi(a):
     batch = None
     if rank == 0 and a.batch > 0:
         batch = run_batch_companion(a, dev)
+    neu = None
+    if rank == 0 and a.nneu > 0:
+        neu = run_neumann_companion(a.nneu, dev, flush)
     tc = None
     if rank == 0 and a.ntc > 0:
         tc = run_tc_companion(a, dev, flush, ctx, N) if N % 128 == 0 and N <= 8192 else None
@@ -506,6 +511,7 @@ def run_kfbi(a):
             **fp64,
             "companion_3d": companion,
             "companion_batch": batch,
+            "companion_neumann": neu,
             "companion_tc": tc}
     ctx.close()
     if rank == 0:
@@ -601,6 +607,56 @@ def run_3d_companion(N, dev, flush):
             "err_inf_mixed": err_mixed, "fp64_solve_ms": ms64, "err_inf_fp64": err64,
             "fp64_iterations": info64["iterations"], "speedup_vs_fp64": ms64 / ms_mixed,
             "box_solve_fft_vs_tc": tc}
+
+
+def run_neumann_companion(N, dev, flush):
+    """The Neumann BVP (d_n u given on Gamma, single-layer density) on the 2-D Helmholtz
+    configuration's ellipse (kappa = 1, u = exp(x) sin(2y), M = 2N): mixed-precision and
+    plain FP64 solves timed with CUDA events (L2 flushed before each), errors against the
+    exact solution.  Reported beside the 2-D line."""
+    import numpy as np
+    import torch
+    import kfbi_workloads as W
+    import paper_2404_15249_gb300 as K
+
+    prob = W.config_helmholtz(N, 1.0, "ellipse")
+    ctx = K.Kfbi2D(prob.iface.pts, prob.iface.normals, prob.iface.curv, N, 1.0,
+                   precision=K.KFBI_MIXED_FP32, tol=1e-10)
+    fg = torch.as_tensor(prob.f_grid(), device=dev)
+    fc = torch.as_tensor(prob.f_ctrl(), device=dev)
+    gn = torch.as_tensor(prob.gn_ctrl(), device=dev)
+    u = torch.empty((N + 1, N + 1), dtype=torch.float64, device=dev)
+    inside = ctx.inside_mask().cpu().numpy().astype(bool)
+    st = torch.cuda.current_stream()
+
+    def timed(n):
+        out, info = [], None
+        for _ in range(n):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _, _, info = ctx.solve_neumann_bvp(fg, fc, gn, u_out=u)
+            e1.record(st)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        err = float(np.max(np.abs(u.cpu().numpy() - prob.u_grid())[inside]))
+        return statistics.mean(out), info, err
+
+    ctx.solve_neumann_bvp(fg, fc, gn, u_out=u)
+    ms_mixed, info, err_mixed = timed(3)
+    ctx.set_solver(K.KFBI_FP64, 50, 20, 1e-10, 1e-5)
+    ctx.solve_neumann_bvp(fg, fc, gn, u_out=u)
+    ms64, info64, err64 = timed(2)
+    ctx.close()
+    applies = info["applies_fp64"] + info["applies_low"]
+    return {"workload": f"2-D modified Helmholtz Neumann BVP, ellipse (0.7, 0.4, 30 deg), "
+                        f"N={N}, M={2 * N}, kappa=1, u = exp(x) sin(2y), single-layer density, "
+                        f"GMRES(50) to 1e-10",
+            "N": N, "mixed_solve_ms": ms_mixed,
+            "grid_pts_per_s_per_apply": (N + 1) ** 2 * applies / (ms_mixed / 1e3),
+            "iterations": info["iterations"], "applies_low": info["applies_low"],
+            "err_inf_mixed": err_mixed, "fp64_solve_ms": ms64, "err_inf_fp64": err64,
+            "fp64_iterations": info64["iterations"], "speedup_vs_fp64": ms64 / ms_mixed}
 
 
 def run_tc_companion(a, dev, flush, main_ctx, main_N):
