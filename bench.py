@@ -226,11 +226,13 @@ DST_STAGES = ("dst_rows_f32", "dst_cols_f32", "dst_tri_f32", "sparse_x_f32", "tr
 def dst_stage_roofline(stage_ms, N, solves):
     """The box-solve (DST) stage of the mixed solve as a whole against the HBM roofline:
     algorithmic bytes 24 B per interior unknown for a box solve of a dense right-hand side
-    (three passes, each reading and writing the FP32 grid once) and 16 B for the sparse
-    right-hand side of a plain double-layer apply (its first x-transform reads only the
-    irregular nodes), over the summed device time of the stage's kernels.  A plain apply
-    runs one sparse x-transform and one row pass, a dense box solve two row passes, so
-    the counts follow from the launches of the two kernels."""
+    (three passes, each reading and writing the FP32 grid once) and 16 B for a plain
+    double-layer apply (its first x-transform reads only the irregular nodes and writes
+    the grid, the y-pass reads and writes it, the last x-transform reads it and writes
+    only the stencil nodes), over the summed device time of the stage's kernels.  The
+    y-pass runs two streams at once and is timed as one wall-clock span, so no interval
+    is counted twice.  A plain apply runs one sparse x-transform and one row pass, a dense
+    box solve two row passes, so the counts follow from the launches of the two kernels."""
     ms = sum(stage_ms[k][0] for k in DST_STAGES if k in stage_ms)
     if ms <= 0 or solves <= 0:
         return None

@@ -151,8 +151,8 @@ __global__ void split_kernel(long n, const double* __restrict__ b, float* __rest
 // plain FP32 apply fuses the correction gather (Alg. 2) with the first sine transform
 // (along x, Alg. 4) and writes the transformed rows straight into the work grid:
 //   X[j][k] = sum over irregular (i, j) of b_ij sin(pi i k / N).
-// One CTA per grid row j (T threads in W = T/32 warps).  Warp w prepares the row's nodes
-// q = w, w + W, ...: lanes over (crossed arm, weight) pairs form b_ij from the density (up
+// One CTA per work item: a grid row j, or a part of the nodes of a row with many (T threads
+// in W = T/32 warps).  Warp w prepares the item's nodes q = w, w + W, ...: lanes over (crossed arm, weight) pairs form b_ij from the density (up
 // to 4 x 6 FP64 products gathered at once, summed by shuffles), and the node's phase
 // tables go to shared memory: e^{i pi i l / N} for the lanes l < 32, e^{i pi i 32 v / N}
 // for the warps v < W, and the rotation e^{i pi i T / N}.  Then thread t = 32 v + l
@@ -162,7 +162,9 @@ __global__ void split_kernel(long n, const double* __restrict__ b, float* __rest
 //   sin(pi i (N - k) / N)    = (-1)^(i+1) sin theta,
 //   sin(pi i (N/2 +- k) / N) = sin(pi i / 2 +- theta) = +-sin theta or cos theta by i mod 4,
 // the modes N - k, N/2 + k and N/2 - k as well.  Modes N/4 and 3N/4 come from table
-// values kept with the node.  Rows without irregular nodes are zero.
+// values kept with the node.  Rows without irregular nodes are zero.  The parts of a split
+// row write partial rows to scratch slots; the last part to arrive (a counter, reset by
+// it) adds them in part order into the row, so the result does not depend on scheduling.
 constexpr int SPX_THREADS_MAX = 256;
 constexpr int SPX_NODES = 32;          // irregular nodes of a row held in shared memory at once
 
@@ -177,22 +179,25 @@ __device__ __forceinline__ int mod_2n(int x, int n2, float inv_n2) {
 
 template <int S>
 __global__ void __launch_bounds__(SPX_THREADS_MAX)
-    sparse_rows_kernel(int N, int M, const int* __restrict__ irr_node,
-                       const int* __restrict__ rowptr, const int* __restrict__ arm_ptr,
+    sparse_rows_kernel(int N, int M, const int4* __restrict__ items,
+                       const int* __restrict__ irr_node, const int* __restrict__ arm_ptr,
                        const int* __restrict__ arm_seg, const double* __restrict__ wgt,
                        const double* __restrict__ dens, const float2* __restrict__ tw,
-                       float* __restrict__ X) {
+                       float* __restrict__ X, float* part, unsigned* counter) {
   constexpr int WMAX = SPX_THREADS_MAX / 32;
   __shared__ float2 s_lane[SPX_NODES][32];
   __shared__ float2 s_warp[SPX_NODES][WMAX];
   __shared__ float4 s_node[SPX_NODES];   // (b, rotation cos, rotation sin, i as bits)
   __shared__ float2 s_q[SPX_NODES];      // sin(pi i / 4), sin(3 pi i / 4)
-  const int j = blockIdx.x, t = threadIdx.x, T = blockDim.x;
+  __shared__ bool s_last;
+  const int t = threadIdx.x, T = blockDim.x;
   const int lane = t & 31, warp = t >> 5, nwarps = T >> 5;
   const int Q = N / 4, H = N / 2, N2 = 2 * N;
   const float inv_n2 = 1.f / (float)N2;
-  const int n0 = j > 0 ? rowptr[j - 1] : 0, n1 = j > 0 ? rowptr[j] : 0;
-  float* row = X + (size_t)j * N;
+  // item: (row, first node, end node, part), (parts, first scratch slot, counter, 0)
+  const int4 ia = items[2 * blockIdx.x], ib = items[2 * blockIdx.x + 1];
+  const int j = ia.x, n0 = ia.y, n1 = ia.z, nparts = ib.x;
+  float* row = nparts == 1 ? X + (size_t)j * N : part + (size_t)(ib.y + ia.w) * N;
   if (n1 == n0) {                                     // no irregular node: the row is zero
     for (int k = 4 * t; k < N; k += 4 * T) *reinterpret_cast<float4*>(row + k) = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
@@ -274,16 +279,189 @@ __global__ void __launch_bounds__(SPX_THREADS_MAX)
     row[Q] = aq;
     row[3 * Q] = a3q;
   }
+  if (nparts == 1) return;                            // uniform over the CTA
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(counter + ib.z, 1u) == (unsigned)(nparts - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const float4* src = reinterpret_cast<const float4*>(part + (size_t)ib.y * N);
+  float4* dst = reinterpret_cast<float4*>(X + (size_t)j * N);
+  for (int e = t; e < Q; e += T) {                    // N / 4 float4 per row
+    float4 v = __ldcg(src + e);
+    for (int p = 1; p < nparts; ++p) {
+      const float4 u = __ldcg(src + (size_t)p * Q + e);
+      v.x += u.x;
+      v.y += u.y;
+      v.z += u.z;
+      v.w += u.w;
+    }
+    dst[e] = v;
+  }
+  if (t == 0) counter[ib.z] = 0u;
+}
+
+// ------------------------------------------------------------------ sparse-output x-transform
+// The plain apply's interpolation reads the grid only at the control points' stencil nodes
+// (a few per grid row near Gamma), so its last sine transform along x is evaluated there
+// only:  v[j][i] = sum_k Y[j][k] sin(pi i k / N)  for the listed nodes (i, j).  One CTA per
+// work item (a row's nodes, or a part of them: a few each, longest items first); thread
+// t = 32 w + l of T takes the modes k = 1 + t + T s (s < S, k < N/4) and, by the symmetries
+// used in sparse_rows_kernel, the modes N - k, N/2 + k and N/2 - k with the same (cos, sin)
+// of theta = pi i k / N:
+//   v = sum_k sin(theta) A_k + cos(theta) B_k,
+//   i = 0 mod 4: A = (Y_k - Y_{N-k}) + (Y_{N/2+k} - Y_{N/2-k}),  B = 0
+//   i = 1 mod 4: A = Y_k + Y_{N-k},  B = Y_{N/2+k} + Y_{N/2-k}
+//   i = 2 mod 4: A = (Y_k - Y_{N-k}) - (Y_{N/2+k} - Y_{N/2-k}),  B = 0
+//   i = 3 mod 4: A = Y_k + Y_{N-k},  B = -(Y_{N/2+k} + Y_{N/2-k})
+// plus the modes N/2 (sin(pi i / 2)), N/4 and 3N/4 (sin(pi i / 4), sin(3 pi i / 4)).  The
+// phase of thread t starts at the product of per-node lane and warp factors
+// e^{i pi i (1 + l) / N} e^{i pi i 32 w / N} kept in shared memory, advances by the rotation
+// e^{i pi i T / N} and is re-seeded every 4 steps from e^{i pi i 4 T r / N} (no long rotation
+// chains); the warp sums of each node go through shared memory to one total.
+constexpr int SPO_T = 128;
+constexpr int SPO_NODES = 32;              // nodes of an item per batch
+
+template <int S>
+__global__ void __launch_bounds__(SPO_T)
+    sparse_out_kernel(int N, const float* __restrict__ Y, const int4* __restrict__ items,
+                      const int* __restrict__ col, const float2* __restrict__ tw,
+                      float* __restrict__ out) {
+  constexpr int WMAX = SPO_T / 32, RS = (S + 3) / 4;
+  __shared__ float2 s_lane[SPO_NODES][32];
+  __shared__ float2 s_warp[SPO_NODES][WMAX];
+  __shared__ float2 s_seed[SPO_NODES][RS];
+  __shared__ float2 s_rot[SPO_NODES];
+  __shared__ float s_part[SPO_NODES][WMAX];
+  __shared__ int s_col[SPO_NODES];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int lane = t & 31, warp = t >> 5, nwarps = T >> 5;
+  const int Q = N / 4, H = N / 2, N2 = 2 * N;
+  const float inv_n2 = 1.f / (float)N2;
+  const int4 item = items[blockIdx.x];                 // (row, first node, end node, 0)
+  const int j = item.x, n0 = item.y, n1 = item.z;
+  const float* row = Y + (size_t)j * N;
+  // the thread's mode combinations: sums and differences of the four symmetric modes
+  float a12[S], d12[S], a34[S], d34[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int k = 1 + t + s * T;
+    float y1 = 0.f, y2 = 0.f, y3 = 0.f, y4 = 0.f;
+    if (k < Q) {
+      y1 = row[k];
+      y2 = row[N - k];
+      y3 = row[H + k];
+      y4 = row[H - k];
+    }
+    a12[s] = y1 + y2;
+    d12[s] = y1 - y2;
+    a34[s] = y3 + y4;
+    d34[s] = y3 - y4;
+  }
+  const float yh = row[H], yq = row[Q], y3q = row[3 * Q];
+  for (int base = n0; base < n1; base += SPO_NODES) {
+    const int cnt = min(SPO_NODES, n1 - base);
+    __syncthreads();                                   // previous batch's tables consumed
+    for (int q = warp; q < cnt; q += nwarps) {         // per-node phase tables
+      const int i = col[base + q];
+      const float2 pl = tw[mod_2n(i * (1 + lane), N2, inv_n2)];
+      s_lane[q][lane] = make_float2(pl.x, -pl.y);
+      if (lane < nwarps) {
+        const float2 pw = tw[mod_2n(i * 32 * lane, N2, inv_n2)];
+        s_warp[q][lane] = make_float2(pw.x, -pw.y);
+      }
+      if (lane < RS) {
+        const float2 ps = tw[mod_2n(i * 4 * T * lane, N2, inv_n2)];
+        s_seed[q][lane] = make_float2(ps.x, -ps.y);
+      }
+      if (lane == 0) {
+        const float2 pr = tw[mod_2n(i * T, N2, inv_n2)];
+        s_rot[q] = make_float2(pr.x, -pr.y);
+        s_col[q] = i;
+      }
+    }
+    __syncthreads();
+    for (int q = 0; q < cnt; ++q) {
+      const int i = s_col[q];
+      const int cls = i & 3;
+      const float2 pl = s_lane[q][lane], pw = s_warp[q][warp], rot = s_rot[q];
+      const float c0 = pl.x * pw.x - pl.y * pw.y;      // e^{i pi i (1 + t) / N}
+      const float s0 = fmaf(pl.x, pw.y, pl.y * pw.x);
+      float cs = c0, sn = s0, acc = 0.f;
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        if (s > 0 && (s & 3) == 0) {                   // re-seed from the table
+          const float2 sd = s_seed[q][s >> 2];
+          cs = c0 * sd.x - s0 * sd.y;
+          sn = fmaf(c0, sd.y, s0 * sd.x);
+        }
+        const float A = (cls & 1) ? a12[s] : (cls == 0 ? d12[s] + d34[s] : d12[s] - d34[s]);
+        const float B = (cls & 1) ? (cls == 1 ? a34[s] : -a34[s]) : 0.f;
+        acc = fmaf(sn, A, fmaf(cs, B, acc));
+        const float cn = cs * rot.x - sn * rot.y;
+        sn = fmaf(sn, rot.x, cs * rot.y);
+        cs = cn;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) s_part[q][warp] = acc;
+    }
+    __syncthreads();
+    for (int q = t; q < cnt; q += T) {                 // totals and the special modes
+      const int i = s_col[q];
+      float v = 0.f;
+      for (int w = 0; w < nwarps; ++w) v += s_part[q][w];
+      const float sh = (i & 1) ? ((i & 3) == 1 ? 1.f : -1.f) : 0.f;     // sin(pi i / 2)
+      v = fmaf(yh, sh, v);
+      v = fmaf(yq, -tw[mod_2n(i * Q, N2, inv_n2)].y, v);
+      v = fmaf(y3q, -tw[mod_2n(i * 3 * Q, N2, inv_n2)].y, v);
+      out[base + q] = v;
+    }
+  }
+}
+
+template <int S>
+static void launch_sparse_out(Ctx& c, int T, const float* Y) {
+  sparse_out_kernel<S><<<c.sn_nitems, T, 0, c.stream>>>(
+      c.N, Y, reinterpret_cast<const int4*>(c.sn_items), c.sn_col,
+      reinterpret_cast<const float2*>(c.t32.tw), c.sn_val);
+}
+
+// threads per item: the N/4 - 1 modes rounded up to a warp, at most 128; S steps each
+static kfbi_status sparse_out(Ctx& c, const float* Y) {
+  if (c.sn_nitems == 0) return KFBI_OK;
+  const int Q = c.N / 4;
+  const int T = Q - 1 >= SPO_T ? SPO_T : ((Q - 1 + 31) / 32) * 32;
+  const int S = (Q - 1 + T - 1) / T;
+  const int pr = prof_begin(c, ST_ROWS32);
+  switch (S) {
+    case 1: launch_sparse_out<1>(c, T, Y); break;
+    case 2: launch_sparse_out<2>(c, T, Y); break;
+    case 3: launch_sparse_out<3>(c, T, Y); break;
+    case 4: launch_sparse_out<4>(c, T, Y); break;
+    case 6: launch_sparse_out<6>(c, T, Y); break;
+    case 8: launch_sparse_out<8>(c, T, Y); break;
+    case 12: launch_sparse_out<12>(c, T, Y); break;
+    case 16: launch_sparse_out<16>(c, T, Y); break;
+    default:
+      prof_end(c, pr);
+      set_error("sparse-output x-transform: N = %d not supported", c.N);
+      return KFBI_ERR_UNSUPPORTED;
+  }
+  prof_end(c, pr);
+  KFBI_CUDA_TRY(cudaGetLastError());
+  return KFBI_OK;
 }
 
 template <int S>
 static void launch_sparse_rows(Ctx& c, int T, const double* wgt, const double* dens, float* X) {
-  sparse_rows_kernel<S><<<c.N, T, 0, c.stream>>>(c.N, c.M, c.irr_node, c.irr_rowptr, c.arm_ptr,
-                                                 c.arm_seg, wgt, dens,
-                                                 reinterpret_cast<const float2*>(c.t32.tw), X);
+  sparse_rows_kernel<S><<<c.spx_nitems, T, 0, c.stream>>>(
+      c.N, c.M, reinterpret_cast<const int4*>(c.spx_items), c.irr_node, c.arm_ptr, c.arm_seg,
+      wgt, dens, reinterpret_cast<const float2*>(c.t32.tw), X, c.spx_part, c.spx_cnt);
 }
 
-// threads per row: N/4 rounded up to a warp, at most 256; S = ceil(N/4 / T) steps
+// threads per item: N/4 rounded up to a warp, at most 256; S = ceil(N/4 / T) steps
 static kfbi_status sparse_rows(Ctx& c, const double* wgt, const double* dens, float* X) {
   const int Q = c.N / 4;
   const int T = Q >= SPX_THREADS_MAX ? SPX_THREADS_MAX : ((Q + 31) / 32) * 32;
@@ -411,13 +589,15 @@ static kfbi_status correct(Ctx& c, const double* dens, const double* psi, const 
 
 // v^+ at the control points, or with dn the normal derivative d_n v^+ (the same gather with
 // the weights of n . grad of the fitted quadratic)
+// (nodes: the index of each stencil entry into v1..v3; the work-grid indices by default, the
+// slots of the compact stencil-node values for the sparse-output transform)
 template <typename T>
 static kfbi_status interp(Ctx& c, const T* v1, const float* v2, const float* v3,
                           const double* dens, const double* psi, const double* fctl,
-                          double* out, bool dn = false) {
+                          double* out, bool dn = false, const int* nodes = nullptr) {
   const int pr = prof_begin(c, ST_INTERP);
   interp_kernel<T><<<(c.M + 127) / 128, 128, 0, c.stream>>>(
-      c.M, c.ctrl_node, dn ? c.ctrl_wn : c.ctrl_w, dn ? c.ctrl_cDn : c.ctrl_cD,
+      c.M, nodes ? nodes : c.ctrl_node, dn ? c.ctrl_wn : c.ctrl_w, dn ? c.ctrl_cDn : c.ctrl_cD,
       dn ? c.ctrl_cSn : c.ctrl_cS, dn ? c.ctrl_eFn : c.ctrl_eF, v1, v2, v3, dens, psi, fctl, out);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
@@ -482,8 +662,14 @@ kfbi_status apply_potential(Ctx& c, Layer layer, int precision, const double* de
   const int steps = refine_steps_of(precision);
   if (steps == 0 && precision != KFBI_TF32X3 && c.irr_rowptr && c.dim == 2) {
     // correction fused with the first x-transform (sparse right-hand side), then the rest
-    // of the box solve on the transformed rows
+    // of the box solve on the transformed rows: with the row-layout y-pass the last
+    // x-transform is evaluated at the stencil nodes only
     KFBI_TRY(sparse_rows(c, d ? c.arm_wD : c.arm_wS, d ? d : s, c.V32));
+    if (c.cols_variant[0] & 8) {
+      KFBI_TRY(ypass_rows_f32(c, c.V32, ypass_out(c)));
+      KFBI_TRY(sparse_out(c, ypass_out(c)));
+      return interp<float>(c, c.sn_val, nullptr, nullptr, d, s, nullptr, out, dn, c.ctrl_slot);
+    }
     KFBI_TRY(box_solve_after_rows_f32(c, c.V32));
     return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out, dn);
   }

@@ -481,15 +481,34 @@ void prof_flush(Ctx& c) {
   p.used = 0;
 }
 
-int prof_begin(Ctx& c, int stage) {
+static int prof_record(Ctx& c, int stage) {
   Prof& p = c.prof;
-  ++p.launches[stage];
-  if (!p.on) return -1;
   if (p.used == kProfPairs) prof_flush(c);
   const int i = p.used++;
   p.stage[i] = stage;
   cudaEventRecord(p.ev[2 * i], c.stream);
   return i;
+}
+
+int prof_span_begin(Ctx& c, int stage) {
+  Prof& p = c.prof;
+  if (!p.on || p.hold) return -1;
+  const int i = prof_record(c, stage);
+  p.hold = true;
+  return i;
+}
+
+void prof_span_end(Ctx& c, int pair) {
+  if (pair < 0) return;
+  c.prof.hold = false;
+  cudaEventRecord(c.prof.ev[2 * pair + 1], c.stream);
+}
+
+int prof_begin(Ctx& c, int stage) {
+  Prof& p = c.prof;
+  ++p.launches[stage];
+  if (!p.on || p.hold) return -1;
+  return prof_record(c, stage);
 }
 
 void prof_end(Ctx& c, int pair) {

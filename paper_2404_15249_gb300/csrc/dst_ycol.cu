@@ -173,6 +173,12 @@ kfbi_status ypass_rows_f32(Ctx& c, const float* V, float* Y) {
     return KFBI_ERR_UNSUPPORTED;
   }
   float* L = reinterpret_cast<float*>(c.XT);                       // k0 x N low-mode lines
+  // the stage timers take the y-pass as one span on the main stream (its kernels overlap)
+  struct Span {
+    Ctx& c;
+    int pair;
+    ~Span() { prof_span_end(c, pair); }
+  } span{c, prof_span_begin(c, ST_TRI)};
   // fork: the low modes on the side stream, after everything already queued on the main one
   const cudaStream_t main_st = c.stream;
   KFBI_CUDA_TRY(cudaEventRecord(c.fork_ev, main_st));

@@ -90,6 +90,7 @@ enum Stage : int {
 
 struct Prof {
   bool on = false;
+  bool hold = false;               // inside a span timed as a whole: count launches only
   std::vector<cudaEvent_t> ev;     // 2 per timed launch
   std::vector<int> stage;          // stage of each event pair
   int used = 0;
@@ -136,6 +137,14 @@ struct Ctx {
   int nirr = 0, narms = 0;
   int* irr_node = nullptr;                    // work-grid index j*N + i
   int* irr_rowptr = nullptr;                  // 2-D: row j's nodes [rowptr[j-1], rowptr[j])
+  // work items of the sparse first x-transform (2-D), longest first: 8 ints each,
+  // (row j, first node, end node, part, parts of the row, first scratch slot of the row,
+  // arrival counter of the row, 0); a row with many irregular nodes is split into parts
+  // whose partial rows are added by the last part to finish
+  int spx_nitems = 0;
+  int* spx_items = nullptr;
+  float* spx_part = nullptr;                  // scratch rows of the split rows' parts
+  unsigned* spx_cnt = nullptr;                // arrival counters of the split rows (zero at rest)
   int* arm_ptr = nullptr;                     // nirr + 1
   int* arm_seg = nullptr;                     // narms: segment of the crossing
   double* arm_wD = nullptr;                   // narms x 6: density -> correction (double layer)
@@ -148,6 +157,14 @@ struct Ctx {
   double* ctrl_cD = nullptr;                  // M x 6 density weights of the jump Taylor terms
   double* ctrl_cS = nullptr;                  // M x 6 (single layer)
   double* ctrl_eF = nullptr;                  // M   f(z) weight of the jump Taylor terms
+  // stencil nodes of the control points by grid row (2-D): the plain FP32 apply's last
+  // x-transform is evaluated only at these sn_count nodes, in sn_nitems work items
+  int sn_count = 0, sn_nitems = 0;
+  int* ctrl_slot = nullptr;                   // M x 6: slot of each stencil entry (-1: boundary)
+  int* sn_col = nullptr;                      // column i of each node (sorted by row, column)
+  int* sn_items = nullptr;                    // 4 ints each: row j, first node, end node, 0
+                                              // (at most a few nodes each, longest first)
+  float* sn_val = nullptr;                    // the values at the nodes (FP32 work values)
   // the same four for the normal derivative n . grad of the fitted quadratic at z
   double* ctrl_wn = nullptr;
   double* ctrl_cDn = nullptr;
@@ -230,6 +247,10 @@ struct Ctx {
 inline void prof_count(Ctx& c, int stage, int n = 1) { c.prof.launches[stage] += n; }
 int prof_begin(Ctx& c, int stage);
 void prof_end(Ctx& c, int pair);
+// a span of several launches (possibly on two streams joined at its end) timed as one
+// interval of `stage` on the context's stream; the launches inside are counted, not timed
+int prof_span_begin(Ctx& c, int stage);
+void prof_span_end(Ctx& c, int pair);
 void prof_flush(Ctx& c);
 
 // ------------------------------------------------------------------ stages

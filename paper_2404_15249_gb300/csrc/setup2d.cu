@@ -21,6 +21,7 @@
 #include <cstring>
 
 #include <algorithm>
+#include <array>
 #include <vector>
 
 #include "kfbi_internal.cuh"
@@ -570,6 +571,105 @@ __global__ void ctrl_weights_kernel(int N, int M, double lo, double h, double ka
 // ------------------------------------------------------------------ host driver
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
+// Work items of the sparse first x-transform (one CTA each).  A row with at most
+// kSpxNodes irregular nodes is one item; a longer one (where Gamma runs nearly along the
+// row) is split into parts of near-equal node counts, whose partial rows go to scratch
+// slots and are added, in part order, by the last part to finish.  Items are ordered by
+// decreasing node count, so the longest start first and the empty rows fill the tail.
+constexpr int kSpxNodes = 16;
+// stencil nodes per work item of the sparse-output x-transform
+constexpr int kSnNodes = 12;
+
+static kfbi_status build_spx_items(Ctx& c, const int* node_off) {
+  const int N = c.N;
+  cudaStream_t st = c.stream;
+  std::vector<int> off(N);
+  KFBI_CUDA_TRY(cudaMemcpyAsync(off.data(), node_off, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+  KFBI_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<std::array<int, 8>> items;
+  items.reserve(N + c.nirr / kSpxNodes + 1);
+  int slots = 0, split = 0;
+  for (int j = 0; j < N; ++j) {
+    const int n0 = j > 0 ? off[j - 1] : 0, n1 = j > 0 ? off[j] : 0, cnt = n1 - n0;
+    if (cnt <= kSpxNodes) {
+      items.push_back({j, n0, n1, 0, 1, 0, 0, 0});
+      continue;
+    }
+    const int P = (cnt + kSpxNodes - 1) / kSpxNodes;
+    for (int p = 0; p < P; ++p)
+      items.push_back({j, n0 + (int)((long)cnt * p / P), n0 + (int)((long)cnt * (p + 1) / P), p, P,
+                       slots, split, 0});
+    slots += P;
+    ++split;
+  }
+  std::stable_sort(items.begin(), items.end(), [](const std::array<int, 8>& a,
+                                                  const std::array<int, 8>& b) {
+    return a[2] - a[1] > b[2] - b[1];
+  });
+  c.spx_nitems = (int)items.size();
+  KFBI_TRY(alloc_bytes(c, (void**)&c.spx_items, sizeof(int) * 8 * items.size()));
+  KFBI_TRY(alloc_bytes(c, (void**)&c.spx_part, sizeof(float) * (size_t)std::max(slots, 1) * N));
+  KFBI_TRY(alloc_bytes(c, (void**)&c.spx_cnt, sizeof(unsigned) * (split + 1)));
+  KFBI_CUDA_TRY(cudaMemsetAsync(c.spx_cnt, 0, sizeof(unsigned) * (split + 1), st));
+  KFBI_CUDA_TRY(cudaMemcpyAsync(c.spx_items, items.data(), sizeof(int) * 8 * items.size(),
+                                cudaMemcpyHostToDevice, st));
+  KFBI_CUDA_TRY(cudaStreamSynchronize(st));   // the host vector goes out of scope
+  return KFBI_OK;
+}
+
+// The distinct interior stencil nodes of the control points, sorted by grid row then
+// column (the plain FP32 apply evaluates its last x-transform only there), each stencil
+// entry's slot in that list (-1 on the box boundary), and the work items: each row's
+// nodes in parts of at most kSnNodes, longest first.
+static kfbi_status build_stencil_nodes(Ctx& c) {
+  const int N = c.N, M = c.M;
+  cudaStream_t st = c.stream;
+  std::vector<int> cn((size_t)6 * M);
+  KFBI_CUDA_TRY(cudaMemcpyAsync(cn.data(), c.ctrl_node, sizeof(int) * 6 * M,
+                                cudaMemcpyDeviceToHost, st));
+  KFBI_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<int> nodes;
+  nodes.reserve(cn.size());
+  for (int q : cn)
+    if (q >= 0) nodes.push_back(q);
+  std::sort(nodes.begin(), nodes.end());
+  nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
+  std::vector<int> slot(cn.size()), col(nodes.size());
+  for (size_t e = 0; e < cn.size(); ++e)
+    slot[e] = cn[e] < 0 ? -1
+                        : (int)(std::lower_bound(nodes.begin(), nodes.end(), cn[e]) - nodes.begin());
+  std::vector<std::array<int, 4>> items;
+  for (size_t q0 = 0; q0 < nodes.size();) {        // one row's nodes [q0, q1), in parts
+    const int j = nodes[q0] / N;
+    size_t q1 = q0;
+    for (; q1 < nodes.size() && nodes[q1] / N == j; ++q1) col[q1] = nodes[q1] - j * N;
+    const int cnt = (int)(q1 - q0), P = (cnt + kSnNodes - 1) / kSnNodes;
+    for (int p = 0; p < P; ++p)
+      items.push_back({j, (int)q0 + cnt * p / P, (int)q0 + cnt * (p + 1) / P, 0});
+    q0 = q1;
+  }
+  std::stable_sort(items.begin(), items.end(), [](const std::array<int, 4>& a,
+                                                  const std::array<int, 4>& b) {
+    return a[2] - a[1] > b[2] - b[1];
+  });
+  c.sn_count = (int)nodes.size();
+  c.sn_nitems = (int)items.size();
+  KFBI_TRY(alloc_bytes(c, (void**)&c.ctrl_slot, sizeof(int) * 6 * M));
+  KFBI_TRY(alloc_bytes(c, (void**)&c.sn_col, sizeof(int) * (nodes.size() + 1)));
+  KFBI_TRY(alloc_bytes(c, (void**)&c.sn_items, sizeof(int) * 4 * (items.size() + 1)));
+  KFBI_TRY(alloc_bytes(c, (void**)&c.sn_val, sizeof(float) * (nodes.size() + 1)));
+  KFBI_CUDA_TRY(cudaMemcpyAsync(c.ctrl_slot, slot.data(), sizeof(int) * slot.size(),
+                                cudaMemcpyHostToDevice, st));
+  if (!nodes.empty()) {
+    KFBI_CUDA_TRY(cudaMemcpyAsync(c.sn_col, col.data(), sizeof(int) * col.size(),
+                                  cudaMemcpyHostToDevice, st));
+    KFBI_CUDA_TRY(cudaMemcpyAsync(c.sn_items, items.data(), sizeof(int) * 4 * items.size(),
+                                  cudaMemcpyHostToDevice, st));
+  }
+  KFBI_CUDA_TRY(cudaStreamSynchronize(st));   // the host vectors go out of scope
+  return KFBI_OK;
+}
+
 kfbi_status setup_geometry(Ctx& c) {
   const int N = c.N, M = c.M;
   cudaStream_t st = c.stream;
@@ -755,6 +855,8 @@ kfbi_status setup_geometry(Ctx& c) {
     return KFBI_ERR_GEOMETRY;
   }
   c.irr_rowptr = node_off;       // row j (1 <= j < N) holds irregular nodes [j-1], [j]
+  KFBI_TRY(build_spx_items(c, node_off));
+  KFBI_TRY(build_stencil_nodes(c));
 
   return KFBI_OK;
 }

@@ -73,8 +73,15 @@ BATCH_PER_SIZE = (30, 4, 16, 6, 5, 13, 2, 38, 1)   # N = 64, 96, ..., 1024
 def test_batched_configuration_matches_the_fp64_oracle():
     """kfbi_batch_solve (mixed precision, GMRES(50) to 1e-10) on a sample of the batched
     configuration against the FP64 oracle's solve of each (problem, right-hand side): the
-    density within 1e-6 relative, and u closer to the oracle's u than the oracle's u is to
-    the exact solution (below the discretisation error)."""
+    GPU density solves the oracle's own discrete BIE K_D phi = g_hat to a relative
+    residual of 2e-10 (backward error: the solve tolerance plus the two operators'
+    difference), the density is within 1e-6 relative of the oracle's, and u is closer to
+    the oracle's u than the oracle's u is to the exact solution (below the discretisation
+    error).  Problem 213's K_D has one isolated small singular value (1.3e-4, the next
+    1.1e-2), along which any residual of the solve tolerance moves the density by about
+    1e-6: its density is held instead to the perturbation bound
+    ||phi - phi_o|| <= (||r|| + ||r_o||) / sigma_min (2-norms) with the residuals r, r_o of
+    the two densities and sigma_min from the oracle's dense K_D."""
     import oracle as O
     cfg = W.config_batch(256, 4)
     picks = list(BATCH_SPECIAL) + list(BATCH_PER_SIZE)
@@ -96,6 +103,7 @@ def test_batched_configuration_matches_the_fp64_oracle():
     infos = K.batch_solve(ctxs, fg, fc, gc, ub, 4, dens_out=dens)
     assert all(i["converged"] for i in infos), [m[:2] for m, i in zip(meta, infos) if not i["converged"]]
     geoms = {}
+    sigma_min = {}
     worst = []
     for k, ((idx, r, q), info) in enumerate(zip(meta, infos)):
         if q.N > 384 and r > 0:
@@ -107,15 +115,26 @@ def test_batched_configuration_matches_the_fp64_oracle():
                                          max_restarts=40)
         assert info_o["converged"]
         phi = dens[k].cpu().numpy()
+        ghat = q.g_ctrl() - O.apply_volume(g, q.f_grid(), q.f_ctrl())
+        res = np.linalg.norm(O.apply_double_layer(g, phi) - ghat)
+        assert res <= 2e-10 * np.linalg.norm(ghat), (idx, r, res / np.linalg.norm(ghat))
         d_rel = np.max(np.abs(phi - phi_o)) / np.max(np.abs(phi_o))
         u = ub[k].cpu().numpy()
         e_gpu = np.max(np.abs(u - u_o)[g.inside])
         e_disc = np.max(np.abs(u_o - q.u_grid())[g.inside])
-        worst.append((d_rel, idx, r))
-        assert d_rel <= 1e-6, (idx, r, d_rel)
+        if idx == 213:
+            if idx not in sigma_min:
+                Kd = np.column_stack([O.apply_double_layer(g, e) for e in np.eye(q.iface.M)])
+                sigma_min[idx] = np.linalg.svd(Kd, compute_uv=False)[-1]
+            res_o = np.linalg.norm(O.apply_double_layer(g, phi_o) - ghat)
+            bound = (res + res_o) / sigma_min[idx]
+            assert np.linalg.norm(phi - phi_o) <= bound, (idx, r, np.linalg.norm(phi - phi_o), bound)
+        else:
+            worst.append((d_rel, idx, r))
+            assert d_rel <= 1e-6, (idx, r, d_rel)
         assert e_gpu < e_disc, (idx, r, e_gpu, e_disc)
     print("batched configuration vs the FP64 oracle: worst density error "
           f"{max(worst)[0]:.3e} (problem {max(worst)[1]}, rhs {max(worst)[2]}), "
-          f"{len(worst)} solves compared")
+          f"{len(worst)} solves compared besides problem 213")
     for c in ctxs:
         c.close()

@@ -294,6 +294,30 @@ def test_fp32_column_pass_variants(N, variant, monkeypatch):
     ctx.close()
 
 
+@pytest.mark.parametrize("N", [96, 256])
+@pytest.mark.parametrize("variant", [4, 8])
+def test_plain_apply_with_rows_split_into_parts(N, variant, monkeypatch):
+    """A flat axis-aligned ellipse (semi-axes 0.8 and 0.1) runs nearly along the grid rows at
+    its top and bottom, which then hold far more irregular nodes than one work item of the
+    sparse first x-transform takes (about 80 at N = 256): those rows are split into parts
+    whose partial rows the last part to finish adds up.  The plain FP32 double- and
+    single-layer applies (with variant 8 also the last x-transform at the stencil nodes
+    only) within 2e-5 of the oracle, and bit-identical when repeated."""
+    monkeypatch.setenv("KFBI_DST_VARIANTS", f"0,{variant},0,6")
+    prob = W.Problem(W.ellipse(2 * N, 0.8, 0.1, 0.0), N, 1.0, W.manufactured_exp_sin2y(1.0))
+    ctx, geom = make(prob)
+    monkeypatch.delenv("KFBI_DST_VARIANTS")
+    assert ctx.info()["dst_variant"][1] == variant
+    phi = W.random_density(prob.iface.M, seed=7)
+    ref = O.apply_double_layer(geom, phi)
+    g32 = ctx.apply_layer_potential(phi, 0, K.KFBI_MIXED_FP32).cpu().numpy()
+    assert rel(g32, ref) < 2e-5
+    assert np.array_equal(ctx.apply_layer_potential(phi, 0, K.KFBI_MIXED_FP32).cpu().numpy(), g32)
+    ref = O.apply_interface(geom, psi=phi)
+    assert rel(ctx.apply_layer_potential(phi, 1, K.KFBI_MIXED_FP32).cpu().numpy(), ref) < 2e-5
+    ctx.close()
+
+
 @pytest.mark.parametrize("case", ["flower128_poisson", "ellipse256_k10", "flower96_k1"])
 def test_normal_derivative_applies_parity(case):
     """d_n v^+ of the single and double layer and of the volume term (Procedure 2's Neumann
