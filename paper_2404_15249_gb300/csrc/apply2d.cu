@@ -152,8 +152,10 @@ __global__ void split_kernel(long n, const double* __restrict__ b, float* __rest
 // (along x, Alg. 4) and writes the transformed rows straight into the work grid:
 //   X[j][k] = sum over irregular (i, j) of b_ij sin(pi i k / N).
 // One CTA per work item: a grid row j, or a part of the nodes of a row with many (T threads
-// in W = T/32 warps).  Warp w prepares the item's nodes q = w, w + W, ...: lanes over (crossed arm, weight) pairs form b_ij from the density (up
-// to 4 x 6 FP64 products gathered at once, summed by shuffles), and the node's phase
+// in W = T/32 warps).  Warp w prepares the item's nodes q = w, w + W, ...: lanes over
+// (crossed arm, weight) pairs form b_ij from the density (up to 4 x 6 FP64 products
+// gathered at once, summed by shuffles; the FP64 value also goes to B64 at the node when
+// a refined apply needs it for its residuals), and the node's phase
 // tables go to shared memory: e^{i pi i l / N} for the lanes l < 32, e^{i pi i 32 v / N}
 // for the warps v < W, and the rotation e^{i pi i T / N}.  Then thread t = 32 v + l
 // accumulates the modes k = t + s T (s < S, k < N/4), starting from the product of its
@@ -183,7 +185,8 @@ __global__ void __launch_bounds__(SPX_THREADS_MAX)
                        const int* __restrict__ irr_node, const int* __restrict__ arm_ptr,
                        const int* __restrict__ arm_seg, const double* __restrict__ wgt,
                        const double* __restrict__ dens, const float2* __restrict__ tw,
-                       float* __restrict__ X, float* part, unsigned* counter) {
+                       float* __restrict__ X, float* part, unsigned* counter,
+                       double* __restrict__ B64) {
   constexpr int WMAX = SPX_THREADS_MAX / 32;
   __shared__ float2 s_lane[SPX_NODES][32];
   __shared__ float2 s_warp[SPX_NODES][WMAX];
@@ -226,6 +229,7 @@ __global__ void __launch_bounds__(SPX_THREADS_MAX)
         s_warp[q][lane] = make_float2(pw.x, -pw.y);
       }
       if (lane == 0) {
+        if (B64) B64[j * N + i] = v;
         const float2 rt = tw[mod_2n(i * T, N2, inv_n2)];
         s_node[q] = make_float4((float)v, rt.x, -rt.y, __int_as_float(i));
         s_q[q] = make_float2(-tw[mod_2n(i * Q, N2, inv_n2)].y, -tw[mod_2n(i * 3 * Q, N2, inv_n2)].y);
@@ -455,25 +459,28 @@ static kfbi_status sparse_out(Ctx& c, const float* Y) {
 }
 
 template <int S>
-static void launch_sparse_rows(Ctx& c, int T, const double* wgt, const double* dens, float* X) {
+static void launch_sparse_rows(Ctx& c, int T, const double* wgt, const double* dens, float* X,
+                               double* B64) {
   sparse_rows_kernel<S><<<c.spx_nitems, T, 0, c.stream>>>(
       c.N, c.M, reinterpret_cast<const int4*>(c.spx_items), c.irr_node, c.arm_ptr, c.arm_seg,
-      wgt, dens, reinterpret_cast<const float2*>(c.t32.tw), X, c.spx_part, c.spx_cnt);
+      wgt, dens, reinterpret_cast<const float2*>(c.t32.tw), X, c.spx_part, c.spx_cnt, B64);
 }
 
 // threads per item: N/4 rounded up to a warp, at most 256; S = ceil(N/4 / T) steps
-static kfbi_status sparse_rows(Ctx& c, const double* wgt, const double* dens, float* X) {
+// (B64: also the FP64 right-hand side at the irregular nodes, for refinement residuals)
+static kfbi_status sparse_rows(Ctx& c, const double* wgt, const double* dens, float* X,
+                               double* B64 = nullptr) {
   const int Q = c.N / 4;
   const int T = Q >= SPX_THREADS_MAX ? SPX_THREADS_MAX : ((Q + 31) / 32) * 32;
   const int S = (Q + T - 1) / T;
   const int pr = prof_begin(c, ST_SPARSE);
   switch (S) {
-    case 1: launch_sparse_rows<1>(c, T, wgt, dens, X); break;
-    case 2: launch_sparse_rows<2>(c, T, wgt, dens, X); break;
-    case 3: launch_sparse_rows<3>(c, T, wgt, dens, X); break;
-    case 4: launch_sparse_rows<4>(c, T, wgt, dens, X); break;
-    case 6: launch_sparse_rows<6>(c, T, wgt, dens, X); break;
-    case 8: launch_sparse_rows<8>(c, T, wgt, dens, X); break;
+    case 1: launch_sparse_rows<1>(c, T, wgt, dens, X, B64); break;
+    case 2: launch_sparse_rows<2>(c, T, wgt, dens, X, B64); break;
+    case 3: launch_sparse_rows<3>(c, T, wgt, dens, X, B64); break;
+    case 4: launch_sparse_rows<4>(c, T, wgt, dens, X, B64); break;
+    case 6: launch_sparse_rows<6>(c, T, wgt, dens, X, B64); break;
+    case 8: launch_sparse_rows<8>(c, T, wgt, dens, X, B64); break;
     default:
       prof_end(c, pr);
       set_error("sparse x-transform: N = %d not supported", c.N);
@@ -532,12 +539,16 @@ __global__ void work_to_grid_kernel(int N, const T* __restrict__ w1, const float
 }
 
 // ------------------------------------------------------------------ interpolation
-// out_k = sum_p w_p v(node_p) + sum_r (cD dens + cS psi) + eF f_k, v = v1 (+ v2 + v3)
+// out_k = sum_p w_p v(node_p) + sum_r (cD dens + cS psi) + eF f_k, v = v1 (+ v2 + v3) at the
+// work-grid node (each grid optional) plus vs at the node's slot in the compact list of
+// stencil-node values (when given)
 template <typename T>
-__global__ void interp_kernel(int M, const int* __restrict__ node, const double* __restrict__ w,
+__global__ void interp_kernel(int M, const int* __restrict__ node, const int* __restrict__ slot,
+                              const double* __restrict__ w,
                               const double* __restrict__ cD, const double* __restrict__ cS,
                               const double* __restrict__ eF, const T* __restrict__ v1,
                               const float* __restrict__ v2, const float* __restrict__ v3,
+                              const float* __restrict__ vs,
                               const double* __restrict__ dens, const double* __restrict__ psi,
                               const double* __restrict__ fctl, double* __restrict__ out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -547,9 +558,10 @@ __global__ void interp_kernel(int M, const int* __restrict__ node, const double*
   for (int p = 0; p < 6; ++p) {
     const int nd = node[6 * k + p];
     if (nd >= 0) {
-      double v = (double)v1[nd];
+      double v = v1 ? (double)v1[nd] : 0.0;
       if (v2) v += (double)v2[nd];
       if (v3) v += (double)v3[nd];
+      if (vs) v += (double)vs[slot[6 * k + p]];
       acc += w[6 * k + p] * v;
     }
   }
@@ -588,17 +600,17 @@ static kfbi_status correct(Ctx& c, const double* dens, const double* psi, const 
 }
 
 // v^+ at the control points, or with dn the normal derivative d_n v^+ (the same gather with
-// the weights of n . grad of the fitted quadratic)
-// (nodes: the index of each stencil entry into v1..v3; the work-grid indices by default, the
-// slots of the compact stencil-node values for the sparse-output transform)
+// the weights of n . grad of the fitted quadratic); v = v1 (+ v2 + v3) on the work grid plus
+// vs, the compact values at the stencil nodes left by the sparse-output transform
 template <typename T>
 static kfbi_status interp(Ctx& c, const T* v1, const float* v2, const float* v3,
                           const double* dens, const double* psi, const double* fctl,
-                          double* out, bool dn = false, const int* nodes = nullptr) {
+                          double* out, bool dn = false, const float* vs = nullptr) {
   const int pr = prof_begin(c, ST_INTERP);
   interp_kernel<T><<<(c.M + 127) / 128, 128, 0, c.stream>>>(
-      c.M, nodes ? nodes : c.ctrl_node, dn ? c.ctrl_wn : c.ctrl_w, dn ? c.ctrl_cDn : c.ctrl_cD,
-      dn ? c.ctrl_cSn : c.ctrl_cS, dn ? c.ctrl_eFn : c.ctrl_eF, v1, v2, v3, dens, psi, fctl, out);
+      c.M, c.ctrl_node, c.ctrl_slot, dn ? c.ctrl_wn : c.ctrl_w, dn ? c.ctrl_cDn : c.ctrl_cD,
+      dn ? c.ctrl_cSn : c.ctrl_cS, dn ? c.ctrl_eFn : c.ctrl_eF, v1, v2, v3, vs, dens, psi, fctl,
+      out);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
@@ -618,12 +630,13 @@ static int refine_steps_of(int precision) {
   return precision == KFBI_FP32_REFINED ? 2 : (precision == KFBI_FP32_REFINED_ONCE ? 1 : 0);
 }
 
-// Refined FP32 box solve.  b32: FP32 right-hand side of the first solve; the residuals use
+// Refinement steps of an FP32 box solve whose first solution is in V32: the residuals use
 // the dense exact pair (bhi, blo) or, when bhi is null, the sparse FP64 right-hand side in
-// B64 at the irregular nodes (zero elsewhere).  Result: v = V32 + U32 (+ T32 if steps = 2).
-static kfbi_status refined_solve(Ctx& c, const float* b32, const float* bhi, const float* blo,
-                                 int steps) {
-  KFBI_TRY(box_solve_f32(c, b32, c.V32));
+// B64 at the irregular nodes (zero elsewhere).  Result: v = V32 + U32 (+ T32 if steps = 2);
+// with stencil_last the last correction is evaluated at the control points' stencil nodes
+// only (its last x-transform by the sparse-output kernel, into sn_val) instead.
+static kfbi_status refine_steps(Ctx& c, const float* bhi, const float* blo, int steps,
+                                bool stencil_last) {
   const float inv_h2 = (float)(1.0 / (c.h * c.h));
   const float k2hi = (float)c.kappa2, k2lo = (float)(c.kappa2 - (double)k2hi);
   for (int s = 0; s < steps; ++s) {
@@ -637,9 +650,24 @@ static kfbi_status refined_solve(Ctx& c, const float* b32, const float* bhi, con
     prof_end(c, pr);
     if (!bhi && c.nirr > 0) prof_count(c, ST_REFINE);
     KFBI_CUDA_TRY(cudaGetLastError());
-    KFBI_TRY(box_solve_f32(c, c.W32, s == 0 ? c.U32 : c.T32));
+    float* corr = s == 0 ? c.U32 : c.T32;
+    if (stencil_last && s == steps - 1) {
+      KFBI_TRY(rows_pass_f32(c, c.W32, corr));
+      KFBI_TRY(ypass_rows_f32(c, corr, ypass_out(c)));
+      KFBI_TRY(sparse_out(c, ypass_out(c)));
+    } else {
+      KFBI_TRY(box_solve_f32(c, c.W32, corr));
+    }
   }
   return KFBI_OK;
+}
+
+// Refined FP32 box solve of the FP32 right-hand side b32 (first solve into V32, then the
+// refinement steps above with full-grid corrections)
+static kfbi_status refined_solve(Ctx& c, const float* b32, const float* bhi, const float* blo,
+                                 int steps) {
+  KFBI_TRY(box_solve_f32(c, b32, c.V32));
+  return refine_steps(c, bhi, blo, steps, false);
 }
 
 // ------------------------------------------------------------------ apply
@@ -668,10 +696,23 @@ kfbi_status apply_potential(Ctx& c, Layer layer, int precision, const double* de
     if (c.cols_variant[0] & 8) {
       KFBI_TRY(ypass_rows_f32(c, c.V32, ypass_out(c)));
       KFBI_TRY(sparse_out(c, ypass_out(c)));
-      return interp<float>(c, c.sn_val, nullptr, nullptr, d, s, nullptr, out, dn, c.ctrl_slot);
+      return interp<float>(c, nullptr, nullptr, nullptr, d, s, nullptr, out, dn, c.sn_val);
     }
     KFBI_TRY(box_solve_after_rows_f32(c, c.V32));
     return interp<float>(c, c.V32, nullptr, nullptr, d, s, nullptr, out, dn);
+  }
+  if (steps > 0 && precision != KFBI_TF32X3 && c.irr_rowptr) {
+    // refined: the first solve from the sparse right-hand side (correction fused with the
+    // first x-transform, which also leaves the FP64 values for the residuals in B64); with
+    // the row-layout y-pass the last correction is evaluated at the stencil nodes only
+    KFBI_TRY(sparse_rows(c, d ? c.arm_wD : c.arm_wS, d ? d : s, c.V32, c.B64));
+    KFBI_TRY(box_solve_after_rows_f32(c, c.V32));
+    const bool stencil = (c.cols_variant[0] & 8) != 0;
+    KFBI_TRY(refine_steps(c, nullptr, nullptr, steps, stencil));
+    if (stencil)
+      return interp<float>(c, c.V32, steps > 1 ? c.U32 : nullptr, nullptr, d, s, nullptr, out, dn,
+                           c.sn_val);
+    return interp<float>(c, c.V32, c.U32, steps > 1 ? c.T32 : nullptr, d, s, nullptr, out, dn);
   }
   KFBI_TRY(correct<float>(c, d, s, nullptr, c.B32, 0, steps ? c.B64 : nullptr));
   if (precision == KFBI_TF32X3) {                   // dense sine transforms on tensor cores

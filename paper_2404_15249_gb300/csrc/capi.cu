@@ -2,7 +2,10 @@
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "kfbi_internal.cuh"
@@ -18,6 +21,24 @@ void set_error(const char* fmt, ...) {
   va_start(ap, fmt);
   vsnprintf(g_err, sizeof(g_err), fmt, ap);
   va_end(ap);
+}
+
+kfbi_status set_smem_limit(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> done;   // (device, kernel) -> bytes set
+  int dev = 0;
+  KFBI_CUDA_TRY(cudaGetDevice(&dev));
+  const std::pair<int, const void*> key(dev, func);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return KFBI_OK;
+  }
+  KFBI_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& b = done[key];
+  if (b < bytes) b = bytes;
+  return KFBI_OK;
 }
 
 kfbi_status alloc_bytes(Ctx& c, void** p, size_t bytes) {

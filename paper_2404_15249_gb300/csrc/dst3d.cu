@@ -27,8 +27,7 @@ kfbi_status box_solve3_n(Ctx& c, const T* rhs, T* A, const cx<T>* tw, const T* l
     KFBI_TRY((stage_table<T, N, E>(c, tw, &stw)));
     const int threads = lpc * P.tpl;
     const size_t smem = yline_smem<T, N, E>();
-    static PerDeviceOnce attr;   // the limit is set once per device
-    KFBI_TRY(set_smem_limit_once(attr, (const void*)yline_kernel<T, N, E, 3>, smem));
+    KFBI_TRY(set_smem_limit((const void*)yline_kernel<T, N, E, 3>, smem));
     int per_sm = 0;
     KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yline_kernel<T, N, E, 3>,
                                                                 threads, smem));

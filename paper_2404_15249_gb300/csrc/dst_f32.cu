@@ -29,9 +29,14 @@ kfbi_status box_solve_after_rows_f32(Ctx& c, float* work) {
                                              c.t32.lam);
 }
 
-kfbi_status ylines_f32_lines(Ctx& c, float* X, int nlines) {
-  return dst::ylines_dispatch<float>(c, X, reinterpret_cast<const dst::cx<float>*>(c.t32.tw),
-                                     c.t32.lam, nlines);
+kfbi_status rows_pass_f32(Ctx& c, const float* in, float* out) {
+  return dst::rows_dispatch<float>(c, in, out, reinterpret_cast<const dst::cx<float>*>(c.t32.tw));
 }
+
+kfbi_status ycol_lines_f32(Ctx& c, const float* V, float* Y, int ncols) {
+  return dst::ycol_lines_dispatch<float>(c, V, Y, reinterpret_cast<const dst::cx<float>*>(c.t32.tw),
+                                         c.t32.lam, ncols);
+}
+
 
 }  // namespace kfbi

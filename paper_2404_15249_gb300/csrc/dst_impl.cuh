@@ -745,6 +745,55 @@ __global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl :
   }
 }
 
+// The low x-modes of the row-layout y-pass (2-D): column k < ncols of the row-layout grid
+// V (x-mode k along y, stride N) takes DST-I along y, the spectral division and DST-I again
+// and is written to column k of Y.  Stage 0 gathers the column straight from global memory
+// (each strided value one 32-byte sector, served by L2, where the preceding pass left the
+// grid) and the outputs are scattered back, so no transposed copy of the low modes is
+// made.  Shared memory holds the raw line and the FFT buffers of each of the lpc lines.
+template <typename T, int N, int EPT>
+__global__ void __launch_bounds__((cplan(N, EPT).tpl > 256 ? cplan(N, EPT).tpl : 256),
+                                  ((cplan(N, EPT).tpl > 256 && EPT >= 16) ? 1 : 2))
+    ycol_lines_kernel(const T* __restrict__ V, T* __restrict__ Y, const cx<T>* __restrict__ stw,
+                      const cx<T>* __restrict__ tw, const T* __restrict__ lam, T kappa2,
+                      T scale, int ncols) {
+  constexpr CPlan P = cplan(N, EPT);
+  constexpr size_t LB = col_line_bytes<T, N>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lpc = blockDim.x / P.tpl;
+  const int line = threadIdx.x / P.tpl, t = threadIdx.x - line * P.tpl;
+  unsigned char* lb = smem_raw + line * LB;
+  T* raw = reinterpret_cast<T*>(lb);
+  cx<T>* z0 = reinterpret_cast<cx<T>*>(lb + ((size_t)(N + 2) * sizeof(T) + 15) / 16 * 16);
+  cx<T>* z1 = z0 + (line_buffers<T, N>() - 1) * line_len(N);
+  for (int kk = blockIdx.x * lpc; kk < ncols; kk += gridDim.x * lpc) {
+    const int k = kk + line;
+    const bool active = k < ncols;
+    const T* col = V + (active ? k : 0);
+    const T lk = active ? lam[k] - kappa2 : T(0);
+    const bool zero_line = !active || k == 0;
+    auto at = [&](int j) -> T { return col[(size_t)j * N]; };       // 0 <= j < N
+    // forward transform of the packed odd extension of the column, spectral division
+    dst_line<T, N, EPT>(
+        [&](int m, bool upper) -> cx<T> {
+          if (!active) return cx<T>{T(0), T(0)};
+          if (!upper) return cx<T>{at(2 * m), at(2 * m + 1)};
+          const int mp = N - m;                                     // 0 < mp <= N/2
+          const T hi = (mp < N / 2) ? at(2 * mp) : T(0);
+          return cx<T>{-hi, -at(2 * mp - 1)};
+        },
+        z0, z1, t, stw, tw, [&](int, int l, T x) {
+          raw[l] = (zero_line || l == 0) ? T(0) : x * scale * recip(lk + lam[l]);
+        });
+    __syncthreads();
+    dst_line<T, N, EPT>([&](int m, bool upper) { return packed<T, N>(raw, m, upper); }, z0, z1,
+                        t, stw, tw, [&](int, int j, T x) {
+                          if (active) Y[(size_t)j * N + k] = x;
+                        });
+    __syncthreads();
+  }
+}
+
 // dynamic shared memory of the two kernels
 template <typename T, int N, int EPT>
 __host__ __device__ constexpr size_t rows_smem(int lpc) {
@@ -810,8 +859,7 @@ kfbi_status launch_rows(Ctx& c, const T* in, T* out, const cx<T>* tw, T scale, i
   static_assert(rows_smem<T, N, EPT>(lpc) <= 227 * 1024, "row pass exceeds shared memory");
   const int threads = lpc * P.tpl;
   const size_t smem = rows_smem<T, N, EPT>(lpc);
-  static PerDeviceOnce attr;   // the limit is set once per device
-  KFBI_TRY(set_smem_limit_once(attr, (const void*)rows_kernel<T, N, EPT>, smem));
+  KFBI_TRY(set_smem_limit((const void*)rows_kernel<T, N, EPT>, smem));
   int per_sm = 0;
   KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_kernel<T, N, EPT>,
                                                               threads, smem));
@@ -835,8 +883,7 @@ kfbi_status launch_cols(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   static_assert(cols_smem<T, N, EPT, MAXT>() <= 227 * 1024, "column pass exceeds shared memory");
   const int threads = L * P.tpl;
   const size_t smem = cols_smem<T, N, EPT, MAXT>();
-  static PerDeviceOnce attr;   // the limit is set once per device
-  KFBI_TRY(set_smem_limit_once(attr, (const void*)cols_kernel<T, N, EPT, MAXT>, smem));
+  KFBI_TRY(set_smem_limit((const void*)cols_kernel<T, N, EPT, MAXT>, smem));
   int per_sm = 0;
   KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &per_sm, cols_kernel<T, N, EPT, MAXT>, threads, smem));
@@ -862,8 +909,7 @@ kfbi_status launch_ylines(Ctx& c, T* V, const cx<T>* tw, const T* lam) {
   T* X = reinterpret_cast<T*>(c.XT);
   const int threads = lpc * P.tpl;
   const size_t smem = yline_smem<T, N, EPT>();
-  static PerDeviceOnce attr;   // the limit is set once per device
-  KFBI_TRY(set_smem_limit_once(attr, (const void*)yline_kernel<T, N, EPT, 2>, smem));
+  KFBI_TRY(set_smem_limit((const void*)yline_kernel<T, N, EPT, 2>, smem));
   int per_sm = 0;
   KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yline_kernel<T, N, EPT, 2>,
                                                               threads, smem));
@@ -898,8 +944,7 @@ kfbi_status launch_ylines_only(Ctx& c, T* X, const cx<T>* tw, const T* lam, int 
   KFBI_TRY((stage_table<T, N, EPT>(c, tw, &stw)));
   const int threads = lpc * P.tpl;
   const size_t smem = yline_smem<T, N, EPT>();
-  static PerDeviceOnce attr;   // the limit is set once per device
-  KFBI_TRY(set_smem_limit_once(attr, (const void*)yline_kernel<T, N, EPT, 2>, smem));
+  KFBI_TRY(set_smem_limit((const void*)yline_kernel<T, N, EPT, 2>, smem));
   int per_sm = 0;
   KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yline_kernel<T, N, EPT, 2>,
                                                               threads, smem));
@@ -920,6 +965,48 @@ kfbi_status launch_ylines_only(Ctx& c, T* X, const cx<T>* tw, const T* lam, int 
   if constexpr (std::is_same<T, float>::value)
     if (split && nfft < N) KFBI_TRY(ytri_f32(c, X, nfft));
   return KFBI_OK;
+}
+
+template <typename T, int N, int EPT>
+kfbi_status launch_ycol_lines(Ctx& c, const T* V, T* Y, const cx<T>* tw, const T* lam, int ncols) {
+  constexpr CPlan P = cplan(N, EPT);
+  constexpr int lpc = yline_lpc<T, N, EPT>();
+  static_assert((size_t)lpc * col_line_bytes<T, N>() <= 227 * 1024,
+                "low-mode column pass exceeds shared memory");
+  const cx<T>* stw = nullptr;
+  KFBI_TRY((stage_table<T, N, EPT>(c, tw, &stw)));
+  const int threads = lpc * P.tpl;
+  const size_t smem = (size_t)lpc * col_line_bytes<T, N>();
+  KFBI_TRY(set_smem_limit((const void*)ycol_lines_kernel<T, N, EPT>, smem));
+  int per_sm = 0;
+  KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ycol_lines_kernel<T, N, EPT>,
+                                                              threads, smem));
+  if (per_sm < 1) per_sm = 1;
+  int blocks = (ncols + lpc - 1) / lpc;
+  blocks = blocks < per_sm * sm_count() ? blocks : per_sm * sm_count();
+  const T scale = T((2.0 / N) * (2.0 / N));
+  const int pr = prof_begin(c, sizeof(T) == 4 ? ST_COLS32 : ST_COLS64);
+  ycol_lines_kernel<T, N, EPT><<<blocks, threads, smem, c.stream>>>(V, Y, stw, tw, lam,
+                                                                    T(c.kappa2), scale, ncols);
+  prof_end(c, pr);
+  KFBI_CUDA_TRY(cudaGetLastError());
+  return KFBI_OK;
+}
+
+// the transform pair along y of columns [0, ncols) of the row-layout grid V into Y
+template <typename T>
+kfbi_status ycol_lines_dispatch(Ctx& c, const T* V, T* Y, const cx<T>* tw, const T* lam, int ncols) {
+  switch (c.N) {
+#define KFBI_CASE(n) \
+  case n: return launch_ycol_lines<T, n, default_ept(n)>(c, V, Y, tw, lam, ncols);
+    KFBI_CASE(32) KFBI_CASE(48) KFBI_CASE(64) KFBI_CASE(96) KFBI_CASE(128) KFBI_CASE(192)
+    KFBI_CASE(256) KFBI_CASE(384) KFBI_CASE(512) KFBI_CASE(768) KFBI_CASE(1024)
+    KFBI_CASE(1536) KFBI_CASE(2048) KFBI_CASE(3072) KFBI_CASE(4096) KFBI_CASE(6144)
+    KFBI_CASE(8192)
+#undef KFBI_CASE
+  }
+  set_error("y-transform pass: no compiled plan for N = %d", c.N);
+  return KFBI_ERR_UNSUPPORTED;
 }
 
 template <typename T>
@@ -1054,6 +1141,23 @@ kfbi_status box_after_rows_dispatch(Ctx& c, T* work, const cx<T>* tw, const T* l
 #undef KFBI_CASE
   }
   set_error("box solve: no compiled plan for N = %d", c.N);
+  return KFBI_ERR_UNSUPPORTED;
+}
+
+// the x-transform of every row of the work grid alone (the first pass of a box solve)
+template <typename T>
+kfbi_status rows_dispatch(Ctx& c, const T* in, T* out, const cx<T>* tw) {
+  const int rv = c.rows_variant[sizeof(T) == 8];
+  switch (c.N) {
+#define KFBI_CASE(n) \
+  case n: return launch_rows_v<T, n>(c, in, out, tw, T(1), rv);
+    KFBI_CASE(32) KFBI_CASE(48) KFBI_CASE(64) KFBI_CASE(96) KFBI_CASE(128) KFBI_CASE(192)
+    KFBI_CASE(256) KFBI_CASE(384) KFBI_CASE(512) KFBI_CASE(768) KFBI_CASE(1024)
+    KFBI_CASE(1536) KFBI_CASE(2048) KFBI_CASE(3072) KFBI_CASE(4096) KFBI_CASE(6144)
+    KFBI_CASE(8192)
+#undef KFBI_CASE
+  }
+  set_error("row pass: no compiled plan for N = %d", c.N);
   return KFBI_ERR_UNSUPPORTED;
 }
 

@@ -400,9 +400,8 @@ template <int BN>
 kfbi_status gemm_n(Ctx& c, const float* ahi, const float* alo, float* out, float* out_lo,
                    int mode) {
   static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
-  static PerDeviceOnce attr_tma, attr_cp;   // the limits are set once per device
-  KFBI_TRY(set_smem_limit_once(attr_tma, (const void*)dst_gemm_kernel<BN, true>, Tile<BN>::SMEM));
-  KFBI_TRY(set_smem_limit_once(attr_cp, (const void*)dst_gemm_kernel<BN, false>, Tile<BN>::SMEM));
+  KFBI_TRY(set_smem_limit((const void*)dst_gemm_kernel<BN, true>, Tile<BN>::SMEM));
+  KFBI_TRY(set_smem_limit((const void*)dst_gemm_kernel<BN, false>, Tile<BN>::SMEM));
   const int N = c.N, M = c.dim == 3 ? N * N : N;
   const double s1 = 2.0 / N;
   const float scale = (float)(c.dim == 3 ? s1 * s1 * s1 : s1 * s1);

@@ -142,8 +142,7 @@ kfbi_status launch_tri(Ctx& c, float* X, int k0) {
   constexpr int LPB = TRI_THREADS / CH;
   constexpr size_t smem = (size_t)LPB * (N + CH + 2 * TRI_EXACT) * sizeof(float);
   static_assert(smem <= 227 * 1024, "tridiagonal pass exceeds shared memory");
-  static PerDeviceOnce attr;   // the limit is set once per device
-  KFBI_TRY(set_smem_limit_once(attr, (const void*)ytri_kernel<N, CH>, smem));
+  KFBI_TRY(set_smem_limit((const void*)ytri_kernel<N, CH>, smem));
   int per_sm = 0;
   KFBI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ytri_kernel<N, CH>,
                                                               TRI_THREADS, smem));

@@ -17,9 +17,9 @@
 // continues F+ over the w rows before the chunk while summing the causal state
 // u_{s-1} = sum_m c^m z_{s-1-m}, then runs F- forward over the chunk.  The warm-ups read
 // rows of the neighbouring chunks, which other warps own, so the pass is out of place: it
-// reads V and writes the result grid Y.  Low modes (k < k0) are copied out by a narrow
-// transpose, take the sine-transform pair along y (yline_kernel) on a side stream while
-// the filters run, and are copied into Y.
+// reads V and writes the result grid Y.  Low modes (k < k0) take the sine-transform pair
+// along y on a side stream while the filters run, gathering their columns of V and
+// scattering them into Y directly (ycol_lines_kernel).
 #include <cmath>
 #include <cstdint>
 
@@ -123,23 +123,6 @@ __global__ void __launch_bounds__(YC_THREADS)
   for (int i = 0; i < MC; ++i) out[(size_t)(s + i) * N] = (s + i == 0) ? 0.f : r[i];
 }
 
-// out[c][r] = in[r][c] for r < R, c < C; in has row stride ld_in, out row stride ld_out
-// (32 x 32 tiles through shared memory)
-__global__ void transpose_block_kernel(const float* __restrict__ in, int ld_in,
-                                       float* __restrict__ out, int ld_out, int R, int C) {
-  __shared__ float tile[32][33];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;            // column, row of the input tile
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int y = by + r, x = bx + threadIdx.x;
-    if (x < C && y < R) tile[r][threadIdx.x] = in[(size_t)y * ld_in + x];
-  }
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int y = bx + r, x = by + threadIdx.x;                    // row y of out = column y of in
-    if (x < R && y < C) out[(size_t)y * ld_out + x] = tile[threadIdx.x][r];
-  }
-}
-
 template <int MC>
 kfbi_status launch_filter(Ctx& c, const float* V, float* Y, int k0) {
   const int N = c.N;
@@ -152,27 +135,16 @@ kfbi_status launch_filter(Ctx& c, const float* V, float* Y, int k0) {
   return KFBI_OK;
 }
 
-kfbi_status transpose_block(Ctx& c, const float* in, int ld_in, float* out, int ld_out, int R,
-                            int C) {
-  const int pr = prof_begin(c, ST_TRANS);
-  transpose_block_kernel<<<dim3((C + 31) / 32, (R + 31) / 32), dim3(32, 8), 0, c.stream>>>(
-      in, ld_in, out, ld_out, R, C);
-  prof_end(c, pr);
-  KFBI_CUDA_TRY(cudaGetLastError());
-  return KFBI_OK;
-}
-
 }  // namespace
 
 // the y-pass of the FP32 2-D box solve from V into Y (row layout, Y != V); the low modes
-// k < tri_k0 run the transform pair in the context's transposed scratch on the side stream
+// k < tri_k0 take the transform pair on the side stream
 kfbi_status ypass_rows_f32(Ctx& c, const float* V, float* Y) {
   const int N = c.N, k0 = c.tri_k0;
   if (k0 <= 0 || k0 >= N || k0 % 32 != 0 || N % 32 != 0) {
     set_error("row-layout y-pass: needs 0 < k0 < N, both multiples of 32 (N = %d, k0 = %d)", N, k0);
     return KFBI_ERR_UNSUPPORTED;
   }
-  float* L = reinterpret_cast<float*>(c.XT);                       // k0 x N low-mode lines
   // the stage timers take the y-pass as one span on the main stream (its kernels overlap)
   struct Span {
     Ctx& c;
@@ -184,9 +156,7 @@ kfbi_status ypass_rows_f32(Ctx& c, const float* V, float* Y) {
   KFBI_CUDA_TRY(cudaEventRecord(c.fork_ev, main_st));
   KFBI_CUDA_TRY(cudaStreamWaitEvent(c.side, c.fork_ev, 0));
   c.stream = c.side;                                               // launches go to the side stream
-  kfbi_status st = transpose_block(c, V, N, L, N, N, k0);          // L[k][j] = V[j][k]
-  if (st == KFBI_OK) st = ylines_f32_lines(c, L, k0);
-  if (st == KFBI_OK) st = transpose_block(c, L, N, Y, N, k0, N);   // Y[j][k] = L[k][j]
+  const kfbi_status st = ycol_lines_f32(c, V, Y, k0);
   c.stream = main_st;
   KFBI_TRY(st);
   KFBI_CUDA_TRY(cudaEventRecord(c.join_ev, c.side));

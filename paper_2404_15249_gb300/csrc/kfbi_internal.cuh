@@ -31,26 +31,11 @@ const char* last_error_message();          // this thread's last set_error text
   } while (0)
 
 // A kernel's dynamic shared-memory limit is an attribute of the kernel in one device's
-// context: it is set once per device ordinal (from whichever host thread launches first;
-// two threads racing both set the same value, which is harmless).
-constexpr int kMaxDeviceOrdinals = 64;
-struct PerDeviceOnce {
-  std::atomic<bool> done[kMaxDeviceOrdinals] = {};
-};
-inline kfbi_status set_smem_limit_once(PerDeviceOnce& once, const void* func, size_t bytes) {
-  int dev = 0;
-  KFBI_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDeviceOrdinals) {
-    set_error("device ordinal %d above %d", dev, kMaxDeviceOrdinals - 1);
-    return KFBI_ERR_ARG;
-  }
-  if (!once.done[dev].load(std::memory_order_acquire)) {
-    KFBI_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    once.done[dev].store(true, std::memory_order_release);
-  }
-  return KFBI_OK;
-}
-
+// context.  It is recorded per (device, kernel address): a kernel template instantiated in
+// several translation units (each compiled as its own module) is a distinct kernel in each,
+// with its own attribute, so the record must not be keyed on the launching host template
+// alone.  Two threads racing both set the same value, which is harmless.
+kfbi_status set_smem_limit(const void* func, size_t bytes);
 // ------------------------------------------------------------------ FFT plan
 // Complex FFT of length N = 2^a or 3*2^a in shared memory.  Every thread of a line
 // holds EPT values per stage; each stage radix divides EPT (16 for 2^a, 24 for 3*2^a).
@@ -260,19 +245,22 @@ kfbi_status alloc_bytes(Ctx& c, void** p, size_t bytes);
 // box solve (dst.cu): three passes in place on the N x N work grid `work`, reading the
 // right-hand side from `rhs` (may equal work).
 kfbi_status box_solve_f32(Ctx& c, const float* rhs, float* work);
+// the first pass of the FP32 box solve alone: the x-transform of every row of in into out
+kfbi_status rows_pass_f32(Ctx& c, const float* in, float* out);
 kfbi_status box_solve_f64(Ctx& c, const double* rhs, double* work);
 // the y-transform pair with the spectral division on the transposed FP32 grid X in place,
 // and the last half of the box solve: transpose X back into V and transform its rows
 kfbi_status ylines_f32(Ctx& c, float* X);
 kfbi_status x_pass_f32(Ctx& c, const float* X, float* V);
-// the y-transform pair on lines [0, nlines) of the transposed FP32 grid X only
-kfbi_status ylines_f32_lines(Ctx& c, float* X, int nlines);
 // FP32 2-D: the box solve after its first row pass (column pass variant + last row pass)
 kfbi_status box_solve_after_rows_f32(Ctx& c, float* work);
 // FP32 2-D y-pass on the row layout from V into Y (Y != V): recursive filters for the
 // modes k >= tri_k0, the transform pair (side stream) for the others (dst_ycol.cu); its
 // result grid is ypass_out(c), the second half of the transposed scratch XT
 kfbi_status ypass_rows_f32(Ctx& c, const float* V, float* Y);
+// the transform pair along y (with the spectral division) of columns [0, ncols) of the
+// row-layout FP32 grid V, written to the same columns of Y
+kfbi_status ycol_lines_f32(Ctx& c, const float* V, float* Y, int ncols);
 inline float* ypass_out(Ctx& c) { return reinterpret_cast<float*>(c.XT) + (size_t)c.N * c.N; }
 kfbi_status init_box_tables(Ctx& c);
 kfbi_status autotune_f32(Ctx& c);   // column-pass variant per precision, on scratch grids
