@@ -126,16 +126,21 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-KERNEL_SOURCE = {"rows_kernel": "dst_impl.cuh", "yline_kernel": "dst_impl.cuh",
-                 "cols_kernel": "dst_impl.cuh", "transpose_vec_kernel": "dst_impl.cuh",
-                 "ytri_kernel": "dst_tri.cu", "sparse_rows_t_kernel": "apply2d.cu"}
+# the CUDA sources that define each kernel (the y-pass span: the filter kernel in
+# dst_ycol.cu and the low-mode column kernel in dst_impl.cuh)
+YPASS = "ycol_filter_kernel+ycol_lines_kernel"
+KERNEL_SOURCE = {"rows_kernel": ("dst_impl.cuh",), "yline_kernel": ("dst_impl.cuh",),
+                 "cols_kernel": ("dst_impl.cuh",), "transpose_vec_kernel": ("dst_impl.cuh",),
+                 "ytri_kernel": ("dst_tri.cu",), "sparse_rows_kernel": ("apply2d.cu",),
+                 "sparse_out_kernel": ("apply2d.cu",), "ds_residual_kernel": ("apply2d.cu",),
+                 YPASS: ("dst_ycol.cu", "dst_impl.cuh")}
 
 
 def kernel_source_hash(kernel):
-    """First 12 hex digits of the SHA-256 of the CUDA source that defines `kernel`."""
+    """First 12 hex digits of the SHA-256 of the CUDA sources that define `kernel`."""
     h = hashlib.sha256()
-    src = KERNEL_SOURCE.get(kernel.split("<")[0], "dst_impl.cuh")
-    h.update(open(os.path.join(ROOT, "paper_2404_15249_gb300", "csrc", src), "rb").read())
+    for src in KERNEL_SOURCE.get(kernel.split("<")[0], ("dst_impl.cuh",)):
+        h.update(open(os.path.join(ROOT, "paper_2404_15249_gb300", "csrc", src), "rb").read())
     return h.hexdigest()[:12]
 
 
@@ -171,6 +176,12 @@ def roofline(stage_ms, N, variants, tri_k0):
         kernels["dst_cols_f32"] = ("yline_kernel<float>", 4)
         lines["dst_cols_f32"] = tri_k0
     lines["dst_tri_f32"] = N - tri_k0
+    if variants[1] & 8:
+        # the row-layout y-pass, timed as one span over its two streams: the filters of the
+        # modes from tri_k0 up and the transform pair of the modes below, every unknown of
+        # the grid read and written once
+        kernels["dst_tri_f32"] = (YPASS, 4)
+        lines["dst_tri_f32"] = N
     if variants[3] & 4:
         kernels["dst_cols_f64"] = ("yline_kernel<double>", 8)
     cand = {k: v for k, v in stage_ms.items() if k in kernels and v[1] > 0 and v[0] > 0}

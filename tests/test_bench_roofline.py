@@ -34,6 +34,17 @@ def test_split_y_pass_bytes():
     assert r["algorithmic_bytes"] == 2 * N * (N - 252) * 4
 
 
+def test_row_layout_y_pass_is_one_span_over_the_whole_grid():
+    # variant 8: the y-pass (filters on one stream, low-mode transform pair on another) is
+    # timed as one span per launch of the filter kernel, covering every unknown
+    stages = {"dst_rows_f32": (3.5, 170), "dst_tri_f32": (3.8, 70), "sparse_x_f32": (1.7, 51)}
+    r = bench.roofline(stages, N, [0, 8, 1, 6], 256)
+    assert r["kernel"] == bench.YPASS
+    assert r["algorithmic_bytes"] == 2 * N * N * 4
+    assert r["achieved"] == pytest.approx(2 * N * N * 4 / (3.8 / 70 / 1e3) / 1e9)
+    assert len(bench.kernel_source_hash(bench.YPASS)) == 12
+
+
 def test_traffic_only_for_the_current_source():
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     lines = [l.split() for l in open(p) if l.strip() and not l.startswith("#")]
