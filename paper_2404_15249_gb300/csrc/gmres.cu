@@ -44,7 +44,8 @@ constexpr int DOT_T = 256;
 static inline int dot_blocks(int M) { return (M + DOT_CHUNK - 1) / DOT_CHUNK; }
 
 // With jp (the Arnoldi step index in device memory, so that one captured launch serves
-// every step) nb = *jp + 1 and the grid covers the largest nb: blocks b >= nb only count.
+// every step) nb = *jp + 1 and the grid covers the largest nb: blocks b >= nb return at once
+// and the last of the gridDim.x * nb active blocks to finish adds the partial sums.
 __global__ void __launch_bounds__(DOT_T) multidot_kernel(const double* __restrict__ V, int ld,
                                                          int M, int nb, const int* jp,
                                                          const double* __restrict__ w,
@@ -55,23 +56,23 @@ __global__ void __launch_bounds__(DOT_T) multidot_kernel(const double* __restric
   __shared__ bool last;
   if (jp) nb = *jp + 1;
   const int b = blockIdx.y, x0 = blockIdx.x * DOT_CHUNK;
-  if (b < nb) {
-    const double* v = V + (size_t)b * ld;
-    double a[DOT_CHUNK / DOT_T];
+  if (b >= nb) return;                       // uniform per block; only active blocks count
+  const double* v = V + (size_t)b * ld;
+  double a[DOT_CHUNK / DOT_T];
 #pragma unroll
-    for (int q = 0; q < DOT_CHUNK / DOT_T; ++q) {
-      const int x = x0 + threadIdx.x + q * DOT_T;
-      a[q] = x < M ? v[x] * w[x] : 0.0;
-    }
-    double t = 0.0;
-#pragma unroll
-    for (int q = 0; q < DOT_CHUNK / DOT_T; ++q) t += a[q];
-    t = block_sum(t, sh);
-    if (threadIdx.x == 0) part[(size_t)blockIdx.x * pld + b] = t;
+  for (int q = 0; q < DOT_CHUNK / DOT_T; ++q) {
+    const int x = x0 + threadIdx.x + q * DOT_T;
+    a[q] = x < M ? v[x] * w[x] : 0.0;
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1;
+  double t = 0.0;
+#pragma unroll
+  for (int q = 0; q < DOT_CHUNK / DOT_T; ++q) t += a[q];
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) {                    // the writer fences, then counts the block
+    part[(size_t)blockIdx.x * pld + b] = t;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x * (unsigned)nb - 1;
+  }
   __syncthreads();
   if (!last) return;
   __threadfence();
@@ -83,44 +84,66 @@ __global__ void __launch_bounds__(DOT_T) multidot_kernel(const double* __restric
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// w += sign * sum_{b < cnt} h[b] V_b  (coefficients staged in shared memory, eight
-// independent loads in flight per thread).  With nrm_out: also ||w||_2 of the updated w,
-// from per-block partial sums added in block order by the last block to finish.
+// w += sign * sum_{b < cnt} h[b] V_b.  A CTA takes 32 consecutive x (one per lane) and
+// MVU_SLICES warps: warp s accumulates the b = s, s + MVU_SLICES, ... (four independent
+// partial sums, every load independent of the others), and the slices' partial sums are
+// added in slice order through shared memory, so a thread waits for about cnt / MVU_SLICES
+// loads instead of cnt and the grid has M / 32 CTAs.  With nrm_out: also ||w||_2 of the
+// updated w, from per-CTA partial sums added in a fixed order by the last CTA to finish.
 // (cnt = *jp + 1 when jp is given: the Arnoldi step index in device memory)
-__global__ void mv_update_kernel(double* __restrict__ w, const double* __restrict__ V, int ld,
-                                 int M, const double* __restrict__ h, int cnt, const int* jp,
-                                 double sign, double* part, unsigned* counter, double* nrm_out) {
-  extern __shared__ double hs[];
-  __shared__ double sh[32];
-  __shared__ bool last;
+constexpr int MVU_X = 32;
+constexpr int MVU_SLICES = 8;
+
+static inline int mvu_blocks(int M) { return (M + MVU_X - 1) / MVU_X; }
+
+__global__ void __launch_bounds__(MVU_X * MVU_SLICES)
+    mv_update_kernel(double* __restrict__ w, const double* __restrict__ V, int ld, int M,
+                     const double* __restrict__ h, int cnt, const int* jp, double sign,
+                     double* part, unsigned* counter, double* nrm_out) {
+  __shared__ double sp[MVU_SLICES][MVU_X];
   if (jp) cnt = *jp + 1;
-  for (int b = threadIdx.x; b < cnt; b += blockDim.x) hs[b] = h[b];
+  const int lane = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int x = blockIdx.x * MVU_X + lane;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  if (x < M) {
+    constexpr int S = MVU_SLICES;
+    int b = sl;
+    for (; b + 3 * S < cnt; b += 4 * S) {
+      a0 += __ldg(h + b) * V[(size_t)b * ld + x];
+      a1 += __ldg(h + b + S) * V[(size_t)(b + S) * ld + x];
+      a2 += __ldg(h + b + 2 * S) * V[(size_t)(b + 2 * S) * ld + x];
+      a3 += __ldg(h + b + 3 * S) * V[(size_t)(b + 3 * S) * ld + x];
+    }
+    for (; b < cnt; b += S) a0 += __ldg(h + b) * V[(size_t)b * ld + x];
+  }
+  sp[sl][lane] = (a0 + a1) + (a2 + a3);
   __syncthreads();
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl != 0) return;
   double wn = 0.0;
   if (x < M) {
-    double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    int b = 0;
-    for (; b + 7 < cnt; b += 8) {
+    double t = sp[0][lane];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) s[u] += hs[b + u] * V[(size_t)(b + u) * ld + x];
-    }
-    for (; b < cnt; ++b) s[0] += hs[b] * V[(size_t)b * ld + x];
-    wn = w[x] + sign * (((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])));
+    for (int q = 1; q < MVU_SLICES; ++q) t += sp[q][lane];
+    wn = w[x] + sign * t;
     w[x] = wn;
   }
   if (!nrm_out) return;                      // uniform over the grid
-  double t = block_sum(wn * wn, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  double s2 = wn * wn;
+  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_down_sync(0xffffffffu, s2, o);
+  unsigned last = 0;
+  if (lane == 0) {
+    part[blockIdx.x] = s2;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  if (!__shfl_sync(0xffffffffu, last, 0)) return;
+  // last CTA: lane l adds the partials l, l + 32, ... in order, then a fixed shuffle tree
+  // (short FP64 dependency chains; the same order on every run)
   __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  if (threadIdx.x == 0) {
-    double u = 0.0;
-    for (int q = 0; q < (int)gridDim.x; ++q) u += __ldcg(part + q);
+  double u = 0.0;
+  for (int q = lane; q < (int)gridDim.x; q += 32) u += __ldcg(part + q);
+  for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(0xffffffffu, u, o);
+  if (lane == 0) {
     *nrm_out = sqrt(u);
     *counter = 0u;
   }
@@ -166,9 +189,6 @@ __global__ void cycle_start_kernel(double* V0, double* vin, const double* r, int
   if (x == 0) *jp = 0;
 }
 
-// next Arnoldi step
-__global__ void advance_kernel(int* jp) { *jp += 1; }
-
 // Finish Arnoldi step j (nrm = ||w||, formed by the second update): V_{j+1} = w / nrm
 // by every block; block 0 also forms column j of the Hessenberg matrix (h1 + h2 from the
 // two CGS passes, subdiagonal nrm), applies the earlier Givens rotations and the new one,
@@ -178,12 +198,24 @@ __global__ void advance_kernel(int* jp) { *jp += 1; }
 // The step index j is read from device memory (jp); the flags scal[0..3] of the step are
 // also written into host-mapped memory flags[4 (j mod 2) + 0..3] for the host to read one
 // step behind, and V_{j+1} into vin, the input of the next apply.
-__global__ void finish_kernel(const int* jp, int m, int M, const double* __restrict__ w, double* V,
+__global__ void finish_kernel(int* jp, int m, int M, const double* __restrict__ w, double* V,
                               int ld, const double* __restrict__ h1, const double* __restrict__ h2,
                               const double* __restrict__ nrm_in, double* hess, double* giv,
-                              double* gvec, double* scal, double* vin, double* flags) {
+                              double* gvec, double* scal, double* vin, double* flags,
+                              unsigned* counter) {
   extern __shared__ double dyn[];
   const int j = *jp;
+  // the last CTA to arrive advances the step index (every CTA has read it by then)
+  auto advance = [&] {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(counter, 1u) == gridDim.x - 1) {
+        *jp = j + 1;
+        *counter = 0u;
+      }
+    }
+  };
   const double nrm = *nrm_in;
   const double beta = scal[2];
   const bool breakdown = !(nrm > 1e-14 * beta);
@@ -193,20 +225,26 @@ __global__ void finish_kernel(const int* jp, int m, int M, const double* __restr
     V[(size_t)(j + 1) * ld + x] = v;
     vin[x] = v;
   }
-  if (blockIdx.x != 0) return;
+  if (blockIdx.x != 0) {
+    advance();
+    return;
+  }
   double* col = dyn;                 // m + 1
   double* gs = dyn + (m + 1);        // 2m
   for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = h1[i] + h2[i];
   for (int i = threadIdx.x; i < 2 * j; i += blockDim.x) gs[i] = giv[i];
   __syncthreads();
   if (threadIdx.x == 0) {
-    col[j + 1] = nrm;
+    // the earlier rotations, in order; the entry that each rotation passes on to the next
+    // stays in a register (two dependent FP64 operations per rotation)
+    double carry = col[0];
     for (int i = 0; i < j; ++i) {
-      const double cs = gs[2 * i], sn = gs[2 * i + 1];
-      const double t = cs * col[i] + sn * col[i + 1];
-      col[i + 1] = -sn * col[i] + cs * col[i + 1];
-      col[i] = t;
+      const double cs = gs[2 * i], sn = gs[2 * i + 1], b = col[i + 1];
+      col[i] = cs * carry + sn * b;
+      carry = -sn * carry + cs * b;
     }
+    col[j] = carry;
+    col[j + 1] = nrm;
     const double den = hypot(col[j], col[j + 1]);
     const double cs = col[j] / den, sn = col[j + 1] / den;
     giv[2 * j] = cs;
@@ -219,16 +257,18 @@ __global__ void finish_kernel(const int* jp, int m, int M, const double* __restr
     scal[0] = fabs(sn * gj);
     scal[1] = breakdown ? 1.0 : 0.0;
     scal[3] = (isfinite(nrm) && isfinite(den)) ? 0.0 : 1.0;
+    // host-mapped slot: the host reads it after an event recorded behind this kernel,
+    // whose completion makes the writes visible (no fence needed here)
     double* f = flags + 4 * (j & 1);
     f[0] = scal[0];
     f[1] = scal[1];
     f[2] = scal[2];
     f[3] = scal[3];
-    __threadfence_system();
   }
   __syncthreads();
   double* hc = hess + (size_t)j * (m + 1);
   for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hc[i] = col[i];
+  advance();
 }
 
 // back substitution R y = g (k x k, R upper triangular in hess), R and g staged in
@@ -296,7 +336,7 @@ kfbi_status alloc_gmres(Ctx& c, int m) {
   KFBI_CUDA_TRY(cudaMalloc((void**)&c.gvec, sizeof(double) * (m + 1)));
   KFBI_CUDA_TRY(cudaMalloc((void**)&c.hcol, sizeof(double) * 2 * (m + 1)));
   KFBI_CUDA_TRY(cudaMalloc((void**)&c.yvec, sizeof(double) * m));
-  const size_t nparts = std::max((size_t)dot_blocks(M) * (m + 1), (size_t)vb(M));
+  const size_t nparts = std::max((size_t)dot_blocks(M) * (m + 1), (size_t)mvu_blocks(M));
   KFBI_CUDA_TRY(cudaMalloc((void**)&c.gm_part, sizeof(double) * nparts));
   KFBI_CUDA_TRY(cudaMalloc((void**)&c.gm_counter, sizeof(unsigned)));
   KFBI_CUDA_TRY(cudaMemset(c.gm_counter, 0, sizeof(unsigned)));
@@ -361,21 +401,20 @@ static kfbi_status arnoldi_step(Ctx& c, int prec) {
   double* h2 = c.hcol + (m + 1);
   KFBI_TRY(op_apply(c, prec, vin, w));
   const int pk = prof_begin(c, ST_KRYLOV);
-  prof_count(c, ST_KRYLOV, 5);
-  const size_t hsm = sizeof(double) * (m + 1);
+  prof_count(c, ST_KRYLOV, 4);
   const dim3 dg(dot_blocks(M), m + 1);
+  const int ub = mvu_blocks(M), ut = MVU_X * MVU_SLICES;
   multidot_kernel<<<dg, DOT_T, 0, st>>>(c.basis, M, M, 0, c.gm_j, w, c.gm_part, m + 1,
                                         c.gm_counter, h1);
-  mv_update_kernel<<<vb(M), 256, hsm, st>>>(w, c.basis, M, M, h1, 0, c.gm_j, -1.0, nullptr,
-                                            nullptr, nullptr);
+  mv_update_kernel<<<ub, ut, 0, st>>>(w, c.basis, M, M, h1, 0, c.gm_j, -1.0, nullptr, nullptr,
+                                      nullptr);
   multidot_kernel<<<dg, DOT_T, 0, st>>>(c.basis, M, M, 0, c.gm_j, w, c.gm_part, m + 1,
                                         c.gm_counter, h2);
-  mv_update_kernel<<<vb(M), 256, hsm, st>>>(w, c.basis, M, M, h2, 0, c.gm_j, -1.0, c.gm_part,
-                                            c.gm_counter, c.scal + 5);
+  mv_update_kernel<<<ub, ut, 0, st>>>(w, c.basis, M, M, h2, 0, c.gm_j, -1.0, c.gm_part,
+                                      c.gm_counter, c.scal + 5);
   finish_kernel<<<vb(M), 256, sizeof(double) * (3 * m + 1), st>>>(
       c.gm_j, m, M, w, c.basis, M, h1, h2, c.scal + 5, c.hess, c.givens, c.gvec, c.scal, vin,
-      c.d_flags);
-  advance_kernel<<<1, 1, 0, st>>>(c.gm_j);
+      c.d_flags, c.gm_counter);
   prof_end(c, pk);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
@@ -505,9 +544,9 @@ static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const do
     const size_t lsm = sizeof(double) * (size_t)k * (k + 1);
     const bool staged = lsm <= 48 * 1024;
     lsq_kernel<<<1, 256, staged ? lsm : 0, st>>>(k, m, c.hess, c.gvec, c.yvec, staged ? 1 : 0);
-    mv_update_kernel<<<vb(M), 256, sizeof(double) * k, st>>>(x, c.basis, M, M, c.yvec, k,
-                                                            nullptr, 1.0, nullptr, nullptr,
-                                                            nullptr);
+    mv_update_kernel<<<mvu_blocks(M), MVU_X * MVU_SLICES, 0, st>>>(x, c.basis, M, M, c.yvec, k,
+                                                                  nullptr, 1.0, nullptr, nullptr,
+                                                                  nullptr);
     KFBI_CUDA_TRY(cudaGetLastError());
     KFBI_TRY(apply_K(c, prec_true, x, tmp, cnt));
     prof_count(c, ST_KRYLOV, 2);
