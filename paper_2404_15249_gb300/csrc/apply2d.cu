@@ -27,14 +27,17 @@ namespace kfbi {
 __device__ __forceinline__ int wrap(int k, int M) { return k < 0 ? k + M : (k >= M ? k - M : k); }
 
 // ------------------------------------------------------------------ correction
-// b[irr_node[k]] = (add ? b : 0) + sum_arms sum_r (wD dens + wS psi + wF f)
+// b[irr_node[k]] = (add ? b : 0) + sum_arms sum_r (wD dens + wS psi + wF f); with Blo the
+// right-hand side is the FP32 pair (B, Blo): the sum is formed in FP64 from the pair and
+// split into a pair again
 template <typename T>
 __global__ void correction_kernel(int nirr, int M, const int* __restrict__ irr_node,
                                   const int* __restrict__ arm_ptr, const int* __restrict__ arm_seg,
                                   const double* __restrict__ wD, const double* __restrict__ wS,
                                   const double* __restrict__ wF, const double* __restrict__ dens,
                                   const double* __restrict__ psi, const double* __restrict__ fctl,
-                                  T* __restrict__ B, int add, double* __restrict__ B64) {
+                                  T* __restrict__ B, int add, double* __restrict__ B64,
+                                  float* __restrict__ Blo) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nirr) return;
   double acc = 0.0;
@@ -49,8 +52,34 @@ __global__ void correction_kernel(int nirr, int M, const int* __restrict__ irr_n
     }
   }
   const int node = irr_node[k];
-  B[node] = add ? (T)((double)B[node] + acc) : (T)acc;
+  if (Blo) {
+    const double v = (add ? (double)B[node] + (double)Blo[node] : 0.0) + acc;
+    const T h = (T)v;
+    B[node] = h;
+    Blo[node] = (float)(v - (double)h);
+  } else {
+    B[node] = add ? (T)((double)B[node] + acc) : (T)acc;
+  }
   if (B64) B64[node] = acc;        // FP64 copy for the refinement residual
+}
+
+// dense right-hand side as an FP32 pair (hi, lo = FP32 of the FP64 remainder): F at inside
+// interior nodes, 0 elsewhere
+__global__ void rhs_pair_kernel(int N, const double* __restrict__ F,
+                                const uint8_t* __restrict__ inside, float* __restrict__ hi,
+                                float* __restrict__ lo) {
+  const int j = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const long idx = (long)j * N + i;
+    double v = 0.0;
+    if (F && i > 0 && j > 0) {
+      const long g = (long)j * (N + 1) + i;
+      if (inside[g]) v = F[g];
+    }
+    const float h = (float)v;
+    hi[idx] = h;
+    lo[idx] = (float)(v - (double)h);
+  }
 }
 
 // ------------------------------------------------------------------ double-single residual
@@ -518,23 +547,35 @@ __global__ void grid_to_work_kernel(int N, const double* __restrict__ G, T* __re
   }
 }
 
-// work grid(s) -> (N+1)^2 FP64 grid: value w1 (+ w2 + w3); mask keeps inside nodes only
+// work grid(s) -> (N+1)^2 FP64 grid: value w1 (+ w2 + w3); mask keeps inside nodes only.
+// Each thread takes W2G_U nodes of its row, W2G_U apart (independent loads in flight).
+constexpr int W2G_U = 4;
 template <typename T>
 __global__ void work_to_grid_kernel(int N, const T* __restrict__ w1, const float* __restrict__ w2,
                                     const float* __restrict__ w3, const uint8_t* __restrict__ mask,
                                     double* __restrict__ G) {
   const int j = blockIdx.y;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= N; i += gridDim.x * blockDim.x) {
-    const long g = (long)j * (N + 1) + i;
-    double v = 0.0;
-    if (i < N && j < N) {
-      const long q = (long)j * N + i;
-      v = (double)w1[q];
-      if (w2) v += (double)w2[q];
-      if (w3) v += (double)w3[q];
+  const int stride = gridDim.x * blockDim.x;
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 <= N; i0 += W2G_U * stride) {
+    double v[W2G_U];
+#pragma unroll
+    for (int u = 0; u < W2G_U; ++u) {
+      const int i = i0 + u * stride;
+      v[u] = 0.0;
+      if (i < N && j < N) {
+        const long q = (long)j * N + i;
+        v[u] = (double)w1[q];
+        if (w2) v[u] += (double)w2[q];
+        if (w3) v[u] += (double)w3[q];
+      }
     }
-    if (mask && !mask[g]) v = 0.0;
-    G[g] = v;
+#pragma unroll
+    for (int u = 0; u < W2G_U; ++u) {
+      const int i = i0 + u * stride;
+      if (i > N) break;
+      const long g = (long)j * (N + 1) + i;
+      G[g] = (mask && !mask[g]) ? 0.0 : v[u];
+    }
   }
 }
 
@@ -588,12 +629,12 @@ static inline int gs_blocks(long n) {
 
 template <typename T>
 static kfbi_status correct(Ctx& c, const double* dens, const double* psi, const double* fctl,
-                           T* B, int add, double* B64 = nullptr) {
+                           T* B, int add, double* B64 = nullptr, float* Blo = nullptr) {
   if (c.nirr == 0) return KFBI_OK;
   const int pr = prof_begin(c, ST_CORR);
   correction_kernel<T><<<(c.nirr + 127) / 128, 128, 0, c.stream>>>(
       c.nirr, c.M, c.irr_node, c.arm_ptr, c.arm_seg, c.arm_wD, c.arm_wS, c.arm_wF, dens, psi,
-      fctl, B, add, B64);
+      fctl, B, add, B64, Blo);
   prof_end(c, pr);
   KFBI_CUDA_TRY(cudaGetLastError());
   return KFBI_OK;
@@ -738,6 +779,17 @@ static kfbi_status dense_rhs64(Ctx& c, const double* dens, const double* f_grid,
   return correct<double>(c, dens, psi, f_ctrl, c.V64, 1);
 }
 
+// F~ + corrections as an FP32 pair in (H32, D32), without the FP64 grid (the refined
+// solves' right-hand side when no caller asks for the grid itself)
+static kfbi_status dense_rhs_pair(Ctx& c, const double* dens, const double* f_grid,
+                                  const double* f_ctrl, const double* psi = nullptr) {
+  prof_count(c, ST_GRID);
+  rhs_pair_kernel<<<rows_grid(c.N, c.N), 256, 0, c.stream>>>(c.N, f_grid, c.inside, c.H32,
+                                                             c.D32);
+  KFBI_CUDA_TRY(cudaGetLastError());
+  return correct<float>(c, dens, psi, f_ctrl, c.H32, 1, nullptr, c.D32);
+}
+
 // refined FP32 solve of the FP64 right-hand side in V64, split into an exact pair
 static kfbi_status refined_dense(Ctx& c, int steps) {
   const long n = (long)c.N * c.N;
@@ -758,6 +810,14 @@ kfbi_status interface_solve(Ctx& c, int precision, const double* dens, const dou
     return interface_solve3(c, precision, dens, f_grid, f_ctrl, rhs_grid, v_grid, out);
   }
   const int steps = refine_steps_of(precision);
+  if (steps > 0 && !rhs_grid) {                     // refined, the right-hand side as a pair
+    KFBI_TRY(dense_rhs_pair(c, dens, f_grid, f_ctrl, psi));
+    KFBI_TRY(refined_solve(c, c.H32, c.H32, c.D32, steps));
+    const float* v3 = steps > 1 ? c.T32 : nullptr;
+    if (v_grid) KFBI_TRY(to_grid<float>(c, c.V32, c.U32, v3, nullptr, v_grid));
+    if (out) KFBI_TRY(interp<float>(c, c.V32, c.U32, v3, dens, psi, f_ctrl, out, dn));
+    return KFBI_OK;
+  }
   if (precision == KFBI_FP64 || steps > 0) {
     KFBI_TRY(dense_rhs64(c, dens, f_grid, f_ctrl, psi));
     if (rhs_grid) KFBI_TRY(to_grid<double>(c, c.V64, nullptr, nullptr, nullptr, rhs_grid));
@@ -797,13 +857,14 @@ kfbi_status combined_u(Ctx& c, int precision, const double* dens, const double* 
     }
     return combined_u3(c, precision, dens, f_grid, f_ctrl, u_grid);
   }
-  KFBI_TRY(dense_rhs64(c, dens, f_grid, f_ctrl, psi));
   if (precision == KFBI_FP64) {
+    KFBI_TRY(dense_rhs64(c, dens, f_grid, f_ctrl, psi));
     KFBI_TRY(box_solve_f64(c, c.V64, c.V64));
     return to_grid<double>(c, c.V64, nullptr, nullptr, c.inside, u_grid);
   }
   const int steps = refine_steps_of(precision) > 0 ? refine_steps_of(precision) : 1;
-  KFBI_TRY(refined_dense(c, steps));
+  KFBI_TRY(dense_rhs_pair(c, dens, f_grid, f_ctrl, psi));
+  KFBI_TRY(refined_solve(c, c.H32, c.H32, c.D32, steps));
   return to_grid<float>(c, c.V32, c.U32, steps > 1 ? c.T32 : nullptr, c.inside, u_grid);
 }
 

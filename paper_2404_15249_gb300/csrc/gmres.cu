@@ -271,32 +271,44 @@ __global__ void finish_kernel(int* jp, int m, int M, const double* __restrict__ 
   advance();
 }
 
-// back substitution R y = g (k x k, R upper triangular in hess), R and g staged in
-// shared memory when they fit (dynamic: k (k + 1) doubles), else read from global memory
+// back substitution R y = g (k x k, R upper triangular in hess: column l at hess + l (m + 1)),
+// column by column across the CTA: y_i = g_i / R_ii, then every thread updates its entries
+// g_r -= R_ri y_i (r < i) of column i.  The reciprocals 1 / R_ii are formed in parallel
+// first, so the serial chain holds one multiplication per column instead of an FP64
+// division (the columns of R staged in shared memory when they fit; dynamic shared memory:
+// k (k + 1) doubles if staged, else 2k)
 __global__ void lsq_kernel(int k, int m, const double* hess, const double* gvec, double* y,
                            int staged) {
   extern __shared__ double dyn[];
   const double* R = hess;
   int ldr = m + 1;
-  const double* g = gvec;
+  double* g;
+  double* rinv;
   if (staged) {
     double* Rs = dyn;                 // k x k, column l at Rs[l * k]
-    double* gsh = dyn + (size_t)k * k;
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
       const int l = e / k, i = e - l * k;
       Rs[e] = hess[(size_t)l * (m + 1) + i];
     }
-    for (int i = threadIdx.x; i < k; i += blockDim.x) gsh[i] = gvec[i];
-    __syncthreads();
     R = Rs;
     ldr = k;
-    g = gsh;
+    g = dyn + (size_t)k * k;
+  } else {
+    g = dyn;
   }
-  if (threadIdx.x != 0) return;
+  rinv = g + k;                       // the reciprocals after g
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    g[i] = gvec[i];
+    rinv[i] = 1.0 / R[(size_t)i * ldr + i];
+  }
+  __syncthreads();
   for (int i = k - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int l = i + 1; l < k; ++l) s -= R[(size_t)l * ldr + i] * y[l];
-    y[i] = s / R[(size_t)i * ldr + i];
+    const double yi = g[i] * rinv[i];
+    if (threadIdx.x == 0) y[i] = yi;
+    const double* col = R + (size_t)i * ldr;
+    for (int r = threadIdx.x; r < i; r += blockDim.x) g[r] -= col[r] * yi;
+    __syncthreads();
   }
 }
 
@@ -541,9 +553,10 @@ static kfbi_status gmres_run(Ctx& c, const Relax& relax, int prec_true, const do
         }
     }
     prof_count(c, ST_KRYLOV, 2);
-    const size_t lsm = sizeof(double) * (size_t)k * (k + 1);
+    const size_t lsm = sizeof(double) * (size_t)k * (k + 2);
     const bool staged = lsm <= 48 * 1024;
-    lsq_kernel<<<1, 256, staged ? lsm : 0, st>>>(k, m, c.hess, c.gvec, c.yvec, staged ? 1 : 0);
+    lsq_kernel<<<1, 256, staged ? lsm : sizeof(double) * 2 * k, st>>>(k, m, c.hess, c.gvec, c.yvec,
+                                                                       staged ? 1 : 0);
     mv_update_kernel<<<mvu_blocks(M), MVU_X * MVU_SLICES, 0, st>>>(x, c.basis, M, M, c.yvec, k,
                                                                   nullptr, 1.0, nullptr, nullptr,
                                                                   nullptr);
