@@ -234,11 +234,12 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
     // KFBI_DST_VARIANTS="r32,c32,r64,c64" fixes the transform variants (profiling runs,
     // where the autotuner's timings would be distorted by the profiler)
     c.tri_k0 = kfbi::tri_first_mode(c);
+    c.ypass_k0 = kfbi::ypass_first_mode(c);
     const char* fixed = std::getenv("KFBI_DST_VARIANTS");
     int v[4];
     if (fixed && std::sscanf(fixed, "%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3]) == 4 &&
         v[0] >= 0 && v[0] <= 1 && v[2] >= 0 && v[2] <= 1 && v[1] >= 0 && v[1] <= 8 &&
-        v[3] >= 0 && v[3] <= 7 && (v[1] != 8 || (c.tri_k0 > 0 && c.tri_k0 < c.N))) {
+        v[3] >= 0 && v[3] <= 7 && (v[1] != 8 || (c.ypass_k0 > 0 && c.ypass_k0 < c.N))) {
       c.rows_variant[0] = v[0];
       c.cols_variant[0] = v[1];
       c.rows_variant[1] = v[2];

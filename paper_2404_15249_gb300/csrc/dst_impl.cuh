@@ -1091,7 +1091,7 @@ kfbi_status autotune(Ctx& c, T* V, const cx<T>* tw, const T* lam, int* rows_choi
   best = 1e30f;
   int best_v = 0;
   // FP32 2-D with well-conditioned modes: also the y-pass on the row layout (variant 8)
-  const bool rowpass = std::is_same<T, float>::value && c.dim == 2 && c.tri_k0 > 0 && c.tri_k0 < N;
+  const bool rowpass = std::is_same<T, float>::value && c.dim == 2 && c.ypass_k0 > 0 && c.ypass_k0 < N;
   for (int v : {0, 1, 2, 3, 4, 6, 8}) {
     if (v == 8 && !rowpass) continue;
     float ms = 0.f;

@@ -163,9 +163,9 @@ kfbi_status launch_tri(Ctx& c, float* X, int k0) {
 
 }  // namespace
 
-// first x-mode of the tridiagonal pass: the smallest k >= 1 with |c*(k)| <= TRI_CMAX, in
-// FP64 on the host (N: no tridiagonal pass); KFBI_TRI=0 keeps every mode on the FFT pass
-int tri_first_mode(const Ctx& c) {
+// the smallest x-mode k >= 1 with |c*(k)| <= cmax, in FP64 on the host, rounded up to a
+// multiple of 32 (N: none); KFBI_TRI=0 keeps every mode on the FFT pass
+static int first_mode_below(const Ctx& c, double cmax) {
   if (const char* e = std::getenv("KFBI_TRI"))
     if (e[0] == '0') return c.N;
   if (c.dim != 2 || c.N < 64) return c.N;
@@ -176,10 +176,18 @@ int tri_first_mode(const Ctx& c) {
     const double cst = 2.0 / ((2.0 + mu) + std::sqrt((2.0 + mu) * (2.0 + mu) - 4.0));
     // rounded up to a multiple of 32: the filter pass then moves whole 128-byte rows of
     // 32 modes (the extra modes take the transform pair, accurate for every mode)
-    if (cst <= TRI_CMAX) return ((k + 31) / 32) * 32 < c.N ? ((k + 31) / 32) * 32 : c.N;
+    if (cst <= cmax) return ((k + 31) / 32) * 32 < c.N ? ((k + 31) / 32) * 32 : c.N;
   }
   return c.N;
 }
+
+// first x-mode of the tridiagonal pass (transposed layout): |c*(k)| <= TRI_CMAX
+int tri_first_mode(const Ctx& c) { return first_mode_below(c, TRI_CMAX); }
+
+// first x-mode of the recursive filters of the row-layout y-pass: |c*(k)| <= 0.95 (warm-ups
+// of at most 368 rows; the filters' FP32 error for the mode at the threshold is about 1e-6
+// of its amplitude, modelled in numpy at N = 4096, against 3e-7 at 0.825)
+int ypass_first_mode(const Ctx& c) { return first_mode_below(c, 0.95); }
 
 kfbi_status ytri_f32(Ctx& c, float* X, int k0) {
   if (k0 >= c.N) return KFBI_OK;

@@ -4,7 +4,7 @@
 //     (T_y + lambda_k - kappa^2) v = x,   T_y = tridiag(1, -2, 1) / h^2,  v_0 = v_N = 0,
 // then the inverse x-transform's scale 2/N.
 //
-// Well-conditioned modes (k >= k0, the elimination coefficient |c| <= 0.825): the operator
+// Well-conditioned modes (k >= k0, the elimination coefficient |c| <= 0.95): the operator
 // of the scaled system  v_{j-1} - mu v_j + v_{j+1} = h^2 x_j,  mu = 2 + h^2 (kappa^2 - lambda_k),
 // factors on infinite sequences as -(1/c) (I - c S-)(I - c S+) with c + 1/c = mu, 0 < c < 1
 // (S-, S+ the shifts), so v = -c h^2 F+ F- x with the causal filter F-: u_j = x_j + c u_{j-1}
@@ -13,7 +13,7 @@
 // solution odd about 0 and N, so it is the finite system's solution with v_0 = v_N = 0.
 // A thread owns one mode (consecutive modes across a warp: every row access is one
 // coalesced 128-byte segment) and one chunk of MC rows: it runs F+ down from w rows past its
-// chunk (the truncated tail weighs c^w <= 1e-8), keeps the chunk's values in registers,
+// chunk (the truncated tail weighs c^w <= 1e-8; w <= 368), keeps the chunk's values in registers,
 // continues F+ over the w rows before the chunk while summing the causal state
 // u_{s-1} = sum_m c^m z_{s-1-m}, then runs F- forward over the chunk.  The warm-ups read
 // rows of the neighbouring chunks, which other warps own, so the pass is out of place: it
@@ -28,7 +28,7 @@
 namespace kfbi {
 namespace {
 
-constexpr int YC_W = 97;            // longest warm-up (before rounding up to 16): 0.825^97 < 1e-8
+constexpr int YC_W = 361;           // longest warm-up (before rounding up to 16): 0.95^361 < 1e-8
 constexpr int YC_WARPS = 8;         // warps per CTA: 8 consecutive chunks of the same 32 modes
 constexpr int YC_THREADS = 32 * YC_WARPS;
 
@@ -96,22 +96,24 @@ __device__ __forceinline__ void filter_chunk(const float* __restrict__ col, int 
   }
 }
 
-// Warp w of CTA (g, b) owns modes k0 + 32 g + lane and chunk b YC_WARPS + w of MC rows; W
+// Warp w of CTA (b, g) owns modes k0 + 32 g + lane and chunk b YC_WARPS + w of MC rows; W
 // comes from the group's lowest mode, whose c is the largest, rounded up to a multiple of
 // 16.  Every access is one coalesced 128-byte row segment (the group's 32 modes; k0 is a
-// multiple of 32).
+// multiple of 32).  The groups vary slowest over the grid, so the lowest modes, whose
+// warm-ups are the longest, start first.
 template <int MC>
 __global__ void __launch_bounds__(YC_THREADS)
     ycol_filter_kernel(const float* __restrict__ V, float* __restrict__ Y, int N, int k0,
                        const float* __restrict__ lam, float h2, float h2k2, float scale) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int kb = k0 + blockIdx.x * 32;
+  const int kb = k0 + blockIdx.y * 32;
   const int k = kb + lane;
-  const int s = (blockIdx.y * YC_WARPS + warp) * MC;               // first row of the chunk
+  const int s = (blockIdx.x * YC_WARPS + warp) * MC;               // first row of the chunk
   if (s >= N) return;                                              // uniform per warp
   const bool act = k < N;
   const int kk = act ? k : N - 1;                                  // idle lanes read a valid column
-  const int W = (min(YC_W, (int)ceilf(-18.43f / logf(filter_c(lam, kb, h2, h2k2))) + 1) + 15) / 16 * 16;
+  // (at most N, so every row read, warm-ups included, lies within one period each side)
+  const int W = min((min(YC_W, (int)ceilf(-18.43f / logf(filter_c(lam, kb, h2, h2k2))) + 1) + 15) / 16 * 16, N);
   const float c = filter_c(lam, kk, h2, h2k2);
   const float g = -c * h2 * scale;
   float r[MC];
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(YC_THREADS)
 template <int MC>
 kfbi_status launch_filter(Ctx& c, const float* V, float* Y, int k0) {
   const int N = c.N;
-  const dim3 grid((N - k0 + 31) / 32, (N + YC_WARPS * MC - 1) / (YC_WARPS * MC));
+  const dim3 grid((N + YC_WARPS * MC - 1) / (YC_WARPS * MC), (N - k0 + 31) / 32);
   const int pr = prof_begin(c, ST_TRI);
   ycol_filter_kernel<MC><<<grid, YC_THREADS, 0, c.stream>>>(
       V, Y, N, k0, c.t32.lam, (float)(c.h * c.h), (float)(c.h * c.h * c.kappa2), (float)(2.0 / N));
@@ -138,9 +140,9 @@ kfbi_status launch_filter(Ctx& c, const float* V, float* Y, int k0) {
 }  // namespace
 
 // the y-pass of the FP32 2-D box solve from V into Y (row layout, Y != V); the low modes
-// k < tri_k0 take the transform pair on the side stream
+// k < ypass_k0 take the transform pair on the side stream
 kfbi_status ypass_rows_f32(Ctx& c, const float* V, float* Y) {
-  const int N = c.N, k0 = c.tri_k0;
+  const int N = c.N, k0 = c.ypass_k0;
   if (k0 <= 0 || k0 >= N || k0 % 32 != 0 || N % 32 != 0) {
     set_error("row-layout y-pass: needs 0 < k0 < N, both multiples of 32 (N = %d, k0 = %d)", N, k0);
     return KFBI_ERR_UNSUPPORTED;

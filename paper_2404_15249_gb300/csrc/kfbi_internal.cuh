@@ -188,6 +188,7 @@ struct Ctx {
   float* tc_slo = nullptr;                          // sine matrix, TF32 low part
   void* tc_maps = nullptr;                          // TMA tensor maps of the GEMM operands
   int tri_k0 = 0;        // 2-D FP32: x-modes >= tri_k0 solved along y by elimination (N: none)
+  int ypass_k0 = 0;      // 2-D FP32 row-layout y-pass: x-modes >= ypass_k0 by the filters (N: none)
   BoxTables<float> t32{};
   BoxTables<double> t64{};
   int rows_variant[2] = {0, 0};                     // row-pass variant per precision (autotuned)
@@ -255,7 +256,7 @@ kfbi_status x_pass_f32(Ctx& c, const float* X, float* V);
 // FP32 2-D: the box solve after its first row pass (column pass variant + last row pass)
 kfbi_status box_solve_after_rows_f32(Ctx& c, float* work);
 // FP32 2-D y-pass on the row layout from V into Y (Y != V): recursive filters for the
-// modes k >= tri_k0, the transform pair (side stream) for the others (dst_ycol.cu); its
+// modes k >= ypass_k0, the transform pair (side stream) for the others (dst_ycol.cu); its
 // result grid is ypass_out(c), the second half of the transposed scratch XT
 kfbi_status ypass_rows_f32(Ctx& c, const float* V, float* Y);
 // the transform pair along y (with the spectral division) of columns [0, ncols) of the
@@ -292,6 +293,8 @@ void free_tc(Ctx& c);
 
 // tridiagonal y-solves of the well-conditioned x-modes (dst_tri.cu)
 int tri_first_mode(const Ctx& c);
+// first x-mode of the row-layout y-pass filters (dst_tri.cu)
+int ypass_first_mode(const Ctx& c);
 kfbi_status ytri_f32(Ctx& c, float* X, int k0);
 
 // 3-D (kfbi3d.cu, dst3d.cu): setup and the same stages on the N^3 work grid
