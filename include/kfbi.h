@@ -333,13 +333,14 @@ kfbi_status kfbi_measure_fma_peak(int fp64, double* h_tflops, void* stream);
 
 /* ---------------------------------------------------------------- batched problems
    Many independent problems (uneven N and M, 2-D or 3-D) solved together: a pool of up
-   to 8 host workers, each driving its own CUDA stream, takes problems from a shared queue
+   to 16 host workers, each driving its own CUDA stream, takes problems from a shared queue
    in decreasing order of cost ((N+1)^dim log N; longest first) and solves all right-hand
-   sides of a problem in turn, each with the context's own solver options, so up to 8
+   sides of a problem in turn, each with the context's own solver options, so up to 16
    problems run concurrently on the device (the environment variable KFBI_BATCH_WORKERS,
-   1..64, sets another count; on one GB300 4 to 8 are equally fast for the 256-problem
-   workload, 16 and 32 slower).  Each context is used by one worker at a time.  The
-   contexts stay owned by the caller and must outlive the batch. */
+   1..64, sets another count; on one GB300, with the Arnoldi steps as CUDA graphs, 16 were
+   fastest for the 256-problem workload: 729 ms against 798 ms with 8 and 778 ms with 32).
+   Each context is used by one worker at a time.  The contexts stay owned by the caller
+   and must outlive the batch. */
 typedef struct kfbi_batch_s* kfbi_batch;
 
 kfbi_status kfbi_batch_create(const kfbi_ctx* ctxs, int count, kfbi_batch* out);

@@ -103,48 +103,81 @@ __device__ __forceinline__ DSPair iterate_at(const float* c1, const float* c2, l
 // r = b - (Lap_h - kappa^2) v, v = c1 (+ c2), b = bhi + blo (dense) or 0 (bhi == nullptr);
 // kappa^2 = k2hi + k2lo exactly.  Every product and sum that can cancel is carried as an
 // exact FP32 pair; only the final residual is rounded to FP32.
-__global__ void ds_residual_kernel(int N, float inv_h2, float k2hi, float k2lo,
-                                   const float* __restrict__ bhi, const float* __restrict__ blo,
-                                   const float* __restrict__ c1, const float* __restrict__ c2,
-                                   float* __restrict__ r) {
-  const int j = blockIdx.y;
-  const long base = (long)j * N;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const long idx = base + i;
-    if (i == 0 || j == 0) {
-      r[idx] = 0.f;
-      continue;
-    }
-    const DSPair vc = iterate_at(c1, c2, idx);
-    const DSPair ve = (i + 1 < N) ? iterate_at(c1, c2, idx + 1) : DSPair{0.f, 0.f};
-    const DSPair vw = iterate_at(c1, c2, idx - 1);
-    const DSPair vn = (j + 1 < N) ? iterate_at(c1, c2, idx + N) : DSPair{0.f, 0.f};
-    const DSPair vs = iterate_at(c1, c2, idx - N);
-    // S = ve + vw + vn + vs - 4 vc  as  s4 + lo
-    float s1, t1, s2, t2, s3, t3, s4, t4;
-    two_sum(ve.hi, vw.hi, s1, t1);
-    two_sum(vn.hi, vs.hi, s2, t2);
-    two_sum(s1, s2, s3, t3);
-    two_sum(s3, -4.f * vc.hi, s4, t4);
-    const float lo = ((t1 + t2) + (t3 + t4)) + ((ve.lo + vw.lo) + (vn.lo + vs.lo) - 4.f * vc.lo);
-    // S / h^2 = p1 + e1 (1/h^2 is a power-of-two multiple of an exact FP32 value)
-    const float p1 = s4 * inv_h2;
-    const float e1 = fmaf(s4, inv_h2, -p1) + lo * inv_h2;
-    // kappa^2 v = p2 + e2
-    const float p2 = k2hi * vc.hi;
-    const float e2 = fmaf(k2hi, vc.hi, -p2) + (k2hi * vc.lo + k2lo * vc.hi);
-    // r = b - p1 + p2 - e1 + e2
-    float d, de;
-    two_sum(p2, -p1, d, de);
-    float tail = de - e1 + e2;
-    if (bhi) {
-      float d2, de2;
-      two_sum(bhi[idx], d, d2, de2);
-      d = d2;
-      tail += de2 + blo[idx];
-    }
-    r[idx] = d + tail;
+// Four consecutive points of a row per thread (N a multiple of 4): the row and the rows
+// above and below as 16-byte loads, the two outer neighbours as scalars.
+__device__ __forceinline__ float ds_point(float inv_h2, float k2hi, float k2lo, DSPair vc,
+                                          DSPair ve, DSPair vw, DSPair vn, DSPair vs,
+                                          const float* bhi, const float* blo, int idx) {
+  float s1, t1, s2, t2, s3, t3, s4, t4;
+  two_sum(ve.hi, vw.hi, s1, t1);
+  two_sum(vn.hi, vs.hi, s2, t2);
+  two_sum(s1, s2, s3, t3);
+  two_sum(s3, -4.f * vc.hi, s4, t4);
+  const float lo = ((t1 + t2) + (t3 + t4)) + ((ve.lo + vw.lo) + (vn.lo + vs.lo) - 4.f * vc.lo);
+  const float p1 = s4 * inv_h2;
+  const float e1 = fmaf(s4, inv_h2, -p1) + lo * inv_h2;
+  const float p2 = k2hi * vc.hi;
+  const float e2 = fmaf(k2hi, vc.hi, -p2) + (k2hi * vc.lo + k2lo * vc.hi);
+  float d, de;
+  two_sum(p2, -p1, d, de);
+  float tail = de - e1 + e2;
+  if (bhi) {
+    float d2, de2;
+    two_sum(bhi[idx], d, d2, de2);
+    d = d2;
+    tail += de2 + blo[idx];
   }
+  return d + tail;
+}
+
+__device__ __forceinline__ void ds_row4(const float* c1, const float* c2, int q, DSPair (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(c1 + q);
+  if (!c2) {
+    v[0] = {a.x, 0.f};
+    v[1] = {a.y, 0.f};
+    v[2] = {a.z, 0.f};
+    v[3] = {a.w, 0.f};
+    return;
+  }
+  const float4 b = *reinterpret_cast<const float4*>(c2 + q);
+  two_sum(a.x, b.x, v[0].hi, v[0].lo);
+  two_sum(a.y, b.y, v[1].hi, v[1].lo);
+  two_sum(a.z, b.z, v[2].hi, v[2].lo);
+  two_sum(a.w, b.w, v[3].hi, v[3].lo);
+}
+
+__global__ void ds_residual4_kernel(int N, float inv_h2, float k2hi, float k2lo,
+                                    const float* __restrict__ bhi, const float* __restrict__ blo,
+                                    const float* __restrict__ c1, const float* __restrict__ c2,
+                                    float* __restrict__ r) {
+  const int j = blockIdx.y;
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (i0 >= N) return;
+  const int base = j * N + i0;
+  float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (j > 0) {
+    DSPair c[4], n[4], so[4];
+    ds_row4(c1, c2, base, c);
+    ds_row4(c1, c2, base - N, so);
+    if (j + 1 < N) {
+      ds_row4(c1, c2, base + N, n);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) n[u] = {0.f, 0.f};
+    }
+    const DSPair w0 = i0 > 0 ? iterate_at(c1, c2, base - 1) : DSPair{0.f, 0.f};
+    const DSPair e3 = i0 + 4 < N ? iterate_at(c1, c2, base + 4) : DSPair{0.f, 0.f};
+    float o[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const DSPair vw = u == 0 ? w0 : c[u > 0 ? u - 1 : 0];
+      const DSPair ve = u == 3 ? e3 : c[u < 3 ? u + 1 : 3];
+      o[u] = (i0 + u == 0) ? 0.f
+                           : ds_point(inv_h2, k2hi, k2lo, c[u], ve, vw, n[u], so[u], bhi, blo, base + u);
+    }
+    res = make_float4(o[0], o[1], o[2], o[3]);
+  }
+  *reinterpret_cast<float4*>(r + base) = res;
 }
 
 // r = b - (Lap_h - kappa^2)(c1 + c2) at the irregular nodes, in FP64 (sparse b)
@@ -683,8 +716,8 @@ static kfbi_status refine_steps(Ctx& c, const float* bhi, const float* blo, int 
   for (int s = 0; s < steps; ++s) {
     const float* c2 = s == 0 ? nullptr : c.U32;      // current iterate = V32 (+ U32)
     const int pr = prof_begin(c, ST_REFINE);
-    ds_residual_kernel<<<rows_grid(c.N, c.N), 256, 0, c.stream>>>(c.N, inv_h2, k2hi, k2lo, bhi,
-                                                                  blo, c.V32, c2, c.W32);
+    ds_residual4_kernel<<<dim3((c.N / 4 + 255) / 256, c.N), 256, 0, c.stream>>>(
+        c.N, inv_h2, k2hi, k2lo, bhi, blo, c.V32, c2, c.W32);
     if (!bhi && c.nirr > 0)
       residual_fix_kernel<<<(c.nirr + 127) / 128, 128, 0, c.stream>>>(
           c.nirr, c.N, 1.0 / (c.h * c.h), c.kappa2, c.irr_node, c.B64, c.V32, c2, c.W32);
