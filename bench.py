@@ -132,7 +132,7 @@ YPASS = "ycol_filter_kernel+ycol_lines_kernel"
 KERNEL_SOURCE = {"rows_kernel": ("dst_impl.cuh",), "yline_kernel": ("dst_impl.cuh",),
                  "cols_kernel": ("dst_impl.cuh",), "transpose_vec_kernel": ("dst_impl.cuh",),
                  "ytri_kernel": ("dst_tri.cu",), "sparse_rows_kernel": ("apply2d.cu",),
-                 "sparse_out_kernel": ("apply2d.cu",), "ds_residual_kernel": ("apply2d.cu",),
+                 "sparse_out_kernel": ("apply2d.cu",), "ds_residual4_kernel": ("apply2d.cu",),
                  YPASS: ("dst_ycol.cu", "dst_impl.cuh")}
 
 

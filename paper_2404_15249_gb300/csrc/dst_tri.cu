@@ -184,10 +184,11 @@ static int first_mode_below(const Ctx& c, double cmax) {
 // first x-mode of the tridiagonal pass (transposed layout): |c*(k)| <= TRI_CMAX
 int tri_first_mode(const Ctx& c) { return first_mode_below(c, TRI_CMAX); }
 
-// first x-mode of the recursive filters of the row-layout y-pass: |c*(k)| <= 0.95 (warm-ups
-// of at most 368 rows; the filters' FP32 error for the mode at the threshold is about 1e-6
-// of its amplitude, modelled in numpy at N = 4096, against 3e-7 at 0.825)
-int ypass_first_mode(const Ctx& c) { return first_mode_below(c, 0.95); }
+// first x-mode of the recursive filters of the row-layout y-pass: |c*(k)| <= 0.9 (warm-ups
+// of at most 176 rows; the filters' FP32 error for the mode at the threshold is 4.7e-7 of
+// its amplitude, modelled in numpy at N = 4096, against 3.4e-7 at 0.825 and 9.9e-7 at 0.95;
+// 0.9 to 0.95 gave the same solve time at N = 4096, 0.88 and 0.97 slower)
+int ypass_first_mode(const Ctx& c) { return first_mode_below(c, 0.9); }
 
 kfbi_status ytri_f32(Ctx& c, float* X, int k0) {
   if (k0 >= c.N) return KFBI_OK;

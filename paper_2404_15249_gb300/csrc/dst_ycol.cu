@@ -4,7 +4,7 @@
 //     (T_y + lambda_k - kappa^2) v = x,   T_y = tridiag(1, -2, 1) / h^2,  v_0 = v_N = 0,
 // then the inverse x-transform's scale 2/N.
 //
-// Well-conditioned modes (k >= k0, the elimination coefficient |c| <= 0.95): the operator
+// Well-conditioned modes (k >= k0, the elimination coefficient |c| <= 0.9): the operator
 // of the scaled system  v_{j-1} - mu v_j + v_{j+1} = h^2 x_j,  mu = 2 + h^2 (kappa^2 - lambda_k),
 // factors on infinite sequences as -(1/c) (I - c S-)(I - c S+) with c + 1/c = mu, 0 < c < 1
 // (S-, S+ the shifts), so v = -c h^2 F+ F- x with the causal filter F-: u_j = x_j + c u_{j-1}
@@ -13,7 +13,7 @@
 // solution odd about 0 and N, so it is the finite system's solution with v_0 = v_N = 0.
 // A thread owns one mode (consecutive modes across a warp: every row access is one
 // coalesced 128-byte segment) and one chunk of MC rows: it runs F+ down from w rows past its
-// chunk (the truncated tail weighs c^w <= 1e-8; w <= 368), keeps the chunk's values in registers,
+// chunk (the truncated tail weighs c^w <= 1e-8; w <= 176), keeps the chunk's values in registers,
 // continues F+ over the w rows before the chunk while summing the causal state
 // u_{s-1} = sum_m c^m z_{s-1-m}, then runs F- forward over the chunk.  The warm-ups read
 // rows of the neighbouring chunks, which other warps own, so the pass is out of place: it
@@ -28,7 +28,7 @@
 namespace kfbi {
 namespace {
 
-constexpr int YC_W = 361;           // longest warm-up (before rounding up to 16): 0.95^361 < 1e-8
+constexpr int YC_W = 176;           // longest warm-up (before rounding up to 16): 0.9^176 < 1e-8
 constexpr int YC_WARPS = 8;         // warps per CTA: 8 consecutive chunks of the same 32 modes
 constexpr int YC_THREADS = 32 * YC_WARPS;
 
