@@ -234,6 +234,31 @@ def fp64_roofline(stage_ms, N, alu):
 DST_STAGES = ("dst_rows_f32", "dst_cols_f32", "dst_tri_f32", "sparse_x_f32", "transpose")
 
 
+def dst_bytes(stage_ms, N):
+    """Algorithmic bytes of the box solves behind the launch counts in stage_ms: 24 B per
+    interior unknown per dense-right-hand-side box solve and 16 B per plain apply's
+    sparse one (a plain apply runs one sparse x-transform and one row pass, a dense box
+    solve two row passes); returns (bytes, dense solves, sparse solves)."""
+    sparse = stage_ms.get("sparse_x_f32", (0.0, 0))[1]
+    rows = stage_ms.get("dst_rows_f32", (0.0, 0))[1]
+    dense = max(rows - sparse, 0) / 2.0
+    return (24.0 * dense + 16.0 * sparse) * float(N - 1) ** 2, dense, sparse
+
+
+def batch_dst_roofline(per_ctx, wall_ms):
+    """The box-solve bytes of a whole batch against the HBM roofline: per_ctx holds
+    (N, stage_ms) of every context over one batch (launch counts), wall_ms the batch's
+    wall time without stage events; concurrent problems overlap, so this is the whole
+    job's rate, not one kernel's."""
+    total = sum(dst_bytes(st, n)[0] for n, st in per_ctx)
+    if wall_ms <= 0 or total <= 0:
+        return None
+    peak, src = peaks()
+    ach = total / (wall_ms / 1e3) / 1e9
+    return {"bound": "hbm", "algorithmic_bytes": total, "wall_ms": wall_ms, "achieved": ach,
+            "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_source": src}
+
+
 def dst_stage_roofline(stage_ms, N, solves):
     """The box-solve (DST) stage of the mixed solve as a whole against the HBM roofline:
     algorithmic bytes 24 B per interior unknown for a box solve of a dense right-hand side
@@ -247,11 +272,8 @@ def dst_stage_roofline(stage_ms, N, solves):
     ms = sum(stage_ms[k][0] for k in DST_STAGES if k in stage_ms)
     if ms <= 0 or solves <= 0:
         return None
-    sparse = stage_ms.get("sparse_x_f32", (0.0, 0))[1] / solves
-    rows = stage_ms.get("dst_rows_f32", (0.0, 0))[1] / solves
-    dense = (rows - sparse) / 2.0
-    unknowns = float(N - 1) ** 2
-    nbytes = (24.0 * dense + 16.0 * sparse) * unknowns
+    nbytes, dense, sparse = dst_bytes(stage_ms, N)
+    nbytes, dense, sparse = nbytes / solves, dense / solves, sparse / solves
     peak, src = peaks()
     ach = nbytes / (ms / solves / 1e3) / 1e9
     return {"bound": "hbm", "stage": "box solves of one mixed BVP solve (" + ", ".join(
@@ -808,10 +830,12 @@ def run_batch_companion(a, dev):
     wall_prof = e0.elapsed_time(e1)
     busy = 0.0
     launches = 0
-    for c in ctxs:
+    per_ctx = []
+    for c, (p, _) in zip(ctxs, cfg):
         t = c.profile_read()
         busy += sum(v[0] for v in t.values())
         launches += sum(v[1] for v in t.values())
+        per_ctx.append((p.N, t))
         c.profile(False)
     # the same batch in plain FP64
     for c in ctxs:
@@ -834,6 +858,7 @@ def run_batch_companion(a, dev):
             "fp64_not_converged": bad64[:16],
             "fp64_total_iterations": sum(i["iterations"] for i in infos64),
             "fp64_max_err_inf": err64,
+            "dst_roofline": batch_dst_roofline(per_ctx, ms),
             "device_busy": {"kernel_ms_sum": busy, "wall_ms": wall_prof, "launches": launches,
                             "note": "summed device time of every launch of every context "
                                     "(events around each launch) over the wall time of the "

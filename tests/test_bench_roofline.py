@@ -84,3 +84,16 @@ def test_fp64_roofline_uses_the_measured_peak():
     assert r["achieved"] == pytest.approx(flops / (100.0 / 200 / 1e3) / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / 1.2)
     assert bench.fp64_roofline(stages, N, None) is None
+
+
+def test_batch_dst_roofline_sums_the_box_solve_bytes_of_every_context():
+    # two contexts: one plain apply (1 sparse x-transform + 1 row pass) at N = 64 and one
+    # dense box solve (2 row passes) at N = 128, over a 2 ms batch
+    per_ctx = [(64, {"sparse_x_f32": (0.1, 1), "dst_rows_f32": (0.1, 1)}),
+               (128, {"dst_rows_f32": (0.2, 2)})]
+    r = bench.batch_dst_roofline(per_ctx, 2.0)
+    want = 16.0 * 63 ** 2 + 24.0 * 127 ** 2
+    assert r["algorithmic_bytes"] == pytest.approx(want)
+    assert r["achieved"] == pytest.approx(want / 2e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert bench.batch_dst_roofline([], 2.0) is None
