@@ -68,3 +68,20 @@ def test_precision_stress_3d_ellipsoid_helmholtz_512():
     # at least second order; the max-norm error near the surface falls faster than 4x at
     # these sizes (7.7 measured, the FP64 path alike)
     assert 3.0 < errs[0] / errs[1] < 10.0, errs
+
+
+def test_mixed_solve_meets_its_tolerance_with_the_fp64_operator():
+    """The mixed solver stops on true residuals formed with twice-refined FP32 applies; its
+    density must also meet the tolerance when the residual is recomputed with the plain
+    FP64 operator (2-D flower, N = 1024, kappa = 1, tol 1e-10: measured 6.8e-11)."""
+    prob = W.config_helmholtz(1024, 1.0, "flower")
+    ctx = K.Kfbi2D(prob.iface.pts, prob.iface.normals, prob.iface.curv, prob.N, prob.kappa,
+                   precision=K.KFBI_MIXED_FP32, tol=1e-10)
+    dev = torch.device("cuda")
+    fg, fc, gc = (torch.as_tensor(x, device=dev) for x in (prob.f_grid(), prob.f_ctrl(), prob.g_ctrl()))
+    _, phi, info = ctx.solve_bvp(fg, fc, gc)
+    assert info["converged"]
+    ghat = gc - ctx.apply_volume(fg, fc, K.KFBI_FP64)
+    r = ghat - ctx.apply_layer_potential(phi, 0, K.KFBI_FP64)
+    assert float(torch.linalg.norm(r) / torch.linalg.norm(ghat)) <= 1.5e-10
+    ctx.close()
