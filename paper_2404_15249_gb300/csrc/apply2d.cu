@@ -20,6 +20,7 @@
 //                        FP32 pair (hi, lo) - FP32 instructions only, because FP64
 //                        throughput on GB300 is 1/64 of FP32.  Where b is sparse (double
 //                        layer) the irregular nodes are recomputed in FP64.
+#include "fpbits.cuh"
 #include "kfbi_internal.cuh"
 
 namespace kfbi {
@@ -76,9 +77,10 @@ __global__ void rhs_pair_kernel(int N, const double* __restrict__ F,
       const long g = (long)j * (N + 1) + i;
       if (inside[g]) v = F[g];
     }
-    const float h = (float)v;
+    float h, l;
+    f64_to_f32_pair(v, h, l);                    // integer operations, not the FP64 pipe
     hi[idx] = h;
-    lo[idx] = (float)(v - (double)h);
+    lo[idx] = l;
   }
 }
 
@@ -201,10 +203,10 @@ __global__ void split_kernel(long n, const double* __restrict__ b, float* __rest
                              float* __restrict__ lo) {
   for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
        k += (long)gridDim.x * blockDim.x) {
-    const double x = b[k];
-    const float h = (float)x;
+    float h, l;
+    f64_to_f32_pair(b[k], h, l);                 // integer operations, not the FP64 pipe
     hi[k] = h;
-    lo[k] = (float)(x - (double)h);
+    lo[k] = l;
   }
 }
 
@@ -580,6 +582,9 @@ __global__ void grid_to_work_kernel(int N, const double* __restrict__ G, T* __re
   }
 }
 
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f32_to_f64(x); }   // exact, integer ops
+
 // work grid(s) -> (N+1)^2 FP64 grid: value w1 (+ w2 + w3); mask keeps inside nodes only.
 // Each thread takes W2G_U nodes of its row, W2G_U apart (independent loads in flight).
 constexpr int W2G_U = 4;
@@ -597,9 +602,9 @@ __global__ void work_to_grid_kernel(int N, const T* __restrict__ w1, const float
       v[u] = 0.0;
       if (i < N && j < N) {
         const long q = (long)j * N + i;
-        v[u] = (double)w1[q];
-        if (w2) v[u] += (double)w2[q];
-        if (w3) v[u] += (double)w3[q];
+        v[u] = to_f64(w1[q]);
+        if (w2) v[u] += to_f64(w2[q]);
+        if (w3) v[u] += to_f64(w3[q]);
       }
     }
 #pragma unroll
