@@ -25,6 +25,7 @@
 #include <numeric>
 #include <vector>
 
+#include "fpbits.cuh"
 #include "kfbi_internal.cuh"
 
 namespace kfbi {
@@ -559,10 +560,10 @@ __global__ void residual_fix3_kernel(int nirr, int N, double inv_h2, double kapp
 __global__ void split3_kernel(long n, const double* __restrict__ b, float* __restrict__ hi,
                               float* __restrict__ lo) {
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const double x = b[q];
-    const float h = (float)x;
+    float h, l;
+    f64_to_f32_pair(b[q], h, l);                 // integer operations, not the FP64 pipe
     hi[q] = h;
-    lo[q] = (float)(x - (double)h);
+    lo[q] = l;
   }
 }
 
@@ -570,7 +571,7 @@ __global__ void split3_kernel(long n, const double* __restrict__ b, float* __res
 __global__ void sum3_kernel(long n, const float* __restrict__ w1, const float* __restrict__ w2,
                             const float* __restrict__ w3, double* __restrict__ out) {
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x)
-    out[q] = (double)w1[q] + (w2 ? (double)w2[q] : 0.0) + (w3 ? (double)w3[q] : 0.0);
+    out[q] = f32_to_f64(w1[q]) + (w2 ? f32_to_f64(w2[q]) : 0.0) + (w3 ? f32_to_f64(w3[q]) : 0.0);
 }
 
 // dense right-hand side: F~ (f inside Omega, 0 outside) on the N^3 work grid
@@ -594,13 +595,16 @@ __global__ void grid_to_work3_kernel(int N, const double* __restrict__ G, T* W) 
   }
 }
 
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f32_to_f64(x); }   // exact, integer ops
+
 template <typename T>
 __global__ void work_to_grid3_kernel(int N, const T* __restrict__ W, const uint8_t* __restrict__ mask,
                                      double* G) {
   const long n = (long)(N + 1) * (N + 1) * (N + 1);
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n; g += (long)gridDim.x * blockDim.x) {
     const int i = (int)(g % (N + 1)), j = (int)((g / (N + 1)) % (N + 1)), k = (int)(g / ((long)(N + 1) * (N + 1)));
-    double v = (i < N && j < N && k < N) ? (double)W[widx3(N, i, j, k)] : 0.0;
+    double v = (i < N && j < N && k < N) ? to_f64(W[widx3(N, i, j, k)]) : 0.0;
     if (mask && !mask[g]) v = 0.0;
     G[g] = v;
   }
