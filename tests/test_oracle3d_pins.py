@@ -22,6 +22,8 @@ P4s  the double-layer apply (reading S10 included) converges at second order to 
 S10  spectrum of the assembled discrete K_D on a sphere: the continuous operator 1/2 I + W
      has its spectrum in (1/2, 1] accumulating only at 1/2 (W compact), so every
      eigenvalue must have real part in [0.4, 1.05] and most must lie near 1/2;
+P13  the shape-operator unpacking (its quadratic form) and the tangent frame
+     (orthonormal, right-handed);
 plus planted mistakes that these pins must catch, and the geometry errors."""
 import numpy as np
 import pytest
@@ -337,3 +339,40 @@ def test_planted_s10_slips_fail_the_spectrum_pin(variant):
     point values into the jumps (spurious eigenvalues near 0) fails the spectral pin."""
     ok, stats = _spectrum_pin(_sphere_spectrum(variant))
     assert not ok, stats
+
+
+# ------------------------------------------------------------------------------ P13
+def test_p13_unpack_shape_gives_the_packed_quadratic_form():
+    """Packed shape operators (Sxx, Syy, Szz, Sxy, Sxz, Syz) unpack to the symmetric
+    matrix whose quadratic form is Sxx x^2 + Syy y^2 + Szz z^2 + 2 (Sxy xy + Sxz xz + Syz yz)."""
+    rng = np.random.default_rng(12)
+    p = rng.standard_normal((40, 6))
+    S = O3.unpack_shape(p)
+    assert np.array_equal(S, np.transpose(S, (0, 2, 1)))
+    x = rng.standard_normal((40, 3))
+    q = np.einsum("pi,pij,pj->p", x, S, x)
+    qf = (p[:, 0] * x[:, 0] ** 2 + p[:, 1] * x[:, 1] ** 2 + p[:, 2] * x[:, 2] ** 2
+          + 2 * (p[:, 3] * x[:, 0] * x[:, 1] + p[:, 4] * x[:, 0] * x[:, 2] + p[:, 5] * x[:, 1] * x[:, 2]))
+    assert np.max(np.abs(q - qf)) <= 1e-12 * np.max(np.abs(qf))
+    # the shape operator of a sphere of radius R, (I - n n^T) / R, maps n to 0
+    n = rng.standard_normal((40, 3))
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    A = (np.eye(3)[None] - n[:, :, None] * n[:, None, :]) / 0.7
+    packed = np.stack([A[:, 0, 0], A[:, 1, 1], A[:, 2, 2], A[:, 0, 1], A[:, 0, 2], A[:, 1, 2]], axis=1)
+    assert np.max(np.abs(np.einsum("pij,pj->pi", O3.unpack_shape(packed), n))) <= 1e-14
+
+
+def test_p13_tangent_frame_is_a_right_handed_orthonormal_frame():
+    """(t1, t2, n) is orthonormal and right-handed (t1 x t2 = n) for unit normals,
+    including the axis directions and normals with equal components, and t1 is
+    orthogonal to the axis least aligned with n."""
+    rng = np.random.default_rng(5)
+    n = np.concatenate([rng.standard_normal((200, 3)), np.eye(3), -np.eye(3),
+                        np.array([[1.0, 1.0, 1.0], [1.0, -1.0, 0.0], [0.0, 1e-9, -1.0]])])
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    t1, t2 = O3.tangent_frame(n)
+    F = np.stack([t1, t2, n], axis=1)                                # rows t1, t2, n
+    assert np.max(np.abs(F @ np.transpose(F, (0, 2, 1)) - np.eye(3)[None])) <= 1e-14
+    assert np.max(np.abs(np.cross(t1, t2) - n)) <= 1e-14
+    e = np.argmin(np.abs(n), axis=1)
+    assert np.max(np.abs(t1[np.arange(len(n)), e])) <= 1e-15

@@ -6,7 +6,8 @@ double-layer potential on a circle, second order; P5 manufactured BVPs, second o
 P6 GMRES vs a dense solve of the assembled K_D; P7 Richardson (gamma in (0,1], Sec. 2.1)
 reaches the same density; P8 90-degree grid symmetry; P9 jump formulas vs an analytic
 jump field; P10 the corrected 5-point scheme is exact for piecewise quadratics with a
-quadratic jump; P11 corrected interpolation reproduces piecewise quadratics.
+quadratic jump; P11 corrected interpolation reproduces piecewise quadratics; P13 the Lagrange basis and
+the sine matrix on their own (nodal, polynomial reproduction; DST-I orthogonality).
 The paper prints no intermediate values for a worked example, so no pin compares
 against printed numbers (there are none).
 """
@@ -468,3 +469,36 @@ def test_planted_normal_sign_breaks_the_single_layer_pin(monkeypatch):
     monkeypatch.setattr(K, "interpolate_plus_grad", lambda g, v, j: (lambda r: (r[0], -r[1]))(orig(g, v, j)))
     bad = np.max(np.abs(K.apply_single_layer_dn(geom_of(iface, N, kappa), np.cos(k * th)) - dn_ex))
     assert bad > 50 * good
+
+
+# ------------------------------------------------------------------ P13 helpers
+def test_p13_lagrange_basis_reproduces_quintics_and_their_derivatives():
+    """The six basis polynomials of the degree-5 interpolant (R3) on the local nodes
+    tau = -2..3: nodal (L_r(tau_s) = delta_rs), and any polynomial of degree <= 5 is
+    reproduced with its first and second tau-derivatives from its node values."""
+    nodes = np.arange(-2.0, 4.0)
+    L0, _, _ = O.lagrange_basis(nodes)
+    assert np.max(np.abs(L0 - np.eye(6))) <= 1e-13
+    p = lambda t: 3 * t**5 - 2 * t**4 + t**3 - 5 * t + 0.25
+    dp = lambda t: 15 * t**4 - 8 * t**3 + 3 * t**2 - 5
+    d2p = lambda t: 60 * t**3 - 24 * t**2 + 6 * t
+    tau = np.linspace(0.0, 1.0, 17)
+    L0, L1, L2 = O.lagrange_basis(tau)
+    pv = p(nodes)
+    assert np.max(np.abs(L0 @ pv - p(tau))) <= 1e-11
+    assert np.max(np.abs(L1 @ pv - dp(tau))) <= 1e-10
+    assert np.max(np.abs(L2 @ pv - d2p(tau))) <= 1e-9
+    # a degree-6 term is not reproduced (the interpolant really is of degree 5)
+    assert np.max(np.abs(L0 @ nodes**6 - tau**6)) > 1e-3
+
+
+@pytest.mark.parametrize("N", [2, 3, 8, 12, 17])
+def test_p13_sine_matrix_is_the_orthogonal_dst1(N):
+    """DST-I: S[j-1, l-1] = sin(pi j l / N) is symmetric with S S = (N / 2) I, and its
+    first row is sin(pi l / N)."""
+    from oracle.kfbi2d import sine_matrix
+    S = sine_matrix(N)
+    assert S.shape == (N - 1, N - 1)
+    assert np.array_equal(S, S.T)
+    assert np.max(np.abs(S @ S - 0.5 * N * np.eye(N - 1))) <= 1e-13 * N
+    assert np.max(np.abs(S[0] - np.sin(np.pi * np.arange(1, N) / N))) <= 1e-15
