@@ -57,8 +57,9 @@ typedef enum {
 typedef enum {
   KFBI_FP64 = 0,         /* every stage in FP64                                          */
   KFBI_MIXED_FP32 = 1,   /* box solve in FP32 (apply; in 2-D the well-conditioned x-modes
-                            are solved along y by tridiagonal elimination, the others by
-                            the sine-transform pair, see kfbi_ctx_info.tri_first_mode);
+                            have their tridiagonal y-systems solved directly (recursive
+                            filters or elimination), the others take the sine-transform
+                            pair, see kfbi_ctx_info.tri_first_mode);
                             as a solver mode: FP64 Arnoldi and Givens with relaxed-
                             precision matvecs and FP64-accurate residuals (see
                             kfbi_solve_bvp)                                              */
@@ -132,9 +133,12 @@ typedef struct {
                             pair for the lower ones) */
   int dim;               /* 2 or 3                                                        */
   int n_crossings_z;     /* 3-D: points on z-lines; 0 in 2-D                              */
-  int tri_first_mode;    /* 2-D FP32 box solves: x-modes k >= this are solved along y by
-                            tridiagonal elimination (the lower ones by the sine-transform
-                            pair); N when every mode takes the transform pair           */
+  int tri_first_mode;    /* 2-D FP32 box solves: x-modes k >= this have their tridiagonal
+                            y-systems solved directly, by the recursive filters of the
+                            row-layout pass (dst_variant[1] = 8; elimination coefficient
+                            c <= 0.9) or by chunked elimination (c <= 0.825), the lower
+                            ones by the sine-transform pair; a multiple of 32; N when every
+                            mode takes the transform pair                               */
 } kfbi_ctx_info;
 
 /* Fills *opt with dim 2, N 128, box [-1,1], kappa 0, FP64, m 50, 20 restarts,
@@ -303,7 +307,8 @@ kfbi_status kfbi_set_solver(kfbi_ctx ctx, int precision, int gmres_m, int max_re
    10 tile transposes of the work grid, 11 the sparse first x-transform of the plain FP32
    2-D apply (evaluated from the irregular nodes straight into the transposed layout),
    12 the tensor-core GEMMs of the dense box solve (KFBI_TF32X3), 13 the tridiagonal
-   y-solves of the well-conditioned x-modes in the FP32 2-D box solve.  Launch counts are always
+   y-solves of the well-conditioned x-modes in the FP32 2-D box solve (with the row-layout
+   pass: the whole y-pass, its two streams timed as one span).  Launch counts are always
    kept; times only while profiling is on (enabling clears both). */
 #define KFBI_NSTAGES 16
 typedef struct {

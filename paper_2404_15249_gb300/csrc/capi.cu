@@ -407,7 +407,9 @@ kfbi_status kfbi_get_info(kfbi_ctx ctx, kfbi_ctx_info* info) {
   info->n_crossings_x = c.dim == 2 ? c.ncross[0] : c.npts_axis[0];
   info->n_crossings_y = c.dim == 2 ? c.ncross[1] : c.npts_axis[1];
   info->n_crossings_z = c.dim == 2 ? 0 : c.npts_axis[2];
-  info->tri_first_mode = c.dim == 2 ? c.tri_k0 : c.N;
+  // the split of the y-pass variant in use: the row-layout filters (variant bit 8) start
+  // at c <= 0.9, the transposed elimination at c <= 0.825
+  info->tri_first_mode = c.dim != 2 ? c.N : (c.cols_variant[0] & 8) ? c.ypass_k0 : c.tri_k0;
   info->n_irregular = c.nirr;
   info->n_inside = c.n_inside;
   info->device_bytes = c.bytes + (int64_t)sizeof(double) * ((int64_t)(c.gm_m + 1) * c.M);

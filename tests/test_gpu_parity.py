@@ -242,8 +242,9 @@ def test_largest_grid_box_solve_manufactured(N):
 
 @pytest.mark.parametrize("kappa", [0.0, 10.0])
 def test_fp32_box_solve_with_and_without_the_tridiagonal_pass(kappa):
-    """FP32 box solves with the well-conditioned x-modes solved along y by tridiagonal
-    elimination (the default) and with every mode on the sine-transform pair
+    """FP32 box solves with the well-conditioned x-modes' tridiagonal y-systems solved
+    directly (the default: the autotuned variant's recursive filters or elimination, from
+    the reported tri_first_mode) and with every mode on the sine-transform pair
     (KFBI_TRI=0 at setup): both within 2e-5 of the oracle."""
     import os
     N = 256
