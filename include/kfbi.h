@@ -2,10 +2,11 @@
  * kfbi.h - C ABI of the GB300 (sm_103a) kernel-free boundary integral (KFBI) library.
  *
  * The library evaluates the double-layer boundary operator K_D = 1/2 I + W of the
- * modified Helmholtz / Poisson equation  Lap u - kappa^2 u = f  on a 2-D domain Omega
- * embedded in the box B = [lo, hi]^2, WITHOUT a Green's function: the potential is the
- * solution of the equivalent interface problem on a Cartesian grid of B (paper Sec. 2.2,
- * "Indirect evaluation of integrals"; table of F and Phi there):
+ * modified Helmholtz / Poisson equation  Lap u - kappa^2 u = f  on a 2-D (or 3-D, see
+ * kfbi_setup) domain Omega embedded in the box B = [lo, hi]^dim, WITHOUT a Green's
+ * function: the potential is the solution of the equivalent interface problem on a
+ * Cartesian grid of B (paper Sec. 2.2, "Indirect evaluation of integrals"; table of F and
+ * Phi there):
  *     Lap v - kappa^2 v = F in B \ Gamma,  [v] = Phi,  [d_n v] = psi on Gamma,  v = 0 on dB,
  * discretised by Alg. 1: jumps at grid-line/interface crossings, Taylor correction of the
  * right-hand side at irregular nodes (Alg. 2), a fast sine-transform box solve (Alg. 4),
@@ -18,10 +19,12 @@
  *     PyTorch); the library never frees them and never keeps them after the call returns.
  *     Pointers named h_* are host pointers.  All arrays are contiguous, C order, FP64.
  *   - Grid arrays are (N+1) x (N+1) with x fastest: a[j*(N+1) + i] = value at
- *     (lo + i h, lo + j h), h = (hi - lo)/N.
- *   - Interface arrays have M entries (points/normals: M x 2, interleaved x,y).  Points
- *     are counter-clockwise samples of Gamma at equispaced parameter t_k = 2 pi k / M;
- *     normals are outward unit normals; curv is the signed curvature (> 0 where convex).
+ *     (lo + i h, lo + j h), h = (hi - lo)/N; in 3-D (N+1)^3 with x fastest, then y:
+ *     a[(k*(N+1) + j)*(N+1) + i] at (lo + i h, lo + j h, lo + k h).
+ *   - Interface arrays have M entries (points/normals: M x 2, interleaved x,y; 3-D as
+ *     described at kfbi_setup).  2-D points are counter-clockwise samples of Gamma at
+ *     equispaced parameter t_k = 2 pi k / M; normals are outward unit normals; curv is
+ *     the signed curvature (> 0 where convex).
  *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed as void*,
  *     NULL = legacy default stream) unless documented as synchronising.
  *   - All workspace is allocated by kfbi_setup; apply and solve calls allocate nothing.
@@ -162,8 +165,8 @@ void kfbi_default_options(kfbi_options* opt);
    than 10) and the 10-node interpolation stencils are built on the GPU in FP64.  The
    3-D double-layer apply uses the least-squares value of the density in the jumps and
    adds half the difference to the point value (the second-kind identity part acts on
-   the point values); grids are (N+1)^3 with x fastest.  3-D supports the double layer
-   and the volume potential in every precision (the refinement residual uses the
+   the point values); grids are (N+1)^3 with x fastest.  3-D supports the double and
+   single layers and the volume potential in every precision (the refinement residual uses the
    7-point operator).
    2-D setup times the transform variants on the context's grids and keeps the fastest
    (kfbi_ctx_info.dst_variant); the environment variable KFBI_DST_VARIANTS="r32,c32,r64,c64"
