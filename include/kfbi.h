@@ -307,8 +307,9 @@ kfbi_status kfbi_set_solver(kfbi_ctx ctx, int precision, int gmres_m, int max_re
    3 DST columns FP32 (the y-transform pair with the spectral division; in 3-D the
    z-transform pair), 4 DST rows FP64, 5 DST columns FP64, 6 interpolation, 7 dense grid
    build/copy, 8 Krylov vector kernels, 9 residual refinement of FP32 box solves,
-   10 tile transposes of the work grid, 11 the sparse first x-transform of the plain FP32
-   2-D apply (evaluated from the irregular nodes straight into the transposed layout),
+   10 tile transposes of the work grid, 11 the sparse first x-transform of the FP32 2-D
+   applies (evaluated from the irregular nodes straight into the row layout; the last
+   x-transform evaluated at the stencil nodes only is counted in stage 2),
    12 the tensor-core GEMMs of the dense box solve (KFBI_TF32X3), 13 the tridiagonal
    y-solves of the well-conditioned x-modes in the FP32 2-D box solve (with the row-layout
    pass: the whole y-pass, its two streams timed as one span).  Launch counts are always
