@@ -1,7 +1,7 @@
 """The ctypes binding against the C ABI header (no GPU, no library needed): every struct the
 binding declares has the header's fields in the header's order, at the offsets and sizes a
-C compiler gives them, and the binding's constants equal the header's enum values and
-macros.  A field added to one side only, or a changed type, would otherwise make the
+C compiler gives them; the binding's constants equal the header's enum values and macros;
+and every prototype has the binding's argument and return kinds.  A field added to one side only, or a changed type, would otherwise make the
 library write past the binding's buffer or the binding read the wrong field."""
 import ctypes
 import os
@@ -97,3 +97,65 @@ def test_binding_constants_equal_the_header(c_layout):
     for n, v in consts.items():
         assert c_layout["C"][n] == v, n
     assert c_layout["C"]["NSTAGES"] == K.NSTAGES
+
+
+_STRUCT_OF = {"kfbi_options": "Options", "kfbi_solve_info": "SolveInfo",
+              "kfbi_ctx_info": "CtxInfo", "kfbi_stage_times": "StageTimes"}
+_HANDLES = ("kfbi_ctx", "kfbi_batch")
+
+
+def c_class(decl):
+    """Kind of one C parameter or return type: int, double, int64, ptr, ptr:<Struct>,
+    ptrptr (a handle out-pointer or an array of pointers), cstr, or None for void."""
+    toks = [t for t in re.findall(r"[A-Za-z_]\w*|\*", decl) if t != "const"]
+    stars = toks.count("*")
+    ids = [t for t in toks if t != "*"]
+    if len(ids) > 1:
+        ids = ids[:-1]                                 # drop the parameter name
+    base = " ".join(ids)
+    if base == "void" and stars == 0:
+        return None
+    if base == "char" and stars == 1:
+        return "cstr"
+    if stars == 0:
+        if base in _HANDLES:
+            return "ptr"
+        return {"int": "int", "kfbi_status": "int", "double": "double", "int64_t": "int64"}[base]
+    if stars == 1 and base in _STRUCT_OF:
+        return "ptr:" + _STRUCT_OF[base]
+    if stars >= 2 or base in _HANDLES:
+        return "ptrptr"
+    return "ptr"
+
+
+def py_class(t):
+    if t is None:
+        return None
+    if t is ctypes.c_char_p:
+        return "cstr"
+    if t is ctypes.c_void_p:
+        return "ptr"
+    if t is ctypes.c_int:
+        return "int"
+    if t is ctypes.c_double:
+        return "double"
+    if t is ctypes.c_int64:
+        return "int64"
+    target = getattr(t, "_type_", None)
+    if target is ctypes.c_void_p:
+        return "ptrptr"
+    if isinstance(target, type) and issubclass(target, ctypes.Structure):
+        return "ptr:" + target.__name__
+    return "ptr"
+
+
+def test_function_signatures_match_the_header_prototypes():
+    text = re.sub(r"/\*.*?\*/", "", header_text(), flags=re.S)
+    protos = {m.group(2): (m.group(1), m.group(3)) for m in
+              re.finditer(r"([A-Za-z_][\w\s\*]*?)\s*\b(kfbi_\w+)\s*\(([^)]*)\)\s*;", text)}
+    assert set(protos) == set(K._SIGS), set(protos) ^ set(K._SIGS)
+    for name, (ret, args) in protos.items():
+        res, argtypes = K._SIGS[name]
+        assert c_class(ret) == py_class(res), (name, ret, res)
+        cargs = [] if args.strip() == "void" else [c_class(a) for a in args.split(",")]
+        assert cargs == [py_class(a) for a in argtypes], (name, cargs)
