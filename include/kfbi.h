@@ -283,7 +283,8 @@ kfbi_status kfbi_apply_volume_dn(kfbi_ctx ctx, int precision, const double* d_f_
    kfbi_solve_bvp solves K_D phi = g_hat (same solver options, FP64 or relaxed mixed
    precision), then u is the inside-node solution of the interface problem with
    [d_n v] = psi and F = zero-extended f.  kappa must be positive (for kappa = 0 the
-   interior Neumann problem fixes u only up to a constant and K_N is singular).
+   interior Neumann problem fixes u only up to a constant and K_N is singular):
+   KFBI_ERR_ARG otherwise, before any device work.
    d_gn_ctrl: g_N at the M control points (outward normal derivative); d_density_out: psi
    (M) or NULL; other arguments as kfbi_solve_bvp.  2-D only.  Synchronising. */
 kfbi_status kfbi_solve_neumann_bvp(kfbi_ctx ctx, const double* d_f_grid, const double* d_f_ctrl,

@@ -49,13 +49,13 @@ kfbi_status alloc_bytes(Ctx& c, void** p, size_t bytes) {
     set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
     return KFBI_ERR_NOMEM;
   }
+  c.allocs.push_back(*p);                    // recorded first: freed with the context on any error
+  c.bytes += (int64_t)bytes;
   e = cudaMemsetAsync(*p, 0, bytes, c.stream);
   if (e != cudaSuccess) {
     set_error("cudaMemsetAsync failed: %s", cudaGetErrorString(e));
     return KFBI_ERR_CUDA;
   }
-  c.allocs.push_back(*p);
-  c.bytes += (int64_t)bytes;
   return KFBI_OK;
 }
 
@@ -147,7 +147,10 @@ kfbi_status kfbi_setup(const kfbi_options* opt, int64_t M, const double* d_pts,
     return KFBI_ERR_ARG;
   }
   kfbi_ctx_s* hd = new (std::nothrow) kfbi_ctx_s();
-  if (!hd) return KFBI_ERR_NOMEM;
+  if (!hd) {
+    kfbi::set_error("kfbi_setup: host allocation of the context failed");
+    return KFBI_ERR_NOMEM;
+  }
   Ctx& c = hd->c;
   c.opt = *opt;
   c.N = opt->N;
@@ -354,6 +357,10 @@ kfbi_status kfbi_solve_neumann_bvp(kfbi_ctx ctx, const double* d_f_grid, const d
     kfbi::set_error("kfbi_solve_neumann_bvp: 2-D only");
     return KFBI_ERR_UNSUPPORTED;
   }
+  if (!(c->kappa > 0.0)) {              // kappa = 0: u fixed only up to a constant, K_N singular
+    kfbi::set_error("kfbi_solve_neumann_bvp: kappa must be positive");
+    return KFBI_ERR_ARG;
+  }
   return kfbi::solve_bvp(*c, d_f_grid, d_f_ctrl, d_gn_ctrl, d_u_grid, d_density_out, h_info,
                          kfbi::kOpNeumann);
 }
@@ -394,12 +401,18 @@ kfbi_status kfbi_apply_volume_dn(kfbi_ctx ctx, int precision, const double* d_f_
 
 kfbi_status kfbi_get_inside_mask(kfbi_ctx ctx, uint8_t* d_mask, void* stream) {
   Ctx* c = ctx_of(ctx, (cudaStream_t)stream);
-  if (!c || !d_mask) return KFBI_ERR_ARG;
+  if (!c || !d_mask) {
+    kfbi::set_error("kfbi_get_inside_mask: null argument");
+    return KFBI_ERR_ARG;
+  }
   return kfbi::inside_mask(*c, d_mask);
 }
 
 kfbi_status kfbi_get_info(kfbi_ctx ctx, kfbi_ctx_info* info) {
-  if (!ctx || !info) return KFBI_ERR_ARG;
+  if (!ctx || !info) {
+    kfbi::set_error("kfbi_get_info: null argument");
+    return KFBI_ERR_ARG;
+  }
   const Ctx& c = ctx->c;
   info->N = c.N;
   info->M = c.M;
@@ -438,7 +451,10 @@ kfbi_status kfbi_set_solver(kfbi_ctx ctx, int precision, int gmres_m, int max_re
 }
 
 kfbi_status kfbi_destroy(kfbi_ctx ctx) {
-  if (!ctx) return KFBI_ERR_ARG;
+  if (!ctx) {
+    kfbi::set_error("kfbi_destroy: null context");
+    return KFBI_ERR_ARG;
+  }
   free_handle(ctx);
   return KFBI_OK;
 }
@@ -481,7 +497,10 @@ kfbi_status kfbi_batch_solve(kfbi_batch b, int nrhs, const double* const* d_f_gr
 }
 
 kfbi_status kfbi_batch_destroy(kfbi_batch b) {
-  if (!b) return KFBI_ERR_ARG;
+  if (!b) {
+    kfbi::set_error("kfbi_batch_destroy: null batch");
+    return KFBI_ERR_ARG;
+  }
   delete b;
   return KFBI_OK;
 }
@@ -544,7 +563,10 @@ void prof_end(Ctx& c, int pair) {
 extern "C" {
 
 kfbi_status kfbi_profile(kfbi_ctx ctx, int enable) {
-  if (!ctx) return KFBI_ERR_ARG;
+  if (!ctx) {
+    kfbi::set_error("kfbi_profile: null context");
+    return KFBI_ERR_ARG;
+  }
   kfbi::Ctx& c = ctx->c;
   kfbi::Prof& p = c.prof;
   if (enable) {
@@ -568,7 +590,10 @@ kfbi_status kfbi_profile(kfbi_ctx ctx, int enable) {
 }
 
 kfbi_status kfbi_profile_read(kfbi_ctx ctx, kfbi_stage_times* out) {
-  if (!ctx || !out) return KFBI_ERR_ARG;
+  if (!ctx || !out) {
+    kfbi::set_error("kfbi_profile_read: null argument");
+    return KFBI_ERR_ARG;
+  }
   kfbi::Ctx& c = ctx->c;
   kfbi::prof_flush(c);
   for (int s = 0; s < KFBI_NSTAGES; ++s) {

@@ -56,8 +56,20 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     assert lib.kfbi_setup(ctypes.byref(o), 64, dummy, dummy, dummy, None, ctypes.byref(h)) == 1
     assert not h.value
     assert lib.kfbi_apply_layer_potential(None, 0, 0, dummy, dummy, None) == 1
-    assert lib.kfbi_destroy(None) == 1
     assert lib.kfbi_batch_create(None, 0, ctypes.byref(h)) == 1
+    # null handles: KFBI_ERR_ARG with a message naming the entry point
+    info, times = K.CtxInfo(), K.StageTimes()
+    for name, call in (("kfbi_destroy", lambda: lib.kfbi_destroy(None)),
+                       ("kfbi_get_info", lambda: lib.kfbi_get_info(None, ctypes.byref(info))),
+                       ("kfbi_get_inside_mask", lambda: lib.kfbi_get_inside_mask(None, dummy, None)),
+                       ("kfbi_profile", lambda: lib.kfbi_profile(None, 1)),
+                       ("kfbi_profile_read", lambda: lib.kfbi_profile_read(None, ctypes.byref(times))),
+                       ("kfbi_batch_destroy", lambda: lib.kfbi_batch_destroy(None)),
+                       ("kfbi_solve_neumann_bvp",
+                        lambda: lib.kfbi_solve_neumann_bvp(None, dummy, dummy, dummy, dummy, None,
+                                                           None, None))):
+        assert call() == 1, name
+        assert lib.kfbi_last_error().decode().startswith(name), name
 
 
 def test_product_path_does_not_import_the_oracle():

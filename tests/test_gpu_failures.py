@@ -91,3 +91,17 @@ def test_expired_bounded_wait_is_reported_as_timeout(precision, monkeypatch):
     assert info2["converged"]
     assert float((phi2 - phi_ref).abs().max()) <= 1e-8 * scale
     ok.close()
+
+
+def test_neumann_solve_with_kappa_zero_is_refused():
+    """kappa = 0: the interior Neumann problem fixes u only up to a constant (K_N is
+    singular), so the solve is refused with KFBI_ERR_ARG before any device work and the
+    context stays usable."""
+    ctx, prob = _ctx(0)
+    with pytest.raises(K.KfbiError) as e:
+        ctx.solve_neumann_bvp(prob.f_grid(), prob.f_ctrl(), prob.gn_ctrl())
+    assert e.value.status == 1                           # KFBI_ERR_ARG
+    assert "kappa" in str(e.value)
+    u, phi, info = ctx.solve_bvp(prob.f_grid(), prob.f_ctrl(), prob.g_ctrl())
+    assert info["converged"]
+    ctx.close()
