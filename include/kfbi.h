@@ -349,8 +349,9 @@ kfbi_status kfbi_measure_fma_peak(int fp64, double* h_tflops, void* stream);
    problems run concurrently on the device (the environment variable KFBI_BATCH_WORKERS,
    1..64, sets another count; on one GB300, with the Arnoldi steps as CUDA graphs, 16 were
    fastest for the 256-problem workload: 729 ms against 798 ms with 8 and 778 ms with 32).
-   Each context is used by one worker at a time.  The contexts stay owned by the caller
-   and must outlive the batch. */
+   Each context is used by one worker at a time: kfbi_batch_create refuses a context
+   listed twice (KFBI_ERR_ARG).  The contexts stay owned by the caller and must outlive
+   the batch. */
 typedef struct kfbi_batch_s* kfbi_batch;
 
 kfbi_status kfbi_batch_create(const kfbi_ctx* ctxs, int count, kfbi_batch* out);

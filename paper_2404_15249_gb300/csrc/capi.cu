@@ -1,4 +1,5 @@
 // extern "C" entry points of libkfbi (declared and documented in include/kfbi.h).
+#include <algorithm>
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
@@ -471,7 +472,10 @@ kfbi_status kfbi_batch_create(const kfbi_ctx* ctxs, int count, kfbi_batch* out) 
     return KFBI_ERR_ARG;
   }
   kfbi_batch_s* b = new (std::nothrow) kfbi_batch_s();
-  if (!b) return KFBI_ERR_NOMEM;
+  if (!b) {
+    kfbi::set_error("kfbi_batch_create: host allocation failed");
+    return KFBI_ERR_NOMEM;
+  }
   for (int i = 0; i < count; ++i) {
     if (!ctxs[i]) {
       delete b;
@@ -479,6 +483,15 @@ kfbi_status kfbi_batch_create(const kfbi_ctx* ctxs, int count, kfbi_batch* out) 
       return KFBI_ERR_ARG;
     }
     b->ctxs.push_back(ctxs[i]);
+  }
+  // a context listed twice would be driven by two workers at once (one workspace, one
+  // stream): refused
+  std::vector<kfbi_ctx> sorted(b->ctxs);
+  std::sort(sorted.begin(), sorted.end());
+  if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
+    delete b;
+    kfbi::set_error("kfbi_batch_create: a context is listed more than once");
+    return KFBI_ERR_ARG;
   }
   *out = b;
   return KFBI_OK;

@@ -57,6 +57,12 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     assert not h.value
     assert lib.kfbi_apply_layer_potential(None, 0, 0, dummy, dummy, None) == 1
     assert lib.kfbi_batch_create(None, 0, ctypes.byref(h)) == 1
+    # batches hold handles without touching them: stand-in handles test the list checks
+    fake = (ctypes.c_void_p * 3)(64, 128, 64)
+    assert lib.kfbi_batch_create(fake, 3, ctypes.byref(h)) == 1 and not h.value
+    assert b"more than once" in lib.kfbi_last_error()
+    assert lib.kfbi_batch_create(fake, 2, ctypes.byref(h)) == 0 and h.value
+    assert lib.kfbi_batch_destroy(h) == 0
     # null handles: KFBI_ERR_ARG with a message naming the entry point
     info, times = K.CtxInfo(), K.StageTimes()
     for name, call in (("kfbi_destroy", lambda: lib.kfbi_destroy(None)),
