@@ -193,12 +193,12 @@ class Kfbi2D:
     def _new(self, n):
         return self.torch.empty(n, dtype=self.torch.float64, device=self.dev)
 
-    def _out(self, out, numel):
-        """A caller-supplied output buffer: contiguous float64 on this context's device."""
+    def _out(self, out, numel, what="out"):
+        """A caller-supplied buffer: contiguous float64 on this context's device."""
         t = self.torch
         if not (isinstance(out, t.Tensor) and out.dtype == t.float64 and out.is_contiguous()
                 and out.device == t.device(self.dev) and out.numel() == numel):
-            raise ValueError(f"out must be a contiguous float64 tensor of {numel} elements "
+            raise ValueError(f"{what} must be a contiguous float64 tensor of {numel} elements "
                              f"on {self.dev}")
         return out
 
@@ -360,8 +360,22 @@ def box_solve_static_check(stream=None):
 def batch_solve(ctxs, f_grids, f_ctrls, g_ctrls, u_grids, nrhs, stream=None, dens_out=None):
     """kfbi_batch_create / kfbi_batch_solve / kfbi_batch_destroy over Kfbi2D contexts.
     The per-(problem, rhs) lists hold device tensors, problem-major; dens_out (optional)
-    is a list of the same length of float64 tensors of M_p values for the densities."""
+    is a list of the same length of float64 tensors of M_p values for the densities.  The
+    lists are checked (length, dtype, layout, device, size per problem) before the call: the
+    library reads one pointer per (problem, rhs) from each."""
     n = len(ctxs)
+    lists = {"f_grids": f_grids, "f_ctrls": f_ctrls, "g_ctrls": g_ctrls, "u_grids": u_grids}
+    if dens_out is not None:
+        lists["dens_out"] = dens_out
+    for name, ts in lists.items():
+        if len(ts) != n * nrhs:
+            raise ValueError(f"{name} must hold {n * nrhs} tensors (problem-major), got {len(ts)}")
+    for p, c in enumerate(ctxs):
+        size = {"f_grids": (c.N + 1) ** c.dim, "u_grids": (c.N + 1) ** c.dim,
+                "f_ctrls": c.M, "g_ctrls": c.M, "dens_out": c.M}
+        for r in range(nrhs):
+            for name, ts in lists.items():
+                c._out(ts[p * nrhs + r], size[name], f"{name}[{p * nrhs + r}]")
     arr = (ctypes.c_void_p * n)(*[c.handle.value for c in ctxs])
     b = ctypes.c_void_p()
     _check(lib().kfbi_batch_create(arr, n, ctypes.byref(b)), "kfbi_batch_create")

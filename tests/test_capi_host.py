@@ -99,3 +99,33 @@ def test_binding_constants_match_the_header():
     assert {"KFBI_FP64", "KFBI_MIXED_FP32", "KFBI_TF32X3", "KFBI_DOUBLE_LAYER"} <= set(bound)
     for k, v in bound.items():
         assert declared[k] == v, k
+
+
+def test_batch_solve_checks_its_tensor_lists_before_the_library():
+    """The binding's batch_solve refuses lists of the wrong length, dtype or size before any
+    library call (the library reads one pointer per (problem, rhs) from each list)."""
+    import types
+    import torch
+
+    class Stand:
+        dim, dev = 2, "cpu"
+
+        def __init__(self, N, M):
+            self.N, self.M, self.torch = N, M, torch
+            self._out = types.MethodType(K.Kfbi2D._out, self)
+
+    ctxs = [Stand(32, 64), Stand(64, 128)]
+    g = lambda c: torch.zeros((c.N + 1) ** 2, dtype=torch.float64)
+    v = lambda c: torch.zeros(c.M, dtype=torch.float64)
+    fg = [g(c) for c in ctxs for _ in range(2)]
+    fc = [v(c) for c in ctxs for _ in range(2)]
+    with pytest.raises(ValueError, match="g_ctrls must hold 4"):
+        K.batch_solve(ctxs, fg, fc, fc[:3], fg, 2)
+    bad = list(fc)
+    bad[3] = torch.zeros(64, dtype=torch.float64)            # problem 1 has M = 128
+    with pytest.raises(ValueError, match=r"g_ctrls\[3\]"):
+        K.batch_solve(ctxs, fg, fc, bad, fg, 2)
+    bad = list(fg)
+    bad[0] = bad[0].float()
+    with pytest.raises(ValueError, match=r"u_grids\[0\]"):
+        K.batch_solve(ctxs, fg, fc, fc, bad, 2)
