@@ -183,8 +183,13 @@ class Kfbi2D:
         self.handle = h
 
     # ------------------------------------------------------------------ helpers
-    def _vec(self, a):
-        return self.torch.as_tensor(a, dtype=self.torch.float64).contiguous().to(self.dev)
+    def _vec(self, a, numel, what):
+        """An input as a contiguous float64 tensor on this context's device, of numel values
+        (the library reads exactly that many)."""
+        v = self.torch.as_tensor(a, dtype=self.torch.float64).contiguous().to(self.dev)
+        if v.numel() != numel:
+            raise ValueError(f"{what} must have {numel} values, got {v.numel()}")
+        return v
 
     def _grid(self, dtype=None):
         return self.torch.empty((self.N + 1,) * self.dim, dtype=dtype or self.torch.float64,
@@ -204,7 +209,7 @@ class Kfbi2D:
 
     # ------------------------------------------------------------------ API
     def apply_layer_potential(self, density, layer=KFBI_DOUBLE_LAYER, precision=KFBI_FP64, out=None):
-        d = self._vec(density)
+        d = self._vec(density, self.M, "density")
         out = self._new(self.M) if out is None else self._out(out, self.M)
         _check(lib().kfbi_apply_layer_potential(self.handle, int(layer), int(precision), _ptr(d),
                                                 _ptr(out), _stream_ptr(self.stream)),
@@ -214,7 +219,7 @@ class Kfbi2D:
     def apply_layer_potential_dn(self, density, layer=KFBI_SINGLE_LAYER, precision=KFBI_FP64,
                                  out=None):
         """kfbi_apply_layer_potential_dn: d_n v^+ at the control points (2-D)."""
-        d = self._vec(density)
+        d = self._vec(density, self.M, "density")
         out = self._new(self.M) if out is None else self._out(out, self.M)
         _check(lib().kfbi_apply_layer_potential_dn(self.handle, int(layer), int(precision), _ptr(d),
                                                    _ptr(out), _stream_ptr(self.stream)),
@@ -223,7 +228,7 @@ class Kfbi2D:
 
     def apply_volume_dn(self, f_grid, f_ctrl, precision=KFBI_FP64):
         """kfbi_apply_volume_dn: d_n (Y f)^+ at the control points (2-D)."""
-        fg, fc = self._vec(f_grid), self._vec(f_ctrl)
+        fg, fc = self._vec(f_grid, (self.N + 1) ** self.dim, "f_grid"), self._vec(f_ctrl, self.M, "f_ctrl")
         out = self._new(self.M)
         _check(lib().kfbi_apply_volume_dn(self.handle, int(precision), _ptr(fg), _ptr(fc),
                                           _ptr(out), _stream_ptr(self.stream)), "kfbi_apply_volume_dn")
@@ -232,9 +237,10 @@ class Kfbi2D:
     def solve_neumann_bvp(self, f_grid, f_ctrl, gn_ctrl, u_out=None, dens_out=None,
                           allow_not_converged=False):
         """kfbi_solve_neumann_bvp: (u grid, single-layer density psi, info) (2-D)."""
-        fg, fc, gc = self._vec(f_grid), self._vec(f_ctrl), self._vec(gn_ctrl)
-        u = self._grid() if u_out is None else u_out
-        psi = self._new(self.M) if dens_out is None else dens_out
+        fg, fc = self._vec(f_grid, (self.N + 1) ** self.dim, "f_grid"), self._vec(f_ctrl, self.M, "f_ctrl")
+        gc = self._vec(gn_ctrl, self.M, "gn_ctrl")
+        u = self._grid() if u_out is None else self._out(u_out, (self.N + 1) ** self.dim, "u_out")
+        psi = self._new(self.M) if dens_out is None else self._out(dens_out, self.M, "dens_out")
         info = SolveInfo()
         st = lib().kfbi_solve_neumann_bvp(self.handle, _ptr(fg), _ptr(fc), _ptr(gc), _ptr(u),
                                           _ptr(psi), ctypes.byref(info), _stream_ptr(self.stream))
@@ -243,16 +249,16 @@ class Kfbi2D:
         return u, psi, info.as_dict()
 
     def apply_volume(self, f_grid, f_ctrl, precision=KFBI_FP64):
-        fg, fc = self._vec(f_grid), self._vec(f_ctrl)
+        fg, fc = self._vec(f_grid, (self.N + 1) ** self.dim, "f_grid"), self._vec(f_ctrl, self.M, "f_ctrl")
         out = self._new(self.M)
         _check(lib().kfbi_apply_volume(self.handle, int(precision), _ptr(fg), _ptr(fc), _ptr(out),
                                        _stream_ptr(self.stream)), "kfbi_apply_volume")
         return out
 
     def interface_solve(self, density=None, f_grid=None, f_ctrl=None, precision=KFBI_FP64):
-        d = None if density is None else self._vec(density)
-        fg = None if f_grid is None else self._vec(f_grid)
-        fc = None if f_ctrl is None else self._vec(f_ctrl)
+        d = None if density is None else self._vec(density, self.M, "density")
+        fg = None if f_grid is None else self._vec(f_grid, (self.N + 1) ** self.dim, "f_grid")
+        fc = None if f_ctrl is None else self._vec(f_ctrl, self.M, "f_ctrl")
         rhs, v, out = self._grid(), self._grid(), self._new(self.M)
         _check(lib().kfbi_interface_solve(self.handle, int(precision), _ptr(d), _ptr(fg), _ptr(fc),
                                           _ptr(rhs), _ptr(v), _ptr(out), _stream_ptr(self.stream)),
@@ -260,7 +266,7 @@ class Kfbi2D:
         return rhs, v, out
 
     def box_solve(self, b_grid, precision=KFBI_FP64, out=None):
-        b = self._vec(b_grid)
+        b = self._vec(b_grid, (self.N + 1) ** self.dim, "b_grid")
         v = self._grid() if out is None else self._out(out, (self.N + 1) ** self.dim)
         _check(lib().kfbi_box_solve(self.handle, int(precision), _ptr(b), _ptr(v),
                                     _stream_ptr(self.stream)), "kfbi_box_solve")
@@ -271,9 +277,10 @@ class Kfbi2D:
                                      float(tol), float(inner_tol)), "kfbi_set_solver")
 
     def solve_bvp(self, f_grid, f_ctrl, g_ctrl, u_out=None, dens_out=None, allow_not_converged=False):
-        fg, fc, gc = self._vec(f_grid), self._vec(f_ctrl), self._vec(g_ctrl)
-        u = self._grid() if u_out is None else u_out
-        phi = self._new(self.M) if dens_out is None else dens_out
+        fg, fc = self._vec(f_grid, (self.N + 1) ** self.dim, "f_grid"), self._vec(f_ctrl, self.M, "f_ctrl")
+        gc = self._vec(g_ctrl, self.M, "g_ctrl")
+        u = self._grid() if u_out is None else self._out(u_out, (self.N + 1) ** self.dim, "u_out")
+        phi = self._new(self.M) if dens_out is None else self._out(dens_out, self.M, "dens_out")
         info = SolveInfo()
         st = lib().kfbi_solve_bvp(self.handle, _ptr(fg), _ptr(fc), _ptr(gc), _ptr(u), _ptr(phi),
                                   ctypes.byref(info), _stream_ptr(self.stream))
@@ -333,10 +340,17 @@ def box_solve_static(N, b_grid, kappa=0.0, lo=-1.0, hi=1.0, precision=KFBI_FP64,
     library's static device array (nothing allocated by the library).  b_grid and out
     are (N+1, N+1) float64 CUDA tensors (out is created here when None)."""
     import torch
-    if not (isinstance(b_grid, torch.Tensor) and b_grid.is_cuda and b_grid.dtype == torch.float64
-            and b_grid.is_contiguous()):
-        raise ValueError("b_grid must be a contiguous float64 CUDA tensor")
+
+    def grid_ok(t):
+        return (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                and t.is_contiguous() and t.numel() == (int(N) + 1) ** 2)
+
+    if not grid_ok(b_grid):
+        raise ValueError(f"b_grid must be a contiguous float64 CUDA tensor of (N+1)^2 = "
+                         f"{(int(N) + 1) ** 2} values")
     out = torch.empty_like(b_grid) if out is None else out
+    if not (grid_ok(out) and out.device == b_grid.device):
+        raise ValueError("out must be a contiguous float64 tensor of b_grid's size on its device")
     _check(lib().kfbi_box_solve_static(int(N), float(lo), float(hi), float(kappa), int(precision),
                                        _ptr(b_grid), _ptr(out), _stream_ptr(stream)),
            "kfbi_box_solve_static")

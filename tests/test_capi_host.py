@@ -129,3 +129,40 @@ def test_batch_solve_checks_its_tensor_lists_before_the_library():
     bad[0] = bad[0].float()
     with pytest.raises(ValueError, match=r"u_grids\[0\]"):
         K.batch_solve(ctxs, fg, fc, fc, bad, 2)
+
+
+def test_binding_checks_input_and_output_sizes_before_the_library():
+    """Each context method refuses an input or a caller-supplied output whose size is not
+    the one the library reads or writes (grid (N+1)^dim, M values at the points), before
+    any library call; stand-in contexts carry only the sizes."""
+    import types
+    import torch
+
+    class Stand:
+        dev = "cpu"
+
+        def __init__(self, N, M, dim):
+            self.N, self.M, self.dim, self.torch = N, M, dim, torch
+            for f in ("_vec", "_out", "_grid", "_new"):
+                setattr(self, f, types.MethodType(getattr(K.Kfbi2D, f), self))
+
+    z = lambda n: torch.zeros(n, dtype=torch.float64)
+    for N, M, dim in ((32, 64, 2), (16, 300, 3)):
+        c = Stand(N, M, dim)
+        G = (N + 1) ** dim
+        calls = {
+            "density": lambda: K.Kfbi2D.apply_layer_potential(c, z(M - 1)),
+            "f_grid": lambda: K.Kfbi2D.apply_volume(c, z(G + 1), z(M)),
+            "f_ctrl": lambda: K.Kfbi2D.solve_bvp(c, z(G), z(M + 1), z(M)),
+            "g_ctrl": lambda: K.Kfbi2D.solve_bvp(c, z(G), z(M), z(1)),
+            "u_out": lambda: K.Kfbi2D.solve_bvp(c, z(G), z(M), z(M), u_out=z(G - 1)),
+            "dens_out": lambda: K.Kfbi2D.solve_bvp(c, z(G), z(M), z(M), u_out=z(G),
+                                                   dens_out=z(M).float()),
+            "gn_ctrl": lambda: K.Kfbi2D.solve_neumann_bvp(c, z(G), z(M), z(2 * M)),
+            "b_grid": lambda: K.Kfbi2D.box_solve(c, z(N)),
+        }
+        for what, call in calls.items():
+            with pytest.raises(ValueError, match=what):
+                call()
+    with pytest.raises(ValueError, match="b_grid"):
+        K.box_solve_static(64, z(65 * 65))                  # a host tensor
