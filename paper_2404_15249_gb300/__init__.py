@@ -165,9 +165,17 @@ class Kfbi2D:
                  gmres_m=50, max_restarts=20, tol=1e-10, inner_tol=1e-5, stream=None):
         import torch
         self.torch = torch
+        # kfbi_setup copies M x dim points and normals and M x (1 or 6) curvature values
+        P, Nr, C = (torch.as_tensor(a, dtype=torch.float64) for a in (pts, normals, curv))
+        ncurv = 1 if self.dim == 2 else 6
+        if (P.dim() != 2 or P.shape[1] != self.dim or tuple(Nr.shape) != tuple(P.shape)
+                or C.numel() != P.shape[0] * ncurv):
+            raise ValueError(f"pts and normals must be (M, {self.dim}) and the curvature data "
+                             f"M x {ncurv} values; got {tuple(P.shape)}, {tuple(Nr.shape)}, "
+                             f"{tuple(C.shape)}")
         self.dev = torch.device("cuda", torch.cuda.current_device())
-        t = lambda a: torch.as_tensor(a, dtype=torch.float64).contiguous().to(self.dev)
-        self.pts, self.nrm, self.curv = t(pts), t(normals), t(curv)
+        t = lambda a: a.contiguous().to(self.dev)
+        self.pts, self.nrm, self.curv = t(P), t(Nr), t(C)
         self.M = int(self.pts.shape[0])
         self.N = int(N)
         self.stream = stream

@@ -166,3 +166,13 @@ def test_binding_checks_input_and_output_sizes_before_the_library():
                 call()
     with pytest.raises(ValueError, match="b_grid"):
         K.box_solve_static(64, z(65 * 65))                  # a host tensor
+
+
+def test_contexts_check_the_interface_shapes_before_any_device_work():
+    import numpy as np
+    with pytest.raises(ValueError, match=r"\(M, 2\)"):
+        K.Kfbi2D(np.zeros((10, 2)), np.zeros((10, 3)), np.zeros(10), 32)
+    with pytest.raises(ValueError, match="M x 1"):
+        K.Kfbi2D(np.zeros((10, 2)), np.zeros((10, 2)), np.zeros(9), 32)
+    with pytest.raises(ValueError, match="M x 6"):
+        K.Kfbi3D(np.zeros((10, 3)), np.zeros((10, 3)), np.zeros((10, 3)), 32)
